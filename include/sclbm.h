@@ -1,0 +1,259 @@
+/*
+ * sclbm.h -- C ABI of libsclbm, the GB300 (sm_103a) implementation of the
+ * data-parallel hot path of the non-intrusive stochastic-collocation lattice
+ * Boltzmann method of arXiv:2508.18202 (Zhong, Teutscher, Kummerlaender,
+ * Krause, Frank, Simonis: "Uncertain data assimilation for urban wind flow
+ * simulations with OpenLB-UQ").
+ *
+ * The problem (Sec. 2.1): incompressible flow whose inflow boundary data are
+ * uncertain; the uncertainty is carried by a vector Z of independent random
+ * inputs (relative wind-speed error, profile exponent, wind direction).  The
+ * method (Sec. 2.4, steps 2-7): pick a quadrature rule {Z^(j), a_j} on the
+ * input space (Sec. 2.3), run the deterministic D3Q19 lattice Boltzmann solver
+ * (Sec. 2.2) at every node with that node's inflow, then reduce the
+ * per-node quantities of interest to quadrature moments (Eq. quad_moments),
+ * gPC coefficients (Eqs. gPC, coef_discrete) and vertical-profile confidence
+ * bands (Sec. 4).
+ *
+ * Conventions
+ *   - Every function returns an int status: SC_OK (0) or a negative SC_ERR_*.
+ *     Nothing aborts the process; no C++ exception crosses the ABI.  After an
+ *     error on a handle, sc_lbm_last_error() names the cause.
+ *   - Cell index: c = x + nx*(y + ny*z), x fastest.  Faces: 0 -x, 1 +x,
+ *     2 -y, 3 +y, 4 -z (ground), 5 +z (sky).
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary (optionally pinned) host memory owned by the
+ *     caller.  The library never frees caller memory.  The only memory the
+ *     library owns is the small host-side state behind an sc_lbm_t.
+ *   - All device work of a handle is issued on the CUDA stream given to
+ *     sc_lbm_init and is asynchronous unless a function says it synchronises.
+ *     Device-side failures (non-finite populations, an expired wait) are
+ *     latched in the workspace and reported by the next synchronising call.
+ */
+#ifndef SCLBM_H
+#define SCLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define SC_OK 0
+#define SC_ERR_ARG (-1)          /* invalid argument or configuration          */
+#define SC_ERR_WORKSPACE (-2)    /* workspace missing, misaligned or too small */
+#define SC_ERR_CUDA (-3)         /* a CUDA runtime call failed                 */
+#define SC_ERR_DIVERGED (-4)     /* non-finite or non-positive density seen    */
+#define SC_ERR_TIMEOUT (-5)      /* a bounded device-side wait expired         */
+#define SC_ERR_UNSUPPORTED (-6)  /* valid request this build does not support  */
+#define SC_ERR_STATE (-7)        /* call not valid in the handle's state       */
+
+/* ------------------------------------------------------------ enumerations */
+/* boundary kind per face (Sec. 2.2 boundary list; OUTFLOW added for channels) */
+#define SC_BC_VELOCITY 0     /* prescribed inflow velocity (moving-wall links) */
+#define SC_BC_OUTFLOW 1      /* zero-gradient outflow; only on face 1 (+x)     */
+#define SC_BC_BOUNCE_BACK 2  /* no-slip wall, half-way bounce-back             */
+#define SC_BC_FREE_SLIP 3    /* specular reflection (the paper's sky)          */
+#define SC_BC_PERIODIC 4     /* both faces of an axis must be periodic         */
+
+/* uncertain inputs (Sec. 2.1 Eq. mult_noise, Sec. 3), uniform on [lo, hi]    */
+#define SC_IN_SPEED_REL 0    /* xi: inflow speed u_ref (1 + xi)                */
+#define SC_IN_ALPHA 1        /* power-law exponent alpha                       */
+#define SC_IN_ANGLE_DEG 2    /* wind direction theta in degrees                */
+
+/* quadrature rules (Sec. 2.3-2.4)                                            */
+#define SC_Q_GL 0            /* tensor Gauss-Legendre, quad_level points/dim   */
+#define SC_Q_CC_SMOLYAK 1    /* Clenshaw-Curtis Smolyak grid, level (1-based)  */
+
+/* population precision                                                       */
+#define SC_P_FP64_PLAIN 0    /* FP64, unshifted, two arrays, one node per launch */
+#define SC_P_FP32_SHIFT 1    /* FP32 storing g_i = f_i - w_i, in place (AA)     */
+#define SC_P_BF16_STORE 2    /* BF16 storage of g_i, FP32 arithmetic            */
+#define SC_P_FP16_STORE 3    /* FP16 storage of g_i, FP32 arithmetic            */
+
+/* execution of sc_lbm_step for the in-place precisions                       */
+#define SC_EXEC_LAUNCH 0     /* one kernel launch per time step                */
+#define SC_EXEC_GRAPH 1      /* replay of a captured CUDA graph of steps       */
+#define SC_EXEC_PERSISTENT 2 /* one cooperative launch, grid barrier per step  */
+
+#define SC_MAX_DOMAINS 8
+#define SC_MAX_NODES 512
+
+/* ------------------------------------------------------------ configuration */
+/* One simulation domain (a box of nx*ny*nz cells, lattice units dx = dt = 1).
+ * Geometry: the half-open boxes [x0,x1)x[y0,y1)x[z0,z1) in `boxes` when
+ * n_boxes > 0, else n_buildings seeded rectangular blocks standing on the
+ * ground (see sc_lbm_geometry).  quad_level: points per dimension (SC_Q_GL)
+ * or the sparse-grid level (SC_Q_CC_SMOLYAK) used for this domain.          */
+typedef struct {
+  int nx, ny, nz;
+  uint64_t geom_seed;
+  int n_buildings, fp_min, fp_max, h_min, h_max;
+  const int32_t* boxes; /* host, [n_boxes][6], read during calls only */
+  int n_boxes;
+  int bc[6];
+  int quad_level;
+} sc_domain_desc;
+
+/* The ensemble.  tau0 = 3 nu + 1/2 (Eq. tauEff with dx = dt = 1); c_smag is
+ * the Smagorinsky constant C_S of Eq. turbVisc (0 = plain BGK).  Nominal
+ * inflow u_in(z) = u_ref (1 + xi) (h/H)^alpha (cos theta, sin theta, 0) with
+ * h = z + 1/2 and H = H_ref (H_ref <= 0 selects the domain height nz); each
+ * uncertain input k replaces xi, alpha or theta by the node coordinate.
+ * ramp_steps: length of the start-up ramp of the inflow (0 = impulsive).
+ * gpc_degree: total degree of the Legendre gPC projection, -1 for none.     */
+typedef struct {
+  int n_domains;
+  const sc_domain_desc* domains; /* host, read during calls only */
+  double tau0, c_smag;
+  double u_ref, alpha, angle_deg, H_ref;
+  int n_inputs;
+  int inputs[3];
+  double lo[3], hi[3];
+  int quad_rule;
+  int ramp_steps;
+  int precision;
+  int gpc_degree;
+} sc_lbm_config;
+
+/* Launch shape of the stream-collide kernels (chosen by sc_lbm_autotune or
+ * set by the caller).  block_x (multiple of 32) by block_y threads cover a
+ * block_x * block_y patch of an x-y plane; each thread walks slab_z cells in
+ * z.  tile_order 0 runs the nodes of one patch back to back (shared geometry
+ * stays in L2), 1 runs all patches of one node first.  graph_steps: time
+ * steps per captured graph (SC_EXEC_GRAPH).                                 */
+typedef struct {
+  int block_x, block_y, slab_z, tile_order, exec_mode, graph_steps;
+} sc_lbm_tuning;
+
+typedef struct sc_lbm_s* sc_lbm_t;
+
+/* ------------------------------------------------------------ host-only calls
+ * These need no GPU and touch no device memory.                            */
+
+/* Bytes of device workspace sc_lbm_init needs for cfg.  SC_ERR_ARG when the
+ * configuration is invalid.                                                  */
+int sc_lbm_workspace_size(const sc_lbm_config* cfg, size_t* bytes_out);
+
+/* Collocation nodes and probability weights of `domain` (Sec. 2.3 Eq.
+ * coef_discrete's {Z^(j), a_j}; Sec. 2.4 step 3).  Z: host [n][n_inputs],
+ * w: host [n].  With Z == NULL only *n_nodes is written.  Nodes are ordered
+ * lexicographically by their integer index on the finest 1-D grid; sparse
+ * grid weights may be negative.  SC_ERR_ARG if cap < *n_nodes.  The result
+ * is bit-for-bit reproducible (IEEE double, no contraction).               */
+int sc_lbm_quadrature(const sc_lbm_config* cfg, int domain, int* n_nodes, double* Z,
+                      double* w, int cap);
+
+/* Solid flags (1 solid, 0 fluid) of `domain` into host uint8 [nz*ny*nx].
+ * Seeded blocks use SplitMix64 (Steele, Lea & Flood 2014) on geom_seed; per
+ * block, in this order: wx, wy ~ U{fp_min..fp_max}; h ~ U{h_min..min(h_max,
+ * nz-4)}; x0 ~ U{nx/8 .. nx - nx/8 - wx}; y0 ~ U{2 .. ny - 2 - wy}; with
+ * U{a..b} = a + (next mod (b - a + 1)).  The paper's geometry is a real
+ * scene (Sec. 3) that is not available; this generator stands in for it.   */
+int sc_lbm_geometry(const sc_lbm_config* cfg, int domain, uint8_t* flags);
+
+/* n distinct probe columns (host int32 [n][2] = x, y) with a fluid ground
+ * cell, drawn from SplitMix64(geom_seed + 1): x ~ U{nx/8..nx-1}, y ~
+ * U{0..ny-1} (Sec. 4, Table probes, stands in for the paper's P1-P3).      */
+int sc_lbm_probe_columns(const sc_lbm_config* cfg, int domain, int n, int32_t* xy);
+
+/* n distinct fluid probe points (host int32 [n][3]) from the same stream:
+ * x ~ U{nx/8..nx-1}, y ~ U{0..ny-1}, z ~ U{0..nz-3}.                       */
+int sc_lbm_probe_points(const sc_lbm_config* cfg, int domain, int n, int32_t* xyz);
+
+/* ------------------------------------------------------------ device calls */
+
+/* Create a handle: validates cfg, builds the quadrature, geometry, link
+ * classification and inflow tables on the host, uploads them into the
+ * caller's device workspace d_ws (>= sc_lbm_workspace_size bytes, 256-byte
+ * aligned) on `cuda_stream` (a cudaStream_t, NULL = legacy default stream),
+ * and sets every node's populations to the equilibrium at rho = 1, u = 0
+ * (Sec. 2.2).  flags_host, if non-NULL, supplies host uint8 solid flags per
+ * domain (flags_host[d] of [nz*ny*nx]) instead of the configured geometry.
+ * The workspace must stay allocated until sc_lbm_destroy.                  */
+int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_stream,
+                const uint8_t* const* flags_host, sc_lbm_t* out);
+
+/* Reset every node to the initial equilibrium and the step count to 0.     */
+int sc_lbm_reset(sc_lbm_t h);
+
+/* Advance every node of every domain by n_steps time steps of the lattice
+ * Boltzmann equation (Sec. 2.2, Eq. deterministicLBE) with BGK collision,
+ * Smagorinsky effective relaxation time (Eqs. tauEff, turbVisc) and the
+ * boundary conditions of the domain's faces and buildings.  Asynchronous.  */
+int sc_lbm_step(sc_lbm_t h, int n_steps);
+
+/* Quadrature reduction of the velocity magnitude |u| at the current time
+ * (Sec. 2.4 steps 6-7):
+ *   mean  = sum_j a_j Q_j / sum_j a_j, std = sqrt(max(var, 0)) with
+ *   var = sum_j a_j Q_j^2 / sum_j a_j - mean^2 (FP64 accumulation)
+ *   (Eq. quad_moments); d_mean, d_std: [nz*ny*nx] doubles, solid cells 0;
+ *   gpc: d_gpc_coef [P][ncell] doubles, coef_alpha = sum_j a_j Q_j
+ *   Phi_alpha(Z^(j)) for the orthonormal Legendre basis (Eq. coef_discrete,
+ *   gamma = 1), P = C(gpc_degree + n_inputs, n_inputs), graded order; NULL
+ *   skips it;
+ *   profiles at the n_p columns probe_xy (host int32 [n_p][2]):
+ *   d_prof [n_p][nz][4] doubles = (mean, std, mean - 1.96 std,
+ *   mean + 1.96 std) (95% band, Sec. 4) and optional d_prof_nodes
+ *   [n_p][n_nodes][nz] floats with each node's profile.
+ * out_host != 0: all outputs are host pointers; the call then copies from
+ * workspace staging and synchronises the stream before returning.
+ * Returns SC_ERR_DIVERGED if a non-finite or non-positive density was met.  */
+int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev,
+                   const int32_t* probe_xy, int n_p, double* prof, float* prof_nodes,
+                   double* gpc_coef, int out_host);
+
+/* Velocity of one node at the current time: d_u device float [3][ncell],
+ * solid cells 0.                                                            */
+int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u);
+
+/* Populations f_i (unshifted, natural layout) of one node at the current
+ * time: d_f device double [19][ncell]; solid cells 0.  Velocity order:
+ * 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 the face diagonals as opposite
+ * pairs (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),
+ * (+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).             */
+int sc_lbm_populations(sc_lbm_t h, int domain, int node, double* d_f);
+
+/* Launch shape: sc_lbm_autotune times candidate shapes on the current
+ * configuration, keeps the fastest and resets the populations afterwards
+ * (tuning steps advance the state).  cache_path (host string, may be NULL)
+ * names a JSON file whose entry for this GPU and configuration is reused or
+ * written.  Synchronises.                                                   */
+int sc_lbm_autotune(sc_lbm_t h, const char* cache_path);
+int sc_lbm_set_tuning(sc_lbm_t h, const sc_lbm_tuning* t);
+int sc_lbm_get_tuning(sc_lbm_t h, sc_lbm_tuning* t);
+
+/* Counters: time steps taken, kernels launched by this handle so far.      */
+int sc_lbm_counters(sc_lbm_t h, long long* steps, long long* kernel_launches);
+
+/* Wait for the handle's stream and report latched device errors
+ * (SC_ERR_DIVERGED, SC_ERR_TIMEOUT) once.                                  */
+int sc_lbm_sync(sc_lbm_t h);
+
+/* Scan every node for non-finite or non-positive density now (latches
+ * SC_ERR_DIVERGED) and synchronise; *n_bad receives the count.             */
+int sc_lbm_check(sc_lbm_t h, long long* n_bad);
+
+/* Test hook for the bounded device-side waits: a nonzero value makes the
+ * next persistent launch wait for a grid-barrier arrival that never comes,
+ * so the wait expires after `spin_limit` polls and the launch returns
+ * SC_ERR_TIMEOUT (through sc_lbm_sync) with the device still usable.        */
+int sc_lbm_debug_barrier(sc_lbm_t h, int never_arrive, long long spin_limit);
+
+/* Host snapshot of the full state (populations, outflow plane, step count)
+ * for checkpoint / resume.  sc_lbm_state_size gives the bytes; save copies
+ * to host_buf and synchronises; load restores from a buffer written by save
+ * for the same configuration (checked by a header checksum).               */
+int sc_lbm_state_size(sc_lbm_t h, size_t* bytes);
+int sc_lbm_save(sc_lbm_t h, void* host_buf, size_t bytes);
+int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes);
+
+const char* sc_lbm_last_error(sc_lbm_t h);
+int sc_lbm_destroy(sc_lbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCLBM_H */

@@ -1,0 +1,968 @@
+// api.cu -- the C ABI of libsclbm (include/sclbm.h): validation, workspace
+// layout, the handle, and the host-side driving of the CUDA kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sclbm_internal.h"
+
+using namespace sclbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxProbes = 256;
+constexpr long long kSpinLimit = 1LL << 26;  // bounded barrier polls (~seconds)
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int precision) {
+  switch (precision) {
+    case SC_P_FP64_PLAIN: return 8;
+    case SC_P_FP32_SHIFT: return 4;
+    default: return 2;
+  }
+}
+
+// Offsets of every buffer inside the caller's workspace.
+struct DomLayout {
+  int nq = 0, P = 0;
+  long long ncell = 0;
+  size_t flags = 0, link = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
+};
+struct Layout {
+  size_t hdr = 0, ramp_f = 0, ramp_d = 0, probes = 0;
+  size_t st_mean = 0, st_std = 0, st_coef = 0, st_prof = 0, st_pnodes = 0;
+  DomLayout dom[kMaxDomains];
+  size_t total = 0;
+};
+
+struct Header {  // first 256 bytes of the workspace
+  unsigned long long step;
+  unsigned long long check_count;
+  unsigned int done;
+  unsigned int err;
+  unsigned int bar_count;
+  unsigned int bar_gen;
+};
+
+int validate(const sc_lbm_config* c, std::string& why) {
+  if (!c) { why = "null config"; return SC_ERR_ARG; }
+  if (c->n_domains < 1 || c->n_domains > kMaxDomains || !c->domains) {
+    why = "n_domains must be 1.." + std::to_string(kMaxDomains);
+    return SC_ERR_ARG;
+  }
+  if (!(c->tau0 > 0.5)) { why = "tau0 must exceed 1/2"; return SC_ERR_ARG; }
+  if (c->c_smag < 0) { why = "c_smag must be >= 0"; return SC_ERR_ARG; }
+  if (c->n_inputs < 1 || c->n_inputs > 3) { why = "n_inputs must be 1..3"; return SC_ERR_ARG; }
+  for (int k = 0; k < c->n_inputs; ++k) {
+    if (c->inputs[k] < SC_IN_SPEED_REL || c->inputs[k] > SC_IN_ANGLE_DEG) {
+      why = "bad input kind";
+      return SC_ERR_ARG;
+    }
+    if (!(c->hi[k] > c->lo[k])) { why = "input range must have hi > lo"; return SC_ERR_ARG; }
+  }
+  if (c->quad_rule != SC_Q_GL && c->quad_rule != SC_Q_CC_SMOLYAK) { why = "bad quad_rule"; return SC_ERR_ARG; }
+  if (c->precision < SC_P_FP64_PLAIN || c->precision > SC_P_FP16_STORE) { why = "bad precision"; return SC_ERR_ARG; }
+  if (c->ramp_steps < 0 || c->ramp_steps > 10000000) { why = "bad ramp_steps"; return SC_ERR_ARG; }
+  if (c->gpc_degree > 8) { why = "gpc_degree too large"; return SC_ERR_UNSUPPORTED; }
+  if (c->gpc_degree >= 0 && hn_gpc_size(c->n_inputs, c->gpc_degree) > kMaxGpcP) {
+    why = "gPC basis larger than " + std::to_string(kMaxGpcP);
+    return SC_ERR_UNSUPPORTED;
+  }
+  for (int d = 0; d < c->n_domains; ++d) {
+    const sc_domain_desc& D = c->domains[d];
+    if (D.nx < 1 || D.ny < 1 || D.nz < 1) { why = "domain sizes must be positive"; return SC_ERR_ARG; }
+    if ((long long)D.nx * D.ny * D.nz > (1LL << 31)) { why = "domain too large"; return SC_ERR_UNSUPPORTED; }
+    for (int a = 0; a < 3; ++a) {
+      const bool lo = D.bc[2 * a] == SC_BC_PERIODIC, hi = D.bc[2 * a + 1] == SC_BC_PERIODIC;
+      if (lo != hi) { why = "periodic faces come in pairs"; return SC_ERR_ARG; }
+    }
+    for (int f = 0; f < 6; ++f) {
+      if (D.bc[f] < SC_BC_VELOCITY || D.bc[f] > SC_BC_PERIODIC) { why = "bad face kind"; return SC_ERR_ARG; }
+      if (D.bc[f] == SC_BC_OUTFLOW && f != 1) {
+        why = "OUTFLOW is supported on face 1 (+x) only";
+        return SC_ERR_UNSUPPORTED;
+      }
+    }
+    if (D.quad_level < 1) { why = "quad_level must be >= 1"; return SC_ERR_ARG; }
+  }
+  return SC_OK;
+}
+
+int node_count(const sc_lbm_config* c, int d, std::vector<double>* Z, std::vector<double>* w) {
+  std::vector<double> z, ww;
+  int rc = hn_quadrature(c->quad_rule, c->n_inputs, c->domains[d].quad_level, c->lo, c->hi, z, ww);
+  if (rc) return -1;
+  if (Z) *Z = z;
+  if (w) *w = ww;
+  return (int)ww.size();
+}
+
+int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
+  int rc = validate(c, why);
+  if (rc) return rc;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L.hdr = take(sizeof(Header));
+  L.ramp_f = take(sizeof(float) * (size_t)(c->ramp_steps + 1));
+  L.ramp_d = take(sizeof(double) * (size_t)(c->ramp_steps + 1));
+  L.probes = take(sizeof(int32_t) * 2 * kMaxProbes);
+  const size_t sb = storage_bytes(c->precision);
+  const int P = c->gpc_degree >= 0 ? hn_gpc_size(c->n_inputs, c->gpc_degree) : 0;
+  long long max_cell = 0;
+  int max_nz = 0, max_nq = 0;
+  for (int d = 0; d < c->n_domains; ++d) {
+    const sc_domain_desc& D = c->domains[d];
+    DomLayout& M = L.dom[d];
+    M.nq = node_count(c, d, nullptr, nullptr);
+    if (M.nq < 1) { why = "quadrature level not supported"; return SC_ERR_ARG; }
+    if (M.nq > SC_MAX_NODES) { why = "too many collocation nodes"; return SC_ERR_UNSUPPORTED; }
+    M.P = P;
+    M.ncell = (long long)D.nx * D.ny * D.nz;
+    M.flags = take((size_t)M.ncell);
+    M.link = take(sizeof(uint32_t) * (size_t)M.ncell);
+    M.uin_f = take(16 * (size_t)M.nq * D.nz);
+    M.uin_d = take(24 * (size_t)M.nq * D.nz);
+    M.g = take(sb * kQ * (size_t)M.ncell * M.nq);
+    if (c->precision == SC_P_FP64_PLAIN) M.g2 = take(sb * kQ * (size_t)M.ncell * M.nq);
+    else M.bout = take(sizeof(float) * 5 * (size_t)D.nz * D.ny * M.nq);
+    M.ab = take(sizeof(double) * (size_t)M.nq * (P + 1));
+    max_cell = std::max(max_cell, M.ncell);
+    max_nz = std::max(max_nz, D.nz);
+    max_nq = std::max(max_nq, M.nq);
+  }
+  L.st_mean = take(sizeof(double) * (size_t)max_cell);
+  L.st_std = take(sizeof(double) * (size_t)max_cell);
+  L.st_coef = take(sizeof(double) * (size_t)max_cell * P);
+  L.st_prof = take(sizeof(double) * 4 * (size_t)kMaxProbes * max_nz);
+  L.st_pnodes = take(sizeof(float) * (size_t)kMaxProbes * max_nq * max_nz);
+  L.total = off;
+  return SC_OK;
+}
+
+// ------------------------------------------------------------ tiny JSON cache
+std::string tune_key(const sc_lbm_config* c, const char* gpu) {
+  std::string k = std::string(gpu) + "|p" + std::to_string(c->precision) + "|s" +
+                  std::to_string(c->c_smag > 0 ? 1 : 0);
+  for (int d = 0; d < c->n_domains; ++d) {
+    const sc_domain_desc& D = c->domains[d];
+    k += "|" + std::to_string(D.nx) + "x" + std::to_string(D.ny) + "x" + std::to_string(D.nz) +
+         "n" + std::to_string(D.quad_level);
+  }
+  return k;
+}
+
+std::map<std::string, std::vector<int>> read_cache(const char* path) {
+  std::map<std::string, std::vector<int>> m;
+  if (!path) return m;
+  FILE* fh = fopen(path, "r");
+  if (!fh) return m;
+  std::string s;
+  char buf[4096];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof buf, fh)) > 0) s.append(buf, got);
+  fclose(fh);
+  size_t pos = 0;
+  while (true) {
+    size_t q0 = s.find('"', pos);
+    if (q0 == std::string::npos) break;
+    size_t q1 = s.find('"', q0 + 1);
+    if (q1 == std::string::npos) break;
+    std::string key = s.substr(q0 + 1, q1 - q0 - 1);
+    size_t b0 = s.find('[', q1), b1 = s.find(']', q1);
+    if (b0 == std::string::npos || b1 == std::string::npos) break;
+    std::vector<int> v;
+    std::string body = s.substr(b0 + 1, b1 - b0 - 1);
+    char* p = &body[0];
+    while (*p) {
+      char* e;
+      long x = strtol(p, &e, 10);
+      if (e == p) { ++p; continue; }
+      v.push_back((int)x);
+      p = e;
+    }
+    m[key] = v;
+    pos = b1 + 1;
+  }
+  return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, std::vector<int>>& m) {
+  if (!path) return;
+  std::string tmp = std::string(path) + ".tmp";
+  FILE* fh = fopen(tmp.c_str(), "w");
+  if (!fh) return;
+  fprintf(fh, "{\n");
+  size_t k = 0;
+  for (const auto& kv : m) {
+    fprintf(fh, "  \"%s\": [", kv.first.c_str());
+    for (size_t t = 0; t < kv.second.size(); ++t) fprintf(fh, "%s%d", t ? ", " : "", kv.second[t]);
+    fprintf(fh, "]%s\n", ++k < m.size() ? "," : "");
+  }
+  fprintf(fh, "}\n");
+  fclose(fh);
+  rename(tmp.c_str(), path);
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ULL) {
+  const unsigned char* p = (const unsigned char*)data;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+}  // namespace
+
+// ======================================================================= handle
+struct sc_lbm_s {
+  sc_lbm_config cfg;
+  std::vector<sc_domain_desc> doms;
+  std::vector<std::vector<int32_t>> boxes;
+  Layout L;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  StepParams P;
+  std::vector<double> wsum;
+  std::vector<int> nq;
+  int gpcP = 0;
+  sc_lbm_tuning tune;
+  long long steps = 0, launches = 0;
+  std::string err;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  int persist_grid = 0;
+  int never_arrive = 0;
+  long long spin_limit = kSpinLimit;
+  Header* hdr() const { return reinterpret_cast<Header*>(ws + L.hdr); }
+};
+
+namespace {
+
+int fail(sc_lbm_t h, int rc, const std::string& why) {
+  if (h) h->err = why;
+  return rc;
+}
+
+int cuda_fail(sc_lbm_t h, cudaError_t e, const char* where) {
+  if (h) h->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return SC_ERR_CUDA;
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);         \
+  } while (0)
+
+void apply_tiling(sc_lbm_t h) {
+  StepParams& P = h->P;
+  P.bx = h->tune.block_x;
+  P.by = h->tune.block_y;
+  P.bz = h->tune.slab_z;
+  P.order = h->tune.tile_order;
+  long long begin = 0;
+  for (int d = 0; d < P.n_domains; ++d) {
+    DevDomain& D = P.dom[d];
+    D.tiles_x = (D.nx + P.bx - 1) / P.bx;
+    D.tiles_y = (D.ny + P.by - 1) / P.by;
+    D.tiles_z = (D.nz + P.bz - 1) / P.bz;
+    D.tiles_per_node = D.tiles_x * D.tiles_y * D.tiles_z;
+    D.tile_begin = begin;
+    begin += D.tiles_per_node * D.nodes;
+  }
+  P.total_tiles = begin;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_len = 0;
+  }
+  h->persist_grid = 0;
+}
+
+int check_tuning(const sc_lbm_tuning& t) {
+  if (t.block_x < 32 || t.block_x % 32 || t.block_y < 1 || t.block_x * t.block_y > 1024) return SC_ERR_ARG;
+  if (t.slab_z < 1 || t.slab_z > 4096) return SC_ERR_ARG;
+  if (t.tile_order < 0 || t.tile_order > 1) return SC_ERR_ARG;
+  if (t.exec_mode < SC_EXEC_LAUNCH || t.exec_mode > SC_EXEC_PERSISTENT) return SC_ERR_ARG;
+  if (t.graph_steps < 1 || t.graph_steps > 100000) return SC_ERR_ARG;
+  return SC_OK;
+}
+
+int reset_state(sc_lbm_t h) {
+  int rc = launch_init_equilibrium(h->P, h->cfg.precision, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "init kernel");
+  ++h->launches;
+  CK(cudaMemsetAsync(h->ws + h->L.hdr, 0, sizeof(Header), h->stream));
+  h->steps = 0;
+  return SC_OK;
+}
+
+// n steps with one launch each
+int run_launches(sc_lbm_t h, int n) {
+  const int grid = (int)h->P.total_tiles;
+  for (int s = 0; s < n; ++s) {
+    int rc = launch_aa_step(h->P, h->cfg.precision, h->stream, grid);
+    if (rc) return cuda_fail(h, (cudaError_t)rc, "aa_step launch");
+    ++h->launches;
+  }
+  return SC_OK;
+}
+
+int run_graph(sc_lbm_t h, int n) {
+  const int G = h->tune.graph_steps;
+  if (!h->stream) return run_launches(h, n);  // capture needs a non-default stream
+  if (!h->graph || h->graph_len != G) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int s = 0; s < G && !rc; ++s)
+      rc = launch_aa_step(h->P, h->cfg.precision, h->stream, (int)h->P.total_tiles);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(h, (cudaError_t)rc, "graph capture launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->graph_len = G;
+  }
+  const int reps = n / G;
+  for (int r = 0; r < reps; ++r) {
+    CK(cudaGraphLaunch(h->graph, h->stream));
+    h->launches += G;
+  }
+  return run_launches(h, n - reps * G);
+}
+
+int run_persistent(sc_lbm_t h, int n) {
+  if (!h->persist_grid) {
+    int grid = 0;
+    int rc = aa_persistent_max_grid(h->P, h->cfg.precision, &grid);
+    if (rc || grid < 1) return cuda_fail(h, (cudaError_t)(rc ? rc : cudaErrorInvalidConfiguration), "occupancy");
+    h->persist_grid = (int)std::min<long long>(grid, h->P.total_tiles);
+  }
+  const int chunk = 500;
+  for (int done = 0; done < n;) {
+    const int k = std::min(chunk, n - done);
+    StepParams P = h->P;
+    P.n_steps = k;
+    P.never_arrive = h->never_arrive;
+    P.spin_limit = h->spin_limit;
+    CK(cudaMemsetAsync(&h->hdr()->bar_count, 0, sizeof(unsigned int), h->stream));
+    int rc = launch_aa_persistent(P, h->cfg.precision, h->stream, h->persist_grid);
+    if (rc) return cuda_fail(h, (cudaError_t)rc, "persistent launch");
+    ++h->launches;
+    done += k;
+  }
+  return SC_OK;
+}
+
+int run_plain(sc_lbm_t h, int n) {
+  for (int d = 0; d < h->P.n_domains; ++d)
+    for (int j = 0; j < h->P.dom[d].nodes; ++j) {
+      StepParams P = h->P;
+      P.plain_domain = d;
+      P.plain_node = j;
+      for (int s = 0; s < n; ++s) {
+        int rc = launch_plain_step(P, (unsigned long long)(h->steps + s), h->stream);
+        if (rc) return cuda_fail(h, (cudaError_t)rc, "plain_step launch");
+        ++h->launches;
+      }
+    }
+  int rc = launch_set_counter(&h->hdr()->step, (unsigned long long)(h->steps + n), h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "set counter");
+  ++h->launches;
+  return SC_OK;
+}
+
+int do_steps(sc_lbm_t h, int n) {
+  if (n <= 0) return SC_OK;
+  int rc;
+  if (h->cfg.precision == SC_P_FP64_PLAIN) rc = run_plain(h, n);
+  else if (h->tune.exec_mode == SC_EXEC_GRAPH) rc = run_graph(h, n);
+  else if (h->tune.exec_mode == SC_EXEC_PERSISTENT) rc = run_persistent(h, n);
+  else rc = run_launches(h, n);
+  if (rc == SC_OK) h->steps += n;
+  return rc;
+}
+
+int read_err(sc_lbm_t h, unsigned* bits) {
+  CK(cudaStreamSynchronize(h->stream));
+  unsigned v = 0;
+  CK(cudaMemcpy(&v, &h->hdr()->err, sizeof v, cudaMemcpyDeviceToHost));
+  if (v) CK(cudaMemset(&h->hdr()->err, 0, sizeof(unsigned)));
+  *bits = v;
+  return SC_OK;
+}
+
+int err_status(sc_lbm_t h, unsigned bits) {
+  if (bits & kErrTimeout) return fail(h, SC_ERR_TIMEOUT, "a bounded device-side wait expired");
+  if (bits & kErrDiverged) return fail(h, SC_ERR_DIVERGED, "non-finite or non-positive density");
+  return SC_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+int sc_lbm_workspace_size(const sc_lbm_config* cfg, size_t* bytes_out) {
+  if (!bytes_out) return SC_ERR_ARG;
+  Layout L;
+  std::string why;
+  int rc = plan(cfg, L, why);
+  if (rc) return rc;
+  *bytes_out = L.total;
+  return SC_OK;
+}
+
+int sc_lbm_quadrature(const sc_lbm_config* cfg, int domain, int* n_nodes, double* Z, double* w,
+                      int cap) {
+  std::string why;
+  if (!n_nodes || validate(cfg, why)) return SC_ERR_ARG;
+  if (domain < 0 || domain >= cfg->n_domains) return SC_ERR_ARG;
+  std::vector<double> z, ww;
+  int n = node_count(cfg, domain, &z, &ww);
+  if (n < 1) return SC_ERR_ARG;
+  *n_nodes = n;
+  if (!Z) return SC_OK;
+  if (cap < n || !w) return SC_ERR_ARG;
+  memcpy(Z, z.data(), sizeof(double) * z.size());
+  memcpy(w, ww.data(), sizeof(double) * ww.size());
+  return SC_OK;
+}
+
+int sc_lbm_geometry(const sc_lbm_config* cfg, int domain, uint8_t* flags) {
+  std::string why;
+  if (!flags || validate(cfg, why)) return SC_ERR_ARG;
+  if (domain < 0 || domain >= cfg->n_domains) return SC_ERR_ARG;
+  std::vector<uint8_t> f;
+  int rc = hn_geometry(cfg->domains[domain], f);
+  if (rc) return rc;
+  memcpy(flags, f.data(), f.size());
+  return SC_OK;
+}
+
+int sc_lbm_probe_columns(const sc_lbm_config* cfg, int domain, int n, int32_t* xy) {
+  std::string why;
+  if (!xy || n < 0 || validate(cfg, why)) return SC_ERR_ARG;
+  if (domain < 0 || domain >= cfg->n_domains) return SC_ERR_ARG;
+  std::vector<uint8_t> f;
+  int rc = hn_geometry(cfg->domains[domain], f);
+  if (rc) return rc;
+  return hn_probe_columns(cfg->domains[domain], f.data(), n, xy);
+}
+
+int sc_lbm_probe_points(const sc_lbm_config* cfg, int domain, int n, int32_t* xyz) {
+  std::string why;
+  if (!xyz || n < 0 || validate(cfg, why)) return SC_ERR_ARG;
+  if (domain < 0 || domain >= cfg->n_domains) return SC_ERR_ARG;
+  std::vector<uint8_t> f;
+  int rc = hn_geometry(cfg->domains[domain], f);
+  if (rc) return rc;
+  return hn_probe_points(cfg->domains[domain], f.data(), n, xyz);
+}
+
+int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_stream,
+                const uint8_t* const* flags_host, sc_lbm_t* out) {
+  if (!out) return SC_ERR_ARG;
+  *out = nullptr;
+  Layout L;
+  std::string why;
+  int rc = plan(cfg, L, why);
+  if (rc) return rc;
+  if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0 || bytes < L.total) return SC_ERR_WORKSPACE;
+  sc_lbm_t h = new (std::nothrow) sc_lbm_s();
+  if (!h) return SC_ERR_ARG;
+  h->cfg = *cfg;
+  h->doms.assign(cfg->domains, cfg->domains + cfg->n_domains);
+  h->boxes.resize(cfg->n_domains);
+  for (int d = 0; d < cfg->n_domains; ++d) {
+    const sc_domain_desc& D = cfg->domains[d];
+    if (D.n_boxes > 0 && D.boxes) h->boxes[d].assign(D.boxes, D.boxes + 6 * D.n_boxes);
+    h->doms[d].boxes = h->boxes[d].empty() ? nullptr : h->boxes[d].data();
+  }
+  h->cfg.domains = h->doms.data();
+  h->L = L;
+  h->ws = (char*)d_ws;
+  h->ws_bytes = bytes;
+  h->stream = (cudaStream_t)cuda_stream;
+  const sc_lbm_config& c = h->cfg;
+  StepParams& P = h->P;
+  memset(&P, 0, sizeof P);
+  P.n_domains = c.n_domains;
+  P.tau0 = (float)c.tau0;
+  P.tau0_d = c.tau0;
+  P.smag18c2 = (float)(18.0 * c.c_smag * c.c_smag);
+  P.smag18c2_d = 18.0 * c.c_smag * c.c_smag;
+  P.csmag_on = c.c_smag > 0 ? 1 : 0;
+  P.ramp_steps = c.ramp_steps;
+  P.ramp_f = (const float*)(h->ws + L.ramp_f);
+  P.ramp_d = (const double*)(h->ws + L.ramp_d);
+  Header* H = h->hdr();
+  P.step = &H->step;
+  P.done = &H->done;
+  P.err = &H->err;
+  P.bar_count = &H->bar_count;
+  P.bar_gen = &H->bar_gen;
+  P.spin_limit = kSpinLimit;
+  h->gpcP = c.gpc_degree >= 0 ? hn_gpc_size(c.n_inputs, c.gpc_degree) : 0;
+
+  // host tables (kept alive until the stream is synchronised below)
+  std::vector<std::vector<uint8_t>> flags(c.n_domains);
+  std::vector<std::vector<uint32_t>> links(c.n_domains);
+  std::vector<std::vector<float>> uinf(c.n_domains);
+  std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
+  std::vector<float> rampf(c.ramp_steps + 1);
+  std::vector<double> rampd(c.ramp_steps + 1);
+  for (int m = 0; m <= c.ramp_steps; ++m) {
+    rampd[m] = hn_ramp(c.ramp_steps, m);
+    rampf[m] = (float)rampd[m];
+  }
+  h->wsum.assign(c.n_domains, 0.0);
+  h->nq.assign(c.n_domains, 0);
+  for (int d = 0; d < c.n_domains; ++d) {
+    const sc_domain_desc& D = c.domains[d];
+    const DomLayout& M = L.dom[d];
+    if (flags_host && flags_host[d]) {
+      flags[d].assign(flags_host[d], flags_host[d] + M.ncell);
+      for (auto& v : flags[d]) v = v ? 1 : 0;
+    } else {
+      rc = hn_geometry(D, flags[d]);
+      if (rc) { delete h; return rc; }
+    }
+    hn_link_words(D, flags[d].data(), links[d]);
+    std::vector<double> Z, w;
+    node_count(&c, d, &Z, &w);
+    const int nq = (int)w.size();
+    h->nq[d] = nq;
+    double ws = 0.0;
+    for (double v : w) ws += v;
+    h->wsum[d] = ws;
+    const double H = c.H_ref > 0 ? c.H_ref : (double)D.nz;
+    uinf[d].assign((size_t)nq * D.nz * 4, 0.0f);
+    uind[d].assign((size_t)nq * D.nz * 3, 0.0);
+    abt[d].assign((size_t)nq * (h->gpcP + 1), 0.0);
+    std::vector<double> phi(h->gpcP > 0 ? h->gpcP : 1);
+    for (int j = 0; j < nq; ++j) {
+      double xi = 0.0, al = c.alpha, th = c.angle_deg;
+      double s[3] = {0, 0, 0};
+      for (int t = 0; t < c.n_inputs; ++t) {
+        const double zt = Z[(size_t)j * c.n_inputs + t];
+        if (c.inputs[t] == SC_IN_SPEED_REL) xi = zt;
+        else if (c.inputs[t] == SC_IN_ALPHA) al = zt;
+        else th = zt;
+        s[t] = (2.0 * zt - c.lo[t] - c.hi[t]) / (c.hi[t] - c.lo[t]);
+      }
+      double* ud = &uind[d][(size_t)j * D.nz * 3];
+      hn_inflow(D.nz, c.u_ref, xi, al, H, th, ud);
+      for (int k = 0; k < D.nz; ++k)
+        for (int a = 0; a < 3; ++a) uinf[d][((size_t)j * D.nz + k) * 4 + a] = (float)ud[3 * k + a];
+      abt[d][(size_t)j * (h->gpcP + 1)] = w[j];
+      if (h->gpcP > 0) {
+        hn_gpc_basis(c.n_inputs, c.gpc_degree, s, phi.data());
+        for (int a = 0; a < h->gpcP; ++a) abt[d][(size_t)j * (h->gpcP + 1) + 1 + a] = w[j] * phi[a];
+      }
+    }
+    DevDomain& V = P.dom[d];
+    V.nx = D.nx;
+    V.ny = D.ny;
+    V.nz = D.nz;
+    V.nodes = nq;
+    V.ncell = M.ncell;
+    for (int f = 0; f < 6; ++f) V.bc[f] = D.bc[f];
+    V.flags = (const uint8_t*)(h->ws + M.flags);
+    V.link = (const uint32_t*)(h->ws + M.link);
+    V.uin_f = (const float4*)(h->ws + M.uin_f);
+    V.uin_d = (const double*)(h->ws + M.uin_d);
+    V.g = h->ws + M.g;
+    V.g2 = c.precision == SC_P_FP64_PLAIN ? (void*)(h->ws + M.g2) : nullptr;
+    V.bout = c.precision == SC_P_FP64_PLAIN ? nullptr : (float*)(h->ws + M.bout);
+  }
+  // default launch shape
+  h->tune.block_x = 128;
+  h->tune.block_y = 2;
+  h->tune.slab_z = 1;
+  h->tune.tile_order = 0;
+  h->tune.exec_mode = SC_EXEC_LAUNCH;
+  h->tune.graph_steps = 50;
+  apply_tiling(h);
+
+  auto up = [&](size_t off, const void* src, size_t n) {
+    return cudaMemcpyAsync(h->ws + off, src, n, cudaMemcpyHostToDevice, h->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  e = up(L.ramp_f, rampf.data(), sizeof(float) * rampf.size());
+  if (e == cudaSuccess) e = up(L.ramp_d, rampd.data(), sizeof(double) * rampd.size());
+  for (int d = 0; d < c.n_domains && e == cudaSuccess; ++d) {
+    const DomLayout& M = L.dom[d];
+    e = up(M.flags, flags[d].data(), flags[d].size());
+    if (e == cudaSuccess) e = up(M.link, links[d].data(), sizeof(uint32_t) * links[d].size());
+    if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
+    if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
+    if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());
+    if (e == cudaSuccess && M.bout)
+      e = cudaMemsetAsync(h->ws + M.bout, 0, sizeof(float) * 5 * (size_t)c.domains[d].nz * c.domains[d].ny * M.nq, h->stream);
+  }
+  if (e != cudaSuccess) {
+    int r = cuda_fail(h, e, "upload");
+    delete h;
+    return r;
+  }
+  rc = reset_state(h);
+  if (rc == SC_OK) {
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "init sync");
+  }
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SC_OK;
+}
+
+int sc_lbm_reset(sc_lbm_t h) {
+  if (!h) return SC_ERR_ARG;
+  return reset_state(h);
+}
+
+int sc_lbm_step(sc_lbm_t h, int n_steps) {
+  if (!h || n_steps < 0) return SC_ERR_ARG;
+  return do_steps(h, n_steps);
+}
+
+int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const int32_t* probe_xy,
+                   int n_p, double* prof, float* prof_nodes, double* gpc_coef, int out_host) {
+  if (!h || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (n_p < 0 || n_p > kMaxProbes || (n_p > 0 && (!probe_xy || !prof))) return SC_ERR_ARG;
+  if ((mean == nullptr) != (stdev == nullptr)) return SC_ERR_ARG;
+  if (gpc_coef && h->gpcP == 0) return fail(h, SC_ERR_ARG, "gpc_degree < 0 in the configuration");
+  const DevDomain& D = h->P.dom[domain];
+  for (int p = 0; p < n_p; ++p) {
+    const int x = probe_xy[2 * p], y = probe_xy[2 * p + 1];
+    if (x < 0 || x >= D.nx || y < 0 || y >= D.ny) return fail(h, SC_ERR_ARG, "probe outside the domain");
+  }
+  const Layout& L = h->L;
+  MomentArgs A;
+  A.domain = domain;
+  A.ab = (const double*)(h->ws + L.dom[domain].ab);
+  A.nq = h->nq[domain];
+  A.stride = h->gpcP + 1;
+  A.P = gpc_coef ? h->gpcP : 0;
+  A.wsum = h->wsum[domain];
+  A.mean = out_host ? (mean ? (double*)(h->ws + L.st_mean) : nullptr) : mean;
+  A.stdev = out_host ? (stdev ? (double*)(h->ws + L.st_std) : nullptr) : stdev;
+  A.coef = out_host ? (gpc_coef ? (double*)(h->ws + L.st_coef) : nullptr) : gpc_coef;
+  A.probes = (const int32_t*)(h->ws + L.probes);
+  A.n_p = n_p;
+  A.prof = out_host ? (double*)(h->ws + L.st_prof) : prof;
+  A.prof_nodes = out_host ? (prof_nodes ? (float*)(h->ws + L.st_pnodes) : nullptr) : prof_nodes;
+  if (n_p > 0)
+    CK(cudaMemcpyAsync(h->ws + L.probes, probe_xy, sizeof(int32_t) * 2 * n_p, cudaMemcpyHostToDevice,
+                       h->stream));
+  int rc = launch_moments(h->P, h->cfg.precision, A, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "moments launch");
+  h->launches += (A.mean ? 1 : 0) + (n_p > 0 ? 1 : 0);
+  if (!out_host) return SC_OK;
+  const size_t nc = (size_t)D.ncell;
+  if (mean) CK(cudaMemcpyAsync(mean, A.mean, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
+  if (stdev) CK(cudaMemcpyAsync(stdev, A.stdev, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
+  if (gpc_coef)
+    CK(cudaMemcpyAsync(gpc_coef, A.coef, sizeof(double) * nc * h->gpcP, cudaMemcpyDeviceToHost, h->stream));
+  if (n_p > 0) {
+    CK(cudaMemcpyAsync(prof, A.prof, sizeof(double) * 4 * n_p * D.nz, cudaMemcpyDeviceToHost, h->stream));
+    if (prof_nodes)
+      CK(cudaMemcpyAsync(prof_nodes, A.prof_nodes, sizeof(float) * (size_t)n_p * A.nq * D.nz,
+                         cudaMemcpyDeviceToHost, h->stream));
+  }
+  unsigned bits = 0;
+  rc = read_err(h, &bits);
+  if (rc) return rc;
+  return err_status(h, bits);
+}
+
+int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u) {
+  if (!h || !d_u || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (node < 0 || node >= h->P.dom[domain].nodes) return SC_ERR_ARG;
+  int rc = launch_export(h->P, h->cfg.precision, domain, node, nullptr, d_u, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "export launch");
+  ++h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_populations(sc_lbm_t h, int domain, int node, double* d_f) {
+  if (!h || !d_f || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (node < 0 || node >= h->P.dom[domain].nodes) return SC_ERR_ARG;
+  int rc = launch_export(h->P, h->cfg.precision, domain, node, d_f, nullptr, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "export launch");
+  ++h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_set_tuning(sc_lbm_t h, const sc_lbm_tuning* t) {
+  if (!h || !t || check_tuning(*t)) return SC_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  h->tune = *t;
+  apply_tiling(h);
+  return SC_OK;
+}
+
+int sc_lbm_get_tuning(sc_lbm_t h, sc_lbm_tuning* t) {
+  if (!h || !t) return SC_ERR_ARG;
+  *t = h->tune;
+  return SC_OK;
+}
+
+int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
+  if (!h) return SC_ERR_ARG;
+  if (h->cfg.precision == SC_P_FP64_PLAIN) return SC_OK;  // the plain path is not tuned
+  int dev = 0;
+  cudaDeviceProp prop;
+  CK(cudaGetDevice(&dev));
+  CK(cudaGetDeviceProperties(&prop, dev));
+  const std::string key = tune_key(&h->cfg, prop.name);
+  auto cache = read_cache(cache_path);
+  auto it = cache.find(key);
+  if (it != cache.end() && it->second.size() == 6) {
+    sc_lbm_tuning t{it->second[0], it->second[1], it->second[2], it->second[3], it->second[4], it->second[5]};
+    if (check_tuning(t) == SC_OK) return sc_lbm_set_tuning(h, &t);
+  }
+  int maxnx = 0;
+  for (int d = 0; d < h->P.n_domains; ++d) maxnx = std::max(maxnx, h->P.dom[d].nx);
+  std::vector<sc_lbm_tuning> cand;
+  const int bxs[] = {32, 64, 128, 256, 512};
+  const int bys[] = {1, 2, 4, 8};
+  const int bzs[] = {1, 2, 4};
+  for (int bx : bxs) {
+    if (bx > 32 && bx / 2 >= maxnx) continue;
+    for (int by : bys)
+      for (int bz : bzs) {
+        if (bx * by > 512 || bx * by < 64) continue;
+        for (int order = 0; order < 2; ++order) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50});
+      }
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  long long lups = 0;
+  for (int d = 0; d < h->P.n_domains; ++d) lups += h->P.dom[d].ncell * h->P.dom[d].nodes;
+  const int reps = (int)std::max<long long>(4, std::min<long long>(40, 2000000000LL / std::max(1LL, lups)));
+  float best = 1e30f;
+  sc_lbm_tuning best_t = h->tune;
+  auto time_it = [&](const sc_lbm_tuning& t, float* ms) -> int {
+    int rc = sc_lbm_set_tuning(h, &t);
+    if (rc) return rc;
+    rc = do_steps(h, 2);
+    if (rc) return rc;
+    CK(cudaEventRecord(e0, h->stream));
+    rc = do_steps(h, 2 * reps);
+    if (rc) return rc;
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    return SC_OK;
+  };
+  for (const auto& t : cand) {
+    float ms = 0;
+    int rc = time_it(t, &ms);
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    if (ms < best) { best = ms; best_t = t; }
+  }
+  // execution mode for the best shape
+  for (int mode : {SC_EXEC_GRAPH, SC_EXEC_PERSISTENT}) {
+    sc_lbm_tuning t = best_t;
+    t.exec_mode = mode;
+    float ms = 0;
+    int rc = time_it(t, &ms);
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    if (ms < best * 0.98f) { best = ms; best_t = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc = sc_lbm_set_tuning(h, &best_t);
+  if (rc) return rc;
+  rc = reset_state(h);
+  if (rc) return rc;
+  unsigned bits = 0;
+  rc = read_err(h, &bits);
+  if (rc) return rc;
+  if (cache_path) {
+    cache[key] = {best_t.block_x, best_t.block_y, best_t.slab_z, best_t.tile_order, best_t.exec_mode,
+                  best_t.graph_steps};
+    write_cache(cache_path, cache);
+  }
+  return err_status(h, bits);
+}
+
+int sc_lbm_counters(sc_lbm_t h, long long* steps, long long* kernel_launches) {
+  if (!h) return SC_ERR_ARG;
+  if (steps) *steps = h->steps;
+  if (kernel_launches) *kernel_launches = h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_sync(sc_lbm_t h) {
+  if (!h) return SC_ERR_ARG;
+  unsigned bits = 0;
+  int rc = read_err(h, &bits);
+  if (rc) return rc;
+  return err_status(h, bits);
+}
+
+int sc_lbm_check(sc_lbm_t h, long long* n_bad) {
+  if (!h) return SC_ERR_ARG;
+  unsigned long long* cnt = &h->hdr()->check_count;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->stream));
+  int rc = launch_check(h->P, h->cfg.precision, cnt, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "check launch");
+  ++h->launches;
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, cnt, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  unsigned bits = 0;
+  rc = read_err(h, &bits);
+  if (rc) return rc;
+  if (n_bad) *n_bad = (long long)v;
+  return err_status(h, bits);
+}
+
+int sc_lbm_debug_barrier(sc_lbm_t h, int never_arrive, long long spin_limit) {
+  if (!h || spin_limit < 1) return SC_ERR_ARG;
+  h->never_arrive = never_arrive ? 1 : 0;
+  h->spin_limit = spin_limit;
+  return SC_OK;
+}
+
+// Snapshot: header, then per domain the population arrays and outflow plane.
+struct SnapHeader {
+  uint64_t magic, version, cfg_hash, payload_hash, steps, bytes;
+};
+
+static uint64_t cfg_hash(sc_lbm_t h) {
+  uint64_t k = fnv1a(&h->cfg.precision, sizeof(int));
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    const DevDomain& D = h->P.dom[d];
+    int v[5] = {D.nx, D.ny, D.nz, D.nodes, 0};
+    k = fnv1a(v, sizeof v, k);
+  }
+  return k;
+}
+
+static size_t payload_bytes(sc_lbm_t h) {
+  size_t b = 0;
+  const size_t sb = storage_bytes(h->cfg.precision);
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    const DevDomain& D = h->P.dom[d];
+    b += sb * kQ * (size_t)D.ncell * D.nodes * (h->cfg.precision == SC_P_FP64_PLAIN ? 2 : 1);
+    if (D.bout) b += sizeof(float) * 5 * (size_t)D.nz * D.ny * D.nodes;
+  }
+  return b;
+}
+
+int sc_lbm_state_size(sc_lbm_t h, size_t* bytes) {
+  if (!h || !bytes) return SC_ERR_ARG;
+  *bytes = sizeof(SnapHeader) + payload_bytes(h);
+  return SC_OK;
+}
+
+int sc_lbm_save(sc_lbm_t h, void* host_buf, size_t bytes) {
+  if (!h || !host_buf) return SC_ERR_ARG;
+  const size_t need = sizeof(SnapHeader) + payload_bytes(h);
+  if (bytes < need) return SC_ERR_ARG;
+  char* out = (char*)host_buf + sizeof(SnapHeader);
+  const size_t sb = storage_bytes(h->cfg.precision);
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    const DevDomain& D = h->P.dom[d];
+    size_t n = sb * kQ * (size_t)D.ncell * D.nodes;
+    CK(cudaMemcpyAsync(out, D.g, n, cudaMemcpyDeviceToHost, h->stream));
+    out += n;
+    if (D.g2) {
+      CK(cudaMemcpyAsync(out, D.g2, n, cudaMemcpyDeviceToHost, h->stream));
+      out += n;
+    }
+    if (D.bout) {
+      size_t nb = sizeof(float) * 5 * (size_t)D.nz * D.ny * D.nodes;
+      CK(cudaMemcpyAsync(out, D.bout, nb, cudaMemcpyDeviceToHost, h->stream));
+      out += nb;
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  SnapHeader hd;
+  hd.magic = 0x53434C424D534E50ULL;
+  hd.version = 1;
+  hd.cfg_hash = cfg_hash(h);
+  hd.payload_hash = fnv1a((const char*)host_buf + sizeof(SnapHeader), need - sizeof(SnapHeader));
+  hd.steps = (uint64_t)h->steps;
+  hd.bytes = need;
+  memcpy(host_buf, &hd, sizeof hd);
+  return SC_OK;
+}
+
+int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < sizeof(SnapHeader)) return SC_ERR_ARG;
+  SnapHeader hd;
+  memcpy(&hd, host_buf, sizeof hd);
+  const size_t need = sizeof(SnapHeader) + payload_bytes(h);
+  if (hd.magic != 0x53434C424D534E50ULL || hd.version != 1 || hd.bytes != need || bytes < need)
+    return fail(h, SC_ERR_ARG, "not a snapshot of this configuration");
+  if (hd.cfg_hash != cfg_hash(h)) return fail(h, SC_ERR_ARG, "snapshot configuration differs");
+  if (hd.payload_hash != fnv1a((const char*)host_buf + sizeof(SnapHeader), need - sizeof(SnapHeader)))
+    return fail(h, SC_ERR_ARG, "snapshot checksum mismatch");
+  const char* in = (const char*)host_buf + sizeof(SnapHeader);
+  const size_t sb = storage_bytes(h->cfg.precision);
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    const DevDomain& D = h->P.dom[d];
+    size_t n = sb * kQ * (size_t)D.ncell * D.nodes;
+    CK(cudaMemcpyAsync(D.g, in, n, cudaMemcpyHostToDevice, h->stream));
+    in += n;
+    if (D.g2) {
+      CK(cudaMemcpyAsync(D.g2, in, n, cudaMemcpyHostToDevice, h->stream));
+      in += n;
+    }
+    if (D.bout) {
+      size_t nb = sizeof(float) * 5 * (size_t)D.nz * D.ny * D.nodes;
+      CK(cudaMemcpyAsync(D.bout, in, nb, cudaMemcpyHostToDevice, h->stream));
+      in += nb;
+    }
+  }
+  int rc = launch_set_counter(&h->hdr()->step, hd.steps, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "set counter");
+  ++h->launches;
+  CK(cudaStreamSynchronize(h->stream));
+  h->steps = (long long)hd.steps;
+  return SC_OK;
+}
+
+const char* sc_lbm_last_error(sc_lbm_t h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+int sc_lbm_destroy(sc_lbm_t h) {
+  if (!h) return SC_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  delete h;
+  return SC_OK;
+}
+
+}  // extern "C"

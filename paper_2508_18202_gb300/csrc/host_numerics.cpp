@@ -1,0 +1,391 @@
+// host_numerics.cpp -- host-side numerics of libsclbm: quadrature rules,
+// seeded geometry and probes, boundary link classification, inflow tables and
+// the gPC basis.  Compiled with -ffp-contract=off so that the quadrature
+// nodes and weights are the same bits on every host.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sclbm_internal.h"
+
+namespace sclbm {
+namespace {
+
+// D3Q19 velocities (rest, axis pairs, face-diagonal pairs), Sec. 2.2 Fig. 1.
+const int kCx[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+const int kCy[kQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+const int kCz[kQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014).
+struct Rng {
+  uint64_t state;
+  uint64_t next() {
+    state += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  int draw(int lo, int hi) {  // U{lo..hi}
+    uint64_t span = (uint64_t)(hi - lo + 1);
+    return lo + (int)(next() % span);
+  }
+};
+
+// 1-D Gauss-Legendre on [-1, 1] (weights sum 2), n <= 5, closed forms.
+bool gl_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.clear();
+  w.clear();
+  switch (n) {
+    case 1:
+      x = {0.0};
+      w = {2.0};
+      return true;
+    case 2: {
+      double r = 1.0 / sqrt(3.0);
+      x = {-r, r};
+      w = {1.0, 1.0};
+      return true;
+    }
+    case 3: {
+      double r = sqrt(3.0 / 5.0);
+      x = {-r, 0.0, r};
+      w = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+      return true;
+    }
+    case 4: {
+      double inner = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+      double outer = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+      double w_in = (18.0 + sqrt(30.0)) / 36.0;
+      double w_out = (18.0 - sqrt(30.0)) / 36.0;
+      x = {-outer, -inner, inner, outer};
+      w = {w_out, w_in, w_in, w_out};
+      return true;
+    }
+    case 5: {
+      double inner = sqrt(5.0 - 2.0 * sqrt(10.0 / 7.0)) / 3.0;
+      double outer = sqrt(5.0 + 2.0 * sqrt(10.0 / 7.0)) / 3.0;
+      double w_in = (322.0 + 13.0 * sqrt(70.0)) / 900.0;
+      double w_out = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
+      x = {-outer, -inner, 0.0, inner, outer};
+      w = {w_out, w_in, 128.0 / 225.0, w_in, w_out};
+      return true;
+    }
+    default:
+      return false;
+  }
+}
+
+int cc_size(int level) { return level <= 1 ? 1 : (1 << (level - 1)) + 1; }
+
+// 1-D Clenshaw-Curtis rule of `level` on [-1, 1], weights summing to 2:
+// nodes -cos(k pi / n) with exact 0, +-1 and mirror pairs; weights
+// (c_k / n) (1 - sum_{j=1}^{n/2} b_j cos(2 j k pi / n) / (4 j^2 - 1)).
+void cc_rule(int level, std::vector<double>& x, std::vector<double>& w) {
+  const int m = cc_size(level);
+  x.assign(m, 0.0);
+  w.assign(m, 0.0);
+  if (m == 1) {
+    w[0] = 2.0;
+    return;
+  }
+  const int n = m - 1;
+  for (int k = 0; k <= n; ++k) x[k] = -cos((double)k * M_PI / (double)n);
+  for (int k = 0; 2 * k < n; ++k) x[n - k] = -x[k];
+  x[0] = -1.0;
+  x[n] = 1.0;
+  if ((n & 1) == 0) x[n / 2] = 0.0;
+  for (int k = 0; k <= n; ++k) {
+    double acc = 0.0;
+    for (int j = 1; j <= n / 2; ++j) {
+      double bj = (2 * j == n) ? 1.0 : 2.0;
+      double cj = cos((double)(2 * j * k) * M_PI / (double)n);
+      acc += bj / (double)(4 * j * j - 1) * cj;
+    }
+    double ck = (k == 0 || k == n) ? 1.0 : 2.0;
+    w[k] = ck / (double)n * (1.0 - acc);
+  }
+}
+
+long long choose(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  long long r = 1;
+  for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+  return r;
+}
+
+// Accumulator keyed by the finest-grid integer index, filled in enumeration
+// order (so each node's weight is summed in the order of contributions).
+struct NodeAcc {
+  int d;
+  std::vector<int> keys;       // [count][d]
+  std::vector<double> weight;  // [count]
+  void add(const int* key, double v) {
+    const int count = (int)weight.size();
+    for (int e = 0; e < count; ++e) {
+      if (std::equal(key, key + d, keys.begin() + (size_t)e * d)) {
+        weight[e] += v;
+        return;
+      }
+    }
+    keys.insert(keys.end(), key, key + d);
+    weight.push_back(0.0 + v);
+  }
+};
+
+}  // namespace
+
+int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi,
+                  std::vector<double>& Z, std::vector<double>& w) {
+  if (d < 1 || d > 3 || level < 1) return SC_ERR_ARG;
+  NodeAcc acc{d, {}, {}};
+  std::vector<double> fine_x;
+  if (rule == SC_Q_GL) {
+    std::vector<double> x1, w1;
+    if (!gl_rule(level, x1, w1)) return SC_ERR_ARG;
+    fine_x = x1;
+    std::vector<double> pw(level);
+    for (int k = 0; k < level; ++k) pw[k] = w1[k] * 0.5;
+    int total = 1;
+    for (int t = 0; t < d; ++t) total *= level;
+    for (int flat = 0; flat < total; ++flat) {
+      int key[3];
+      int rem = flat;
+      for (int t = d - 1; t >= 0; --t) {
+        key[t] = rem % level;
+        rem /= level;
+      }
+      double prod = 1.0;
+      for (int t = 0; t < d; ++t) prod *= pw[key[t]];
+      acc.add(key, prod);
+    }
+  } else if (rule == SC_Q_CC_SMOLYAK) {
+    if (level > 12) return SC_ERR_ARG;
+    std::vector<double> wf;
+    cc_rule(level, fine_x, wf);
+    const int mfine = cc_size(level);
+    std::vector<std::vector<double>> wl(level + 1);
+    for (int l = 1; l <= level; ++l) {
+      std::vector<double> xl;
+      cc_rule(l, xl, wl[l]);
+      for (double& v : wl[l]) v = v * 0.5;
+    }
+    // multi-indices i in {1..level}^d, i_1 most significant
+    int total = 1;
+    for (int t = 0; t < d; ++t) total *= level;
+    for (int flat = 0; flat < total; ++flat) {
+      int lv[3];
+      int rem = flat;
+      for (int t = d - 1; t >= 0; --t) {
+        lv[t] = rem % level + 1;
+        rem /= level;
+      }
+      int sum = 0;
+      for (int t = 0; t < d; ++t) sum += lv[t];
+      if (sum < level || sum > level + d - 1) continue;
+      const int e = level + d - 1 - sum;
+      const long long coef = (e & 1 ? -1 : 1) * choose(d - 1, e);
+      int cnt = 1;
+      for (int t = 0; t < d; ++t) cnt *= cc_size(lv[t]);
+      for (int g = 0; g < cnt; ++g) {
+        int k[3], key[3];
+        int r2 = g;
+        for (int t = d - 1; t >= 0; --t) {
+          k[t] = r2 % cc_size(lv[t]);
+          r2 /= cc_size(lv[t]);
+        }
+        double prod = (double)coef;
+        for (int t = 0; t < d; ++t) {
+          const int m = cc_size(lv[t]);
+          prod *= wl[lv[t]][k[t]];
+          key[t] = (m == 1) ? (mfine - 1) / 2 : k[t] * ((mfine - 1) / (m - 1));
+        }
+        acc.add(key, prod);
+      }
+    }
+  } else {
+    return SC_ERR_ARG;
+  }
+  const int count = (int)acc.weight.size();
+  std::vector<int> order(count);
+  for (int e = 0; e < count; ++e) order[e] = e;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return std::lexicographical_compare(acc.keys.begin() + (size_t)a * d,
+                                        acc.keys.begin() + (size_t)a * d + d,
+                                        acc.keys.begin() + (size_t)b * d,
+                                        acc.keys.begin() + (size_t)b * d + d);
+  });
+  Z.assign((size_t)count * d, 0.0);
+  w.assign(count, 0.0);
+  for (int r = 0; r < count; ++r) {
+    const int e = order[r];
+    for (int t = 0; t < d; ++t) {
+      double x = fine_x[acc.keys[(size_t)e * d + t]];
+      Z[(size_t)r * d + t] = 0.5 * (lo[t] + hi[t]) + 0.5 * (hi[t] - lo[t]) * x;
+    }
+    w[r] = acc.weight[e];
+  }
+  return SC_OK;
+}
+
+int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags) {
+  const long long n = (long long)D.nx * D.ny * D.nz;
+  flags.assign((size_t)n, 0);
+  auto box = [&](int x0, int y0, int z0, int x1, int y1, int z1) {
+    x0 = std::max(x0, 0);
+    y0 = std::max(y0, 0);
+    z0 = std::max(z0, 0);
+    x1 = std::min(x1, D.nx);
+    y1 = std::min(y1, D.ny);
+    z1 = std::min(z1, D.nz);
+    for (int z = z0; z < z1; ++z)
+      for (int y = y0; y < y1; ++y) {
+        uint8_t* row = flags.data() + (size_t)D.nx * ((size_t)y + (size_t)D.ny * z);
+        for (int x = x0; x < x1; ++x) row[x] = 1;
+      }
+  };
+  if (D.n_boxes > 0) {
+    if (!D.boxes) return SC_ERR_ARG;
+    for (int b = 0; b < D.n_boxes; ++b) {
+      const int32_t* B = D.boxes + 6 * b;
+      box(B[0], B[1], B[2], B[3], B[4], B[5]);
+    }
+    return SC_OK;
+  }
+  Rng rng{D.geom_seed};
+  const int hcap = std::min(D.h_max, D.nz - 4);
+  for (int b = 0; b < D.n_buildings; ++b) {
+    if (D.fp_max < D.fp_min || hcap < D.h_min) return SC_ERR_ARG;
+    const int wx = rng.draw(D.fp_min, D.fp_max);
+    const int wy = rng.draw(D.fp_min, D.fp_max);
+    const int h = rng.draw(D.h_min, hcap);
+    const int xlo = D.nx / 8, xhi = D.nx - D.nx / 8 - wx;
+    const int ylo = 2, yhi = D.ny - 2 - wy;
+    if (xhi < xlo || yhi < ylo) return SC_ERR_ARG;
+    const int x0 = rng.draw(xlo, xhi);
+    const int y0 = rng.draw(ylo, yhi);
+    box(x0, y0, 0, x0 + wx, y0 + wy, h);
+  }
+  return SC_OK;
+}
+
+int hn_probe_columns(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xy) {
+  Rng rng{D.geom_seed + 1ULL};
+  int have = 0;
+  long long attempts = 0;
+  while (have < n) {
+    if (++attempts > 1000000) return SC_ERR_ARG;
+    const int x = rng.draw(D.nx / 8, D.nx - 1);
+    const int y = rng.draw(0, D.ny - 1);
+    if (flags[(size_t)x + (size_t)D.nx * y]) continue;
+    bool seen = false;
+    for (int k = 0; k < have && !seen; ++k) seen = xy[2 * k] == x && xy[2 * k + 1] == y;
+    if (seen) continue;
+    xy[2 * have] = x;
+    xy[2 * have + 1] = y;
+    ++have;
+  }
+  return SC_OK;
+}
+
+int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xyz) {
+  Rng rng{D.geom_seed + 1ULL};
+  int have = 0;
+  long long attempts = 0;
+  while (have < n) {
+    if (++attempts > 1000000) return SC_ERR_ARG;
+    const int x = rng.draw(D.nx / 8, D.nx - 1);
+    const int y = rng.draw(0, D.ny - 1);
+    const int z = rng.draw(0, D.nz - 3);
+    if (flags[(size_t)x + (size_t)D.nx * ((size_t)y + (size_t)D.ny * z)]) continue;
+    bool seen = false;
+    for (int k = 0; k < have && !seen; ++k)
+      seen = xyz[3 * k] == x && xyz[3 * k + 1] == y && xyz[3 * k + 2] == z;
+    if (seen) continue;
+    xyz[3 * have] = x;
+    xyz[3 * have + 1] = y;
+    xyz[3 * have + 2] = z;
+    ++have;
+  }
+  return SC_OK;
+}
+
+void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<uint32_t>& link) {
+  const long long n = (long long)D.nx * D.ny * D.nz;
+  link.assign((size_t)n, 0u);
+  const int dims[3] = {D.nx, D.ny, D.nz};
+  for (int z = 0; z < D.nz; ++z)
+    for (int y = 0; y < D.ny; ++y)
+      for (int x = 0; x < D.nx; ++x) {
+        const size_t c = (size_t)x + (size_t)D.nx * ((size_t)y + (size_t)D.ny * z);
+        uint32_t word = 0;
+        if (flags[c]) {
+          link[c] = kLinkSolid;
+          continue;
+        }
+        for (int i = 0; i < kQ; ++i) {
+          const int p[3] = {x - kCx[i], y - kCy[i], z - kCz[i]};
+          bool special = false;
+          for (int a = 0; a < 3; ++a)
+            if (p[a] < 0 || p[a] >= dims[a]) special = true;
+          if (!special) special = flags[(size_t)p[0] + (size_t)D.nx * ((size_t)p[1] + (size_t)D.ny * p[2])] != 0;
+          if (special) word |= 1u << i;
+        }
+        if (x == D.nx - 1 && D.bc[1] == SC_BC_OUTFLOW) word |= kLinkOutlet;
+        link[c] = word;
+      }
+}
+
+void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
+               double* uin) {
+  const double theta = theta_deg * M_PI / 180.0;
+  const double c = cos(theta), s = sin(theta);
+  for (int k = 0; k < nz; ++k) {
+    const double speed = u_ref * (1.0 + xi) * pow(((double)k + 0.5) / H, alpha);
+    uin[3 * k + 0] = speed * c;
+    uin[3 * k + 1] = speed * s;
+    uin[3 * k + 2] = 0.0;
+  }
+}
+
+double hn_ramp(int ramp_steps, long long m) {
+  if (ramp_steps <= 0) return 1.0;
+  const long long mm = m < ramp_steps ? m : ramp_steps;
+  return 0.5 * (1.0 - cos(M_PI * (double)mm / (double)ramp_steps));
+}
+
+int hn_gpc_size(int d, int degree) {
+  if (degree < 0) return 0;
+  return (int)choose(degree + d, d);
+}
+
+// Orthonormal Legendre products on [-1, 1]^d, graded order: total degree
+// ascending; within a degree the exponent of the first input descending, then
+// of the second, ...
+void hn_gpc_basis(int d, int degree, const double* s, double* phi) {
+  double leg[3][16];
+  for (int t = 0; t < d; ++t) {
+    leg[t][0] = 1.0;
+    if (degree >= 1) leg[t][1] = s[t];
+    for (int n = 1; n < degree; ++n)
+      leg[t][n + 1] = ((2 * n + 1) * s[t] * leg[t][n] - n * leg[t][n - 1]) / (double)(n + 1);
+    for (int n = 0; n <= degree; ++n) leg[t][n] *= sqrt(2.0 * n + 1.0);
+  }
+  int out = 0;
+  for (int tot = 0; tot <= degree; ++tot) {
+    if (d == 1) {
+      phi[out++] = leg[0][tot];
+    } else if (d == 2) {
+      for (int a0 = tot; a0 >= 0; --a0) phi[out++] = leg[0][a0] * leg[1][tot - a0];
+    } else {
+      for (int a0 = tot; a0 >= 0; --a0)
+        for (int a1 = tot - a0; a1 >= 0; --a1)
+          phi[out++] = leg[0][a0] * leg[1][a1] * leg[2][tot - a0 - a1];
+    }
+  }
+}
+
+}  // namespace sclbm

@@ -1,0 +1,979 @@
+// lbm_kernels.cu -- CUDA kernels of libsclbm for sm_103a (GB300).
+//
+// Stream-collide of the D3Q19 lattice Boltzmann equation (arXiv:2508.18202
+// Sec. 2.2, Eq. deterministicLBE) with BGK collision and the Smagorinsky
+// effective relaxation time (Eqs. tauEff, turbVisc), for every collocation
+// node of every domain of an ensemble, plus the quadrature / gPC reductions
+// of Sec. 2.3 (Eqs. quad_moments, coef_discrete).
+//
+// Layout (structure of arrays, x fastest): population i of node j of a
+// domain lives at g[(j*19 + i)*ncell + c], c = x + nx*(y + ny*z).  The
+// in-place precisions store g_i = f_i - w_i (the shift keeps the FP32/BF16/
+// FP16 mantissa for the deviation from rest) and advance with the AA access
+// pattern: at an even time level a cell reads its own 19 slots and writes
+// the post-collision values back to the opposite slots of the same cell; at
+// an odd level it pulls f_i from slot opp(i) of the upstream neighbour
+// x - c_i and pushes f*_i into slot i of the downstream neighbour x + c_i.
+// Every slot is then read and written by exactly one thread per step, so one
+// array suffices (152 B per fluid cell update in FP32).
+//
+// Boundary links (bit i of the cell's link word) take a slow path that
+// applies the same per-link rules as the pull formulation:
+//   source inside and solid            -> bounce-back
+//   one face crossed: BOUNCE_BACK      -> bounce-back
+//                     VELOCITY         -> bounce-back + 6 w_i (c_i . u_in(z)) r(t)
+//                     FREE_SLIP        -> specular reflection from the in-plane
+//                                         neighbour (bounce-back if it is solid)
+//                     OUTFLOW (+x)     -> copy of f*_i from the transverse
+//                                         neighbour on the outlet plane (own
+//                                         value if that cell is solid)
+//   two faces crossed: any wall        -> bounce-back; else any inflow ->
+//                                         moving wall; else the cell's own f*
+//                                         reflected across each free-slip face.
+// The outflow copy reads a neighbour's post-collision value that the AA
+// odd step overwrites in place, so even steps also save the five f*_i with
+// c_ix = -1 of every outlet cell into a small per-node plane (bout) that the
+// odd step reads.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "sclbm_internal.h"
+
+namespace sclbm {
+namespace {
+
+// ------------------------------------------------------------ lattice
+__host__ __device__ constexpr int CX(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int CY(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int CZ(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr int C2(int i) { return CX(i) * CX(i) + CY(i) * CY(i) + CZ(i) * CZ(i); }
+template <class T>
+__host__ __device__ constexpr T W(int i) {
+  return C2(i) == 0 ? T(1.0 / 3.0) : (C2(i) == 1 ? T(1.0 / 18.0) : T(1.0 / 36.0));
+}
+// slot in the outflow plane of the five directions with c_x = -1
+__host__ __device__ constexpr int KOUT(int i) {
+  return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1;
+}
+__device__ __forceinline__ int comp(int i, int a) { return a == 0 ? CX(i) : (a == 1 ? CY(i) : CZ(i)); }
+__device__ __forceinline__ int find_dir(int x, int y, int z) {
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    if (CX(i) == x && CY(i) == y && CZ(i) == z) return i;
+  return 0;
+}
+__device__ __forceinline__ int refl(int i, int a) {
+  int c[3] = {CX(i), CY(i), CZ(i)};
+  c[a] = -c[a];
+  return find_dir(c[0], c[1], c[2]);
+}
+
+// ------------------------------------------------------------ storage
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldcg(p));
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<__half> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<double> {
+  using C = double;
+  static __device__ __forceinline__ double ld(const double* p) { return *p; }
+  static __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+
+template <class S, bool CG>
+__device__ __forceinline__ typename Store<S>::C LD(const S* p) {
+  if constexpr (CG) return Store<S>::ldcg(p);
+  else return Store<S>::ld(p);
+}
+
+// ------------------------------------------------------------ collision
+// BGK with the Smagorinsky effective relaxation time (Sec. 2.2).  SHIFT:
+// populations are g = f - w.  The non-equilibrium stress uses the exact
+// second moment of the D3Q19 second-order equilibrium, rho/3 I + rho u u.
+template <class T, bool SHIFT>
+__device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_on) {
+  T m0 = T(0), jx = T(0), jy = T(0), jz = T(0);
+  T pxx = T(0), pyy = T(0), pzz = T(0), pxy = T(0), pxz = T(0), pyz = T(0);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    m0 += g[i];
+    if (CX(i)) jx += CX(i) > 0 ? g[i] : -g[i];
+    if (CY(i)) jy += CY(i) > 0 ? g[i] : -g[i];
+    if (CZ(i)) jz += CZ(i) > 0 ? g[i] : -g[i];
+    if (CX(i)) pxx += g[i];
+    if (CY(i)) pyy += g[i];
+    if (CZ(i)) pzz += g[i];
+    if (CX(i) * CY(i)) pxy += CX(i) * CY(i) > 0 ? g[i] : -g[i];
+    if (CX(i) * CZ(i)) pxz += CX(i) * CZ(i) > 0 ? g[i] : -g[i];
+    if (CY(i) * CZ(i)) pyz += CY(i) * CZ(i) > 0 ? g[i] : -g[i];
+  }
+  const T rho = SHIFT ? T(1) + m0 : m0;
+  const T inv = T(1) / rho;
+  const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const T usq = ux * ux + uy * uy + uz * uz;
+  T tau = tau0;
+  if (smag_on) {
+    // Pi^neq = sum c c g - (m0/3 I + rho u u); m0 = rho - 1 (shifted) or rho
+    const T third = m0 * T(1.0 / 3.0);
+    const T nxx = pxx - third - rho * ux * ux;
+    const T nyy = pyy - third - rho * uy * uy;
+    const T nzz = pzz - third - rho * uz * uz;
+    const T nxy = pxy - rho * ux * uy;
+    const T nxz = pxz - rho * ux * uz;
+    const T nyz = pyz - rho * uy * uz;
+    const T pipi = nxx * nxx + nyy * nyy + nzz * nzz + T(2) * (nxy * nxy + nxz * nxz + nyz * nyz);
+    const T pin = sqrt(T(2) * pipi + T(1e-30));
+    tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + smag18c2 * pin * inv));
+  }
+  const T omega = T(1) / tau;
+  const T base = m0;  // shifted: w (rho - 1) part; plain: w rho part
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const T cu = T(CX(i)) * ux + T(CY(i)) * uy + T(CZ(i)) * uz;
+    const T geq = W<T>(i) * (base + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+    g[i] = g[i] - omega * (g[i] - geq);
+  }
+}
+
+// ------------------------------------------------------------ boundary helpers
+struct Cross {
+  int n;        // faces crossed (0, 1, 2)
+  int f[2];     // face ids
+  int p[3];     // position with periodic axes wrapped
+};
+
+__device__ __forceinline__ Cross classify(const DevDomain& D, int px, int py, int pz) {
+  Cross c;
+  c.n = 0;
+  c.f[0] = c.f[1] = -1;
+  int p[3] = {px, py, pz};
+  const int n[3] = {D.nx, D.ny, D.nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (D.bc[2 * a] == SC_BC_PERIODIC) {
+      if (p[a] < 0) p[a] += n[a];
+      else if (p[a] >= n[a]) p[a] -= n[a];
+    } else if (p[a] < 0) {
+      c.f[c.n < 2 ? c.n : 1] = 2 * a;
+      ++c.n;
+    } else if (p[a] >= n[a]) {
+      c.f[c.n < 2 ? c.n : 1] = 2 * a + 1;
+      ++c.n;
+    }
+  }
+  c.p[0] = p[0];
+  c.p[1] = p[1];
+  c.p[2] = p[2];
+  return c;
+}
+
+__device__ __forceinline__ long long cidx(const DevDomain& D, int x, int y, int z) {
+  return (long long)x + (long long)D.nx * ((long long)y + (long long)D.ny * z);
+}
+
+template <class T>
+__device__ __forceinline__ T ladd(int i, float4 u, T r) {
+  // 6 w_i rho_w (c_i . u_w) r, rho_w = 1
+  const T cu = T(CX(i)) * T(u.x) + T(CY(i)) * T(u.y) + T(CZ(i)) * T(u.z);
+  return T(6) * W<T>(i) * cu * r;
+}
+template <class T>
+__device__ __forceinline__ T ladd_d(int i, const double* u, T r) {
+  const T cu = T(CX(i)) * T(u[0]) + T(CY(i)) * T(u[1]) + T(CZ(i)) * T(u[2]);
+  return T(6) * W<T>(i) * cu * r;
+}
+
+// Per-node pointers.
+template <class S>
+struct Node {
+  S* g;                // [19][ncell]
+  float* bout;         // [nz*ny][5]
+  const float4* uinf;  // [nz]
+  const double* uind;  // [nz][3]
+};
+
+// Inflow correction of direction i at layer z.
+template <class S, class T>
+__device__ __forceinline__ T vel_term(const Node<S>& N, int i, int z, T r) {
+  if constexpr (sizeof(T) == 8) return ladd_d<T>(i, N.uind + 3 * z, r);
+  else return ladd<T>(i, N.uinf[z], r);
+}
+
+// f_i of time level n (odd, AA swapped layout) for a boundary link.
+template <class S, bool CG>
+__device__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
+                                             int y, int z, long long idx,
+                                             typename Store<S>::C r) {
+  using T = typename Store<S>::C;
+  const long long nc = D.ncell;
+  const Cross c = classify(D, x - CX(i), y - CY(i), z - CZ(i));
+  const T own = LD<S, CG>(N.g + (long long)i * nc + idx);  // f*_opp(i)(x)
+  if (c.n == 0) {
+    const long long p = cidx(D, c.p[0], c.p[1], c.p[2]);
+    if (D.flags[p] == 0) return LD<S, CG>(N.g + (long long)OPP(i) * nc + p);
+    return own;
+  }
+  if (c.n == 1) {
+    const int kind = D.bc[c.f[0]];
+    if (kind == SC_BC_BOUNCE_BACK) return own;
+    if (kind == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
+    const int a = c.f[0] >> 1;
+    int s[3] = {x - CX(i), y - CY(i), z - CZ(i)};
+    s[a] = a == 0 ? x : (a == 1 ? y : z);
+    const Cross cs = classify(D, s[0], s[1], s[2]);
+    const long long sp = cidx(D, cs.p[0], cs.p[1], cs.p[2]);
+    if (kind == SC_BC_FREE_SLIP) {
+      if (D.flags[sp] == 0) return LD<S, CG>(N.g + (long long)OPP(refl(i, a)) * nc + sp);
+      return own;
+    }
+    // OUTFLOW on +x: transverse source on the outlet plane
+    if (D.flags[sp] == 0)
+      return T(__ldcg(N.bout + ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + KOUT(i)));
+    return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + KOUT(i)));
+  }
+  const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
+  if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) return own;
+  if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
+  if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) return own;
+  // outflow + free slip: own population reflected across the free-slip face
+  const int fs = (k0 == SC_BC_FREE_SLIP) ? c.f[0] : c.f[1];
+  return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + KOUT(refl(i, fs >> 1))));
+}
+
+// Deliver f*_j of cell x for a boundary link into dst (AA: dst == src array).
+template <class S>
+__device__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
+                             typename Store<S>::C v, int x, int y, int z, long long idx,
+                             typename Store<S>::C r1) {
+  using T = typename Store<S>::C;
+  const long long nc = D.ncell;
+  const Cross c = classify(D, x + CX(j), y + CY(j), z + CZ(j));
+  S* own = dst + (long long)OPP(j) * nc + idx;
+  if (c.n == 0) {
+    const long long q = cidx(D, c.p[0], c.p[1], c.p[2]);
+    if (D.flags[q] == 0) Store<S>::st(dst + (long long)j * nc + q, v);
+    else Store<S>::st(own, v);
+    return;
+  }
+  if (c.n == 1) {
+    const int kind = D.bc[c.f[0]];
+    if (kind == SC_BC_BOUNCE_BACK) {
+      Store<S>::st(own, v);
+    } else if (kind == SC_BC_VELOCITY) {
+      Store<S>::st(own, v + vel_term<S, T>(N, OPP(j), z, r1));
+    } else if (kind == SC_BC_FREE_SLIP) {
+      const int a = c.f[0] >> 1;
+      int t[3] = {x + CX(j), y + CY(j), z + CZ(j)};
+      t[a] = a == 0 ? x : (a == 1 ? y : z);
+      const Cross ct = classify(D, t[0], t[1], t[2]);
+      const long long tp = cidx(D, ct.p[0], ct.p[1], ct.p[2]);
+      if (D.flags[tp] == 0) Store<S>::st(dst + (long long)refl(j, a) * nc + tp, v);
+      else Store<S>::st(own, v);
+    }
+    // OUTFLOW: the population leaves the domain
+    return;
+  }
+  const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
+  if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) {
+    Store<S>::st(own, v);
+  } else if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) {
+    Store<S>::st(own, v + vel_term<S, T>(N, OPP(j), z, r1));
+  } else if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) {
+    Store<S>::st(own, v);
+  }
+  // outflow + free slip: delivered by the outlet pushes of the reflected direction
+}
+
+// Outlet cell (x = nx-1, +x OUTFLOW): deliver f*_j (c_jx = -1) to the outlet
+// links that read it.
+template <class S>
+__device__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x,
+                            int y, int z, long long idx) {
+  const long long nc = D.ncell;
+  // (1) transverse neighbour on the outlet plane copies it
+  {
+    const Cross c = classify(D, x, y + CY(j), z + CZ(j));
+    if (c.n == 0) {
+      const long long t = cidx(D, c.p[0], c.p[1], c.p[2]);
+      if (D.flags[t] == 0) Store<S>::st(dst + (long long)j * nc + t, v);
+    }
+  }
+  // (2) own link j whose transverse source is solid falls back to own value
+  {
+    const Cross c = classify(D, x, y - CY(j), z - CZ(j));
+    if (c.n == 0 && D.flags[cidx(D, c.p[0], c.p[1], c.p[2])] != 0)
+      Store<S>::st(dst + (long long)j * nc + idx, v);
+  }
+  // (3) outflow + free-slip edge: reflected copy into the own cell
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    const int cj = comp(j, a);
+    if (cj == 0) continue;
+    const int face = 2 * a + (cj > 0 ? 1 : 0);
+    const int pos = (a == 1 ? y : z) + cj;
+    const int lim = a == 1 ? D.ny : D.nz;
+    if (D.bc[face] == SC_BC_FREE_SLIP && (pos < 0 || pos >= lim))
+      Store<S>::st(dst + (long long)refl(j, a) * nc + idx, v);
+  }
+}
+
+// ------------------------------------------------------------ per-cell updates
+template <class S, bool CG, bool SHIFT>
+__device__ __forceinline__ void load_odd(const DevDomain& D, const Node<S>& N, uint32_t lw, int x,
+                                         int y, int z, long long idx,
+                                         typename Store<S>::C g[kQ], typename Store<S>::C r) {
+  const long long nc = D.ncell;
+  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    if (!(lw & (1u << i))) {
+      const long long off = CX(i) * sx + CY(i) * sy + CZ(i) * sz;
+      g[i] = LD<S, CG>(N.g + (long long)OPP(i) * nc + idx - off);
+    } else {
+      g[i] = pull_special<S, CG>(D, N, i, x, y, z, idx, r);
+    }
+  }
+}
+
+template <class S, bool CG, bool SHIFT>
+__device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& D,
+                                          const Node<S>& N, uint32_t lw, int y, int z,
+                                          long long idx) {
+  using T = typename Store<S>::C;
+  const long long nc = D.ncell;
+  T g[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(N.g + (long long)i * nc + idx);
+  if constexpr (sizeof(T) == 8)
+    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
+  else
+    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) Store<S>::st(N.g + (long long)OPP(i) * nc + idx, g[i]);
+  if (lw & kLinkOutlet) {
+    float* b = N.bout + ((long long)z * D.ny + y) * 5;
+    b[0] = float(g[2]);
+    b[1] = float(g[8]);
+    b[2] = float(g[10]);
+    b[3] = float(g[12]);
+    b[4] = float(g[14]);
+  }
+}
+
+template <class S, bool CG, bool SHIFT>
+__device__ __forceinline__ void cell_odd(const StepParams& P, const DevDomain& D,
+                                         const Node<S>& N, uint32_t lw, int x, int y, int z,
+                                         long long idx, typename Store<S>::C r,
+                                         typename Store<S>::C r1) {
+  using T = typename Store<S>::C;
+  const long long nc = D.ncell;
+  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
+  T g[kQ];
+  load_odd<S, CG, SHIFT>(D, N, lw, x, y, z, idx, g, r);
+  if constexpr (sizeof(T) == 8)
+    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
+  else
+    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    if (!(lw & (1u << OPP(j)))) {
+      const long long off = CX(j) * sx + CY(j) * sy + CZ(j) * sz;
+      Store<S>::st(N.g + (long long)j * nc + idx + off, g[j]);
+    } else {
+      push_special<S>(D, N, N.g, j, g[j], x, y, z, idx, r1);
+    }
+  }
+  if (lw & kLinkOutlet) {
+    push_outlet<S>(D, N.g, 2, g[2], x, y, z, idx);
+    push_outlet<S>(D, N.g, 8, g[8], x, y, z, idx);
+    push_outlet<S>(D, N.g, 10, g[10], x, y, z, idx);
+    push_outlet<S>(D, N.g, 12, g[12], x, y, z, idx);
+    push_outlet<S>(D, N.g, 14, g[14], x, y, z, idx);
+  }
+}
+
+// ------------------------------------------------------------ step driver
+__device__ __forceinline__ int find_domain(const StepParams& P, long long t) {
+  int d = 0;
+  for (int k = 1; k < P.n_domains; ++k)
+    if (t >= P.dom[k].tile_begin) d = k;
+  return d;
+}
+
+template <class S>
+__device__ __forceinline__ Node<S> node_view(const DevDomain& D, int node) {
+  Node<S> N;
+  N.g = reinterpret_cast<S*>(D.g) + (long long)node * kQ * D.ncell;
+  N.bout = D.bout ? D.bout + (long long)node * D.nz * D.ny * 5 : nullptr;
+  N.uinf = D.uin_f + (long long)node * D.nz;
+  N.uind = D.uin_d + (long long)node * D.nz * 3;
+  return N;
+}
+
+template <class S, bool CG>
+__device__ __forceinline__ void process_tile(const StepParams& P, long long t, unsigned long long n,
+                                             float r, float r1) {
+  using T = typename Store<S>::C;
+  const int d = find_domain(P, t);
+  const DevDomain& D = P.dom[d];
+  const long long local = t - D.tile_begin;
+  int node;
+  long long ct;
+  if (P.order == 0) {
+    node = (int)(local % D.nodes);
+    ct = local / D.nodes;
+  } else {
+    node = (int)(local / D.tiles_per_node);
+    ct = local % D.tiles_per_node;
+  }
+  const int tx = (int)(ct % D.tiles_x);
+  const int ty = (int)((ct / D.tiles_x) % D.tiles_y);
+  const int tz = (int)(ct / (D.tiles_x * D.tiles_y));
+  const int x = tx * P.bx + threadIdx.x;
+  const int y = ty * P.by + threadIdx.y;
+  if (x >= D.nx || y >= D.ny) return;
+  const Node<S> N = node_view<S>(D, node);
+  const int z0 = tz * P.bz;
+  const int z1 = min(z0 + P.bz, D.nz);
+  const bool odd = (n & 1ull) != 0;
+  for (int z = z0; z < z1; ++z) {
+    const long long idx = cidx(D, x, y, z);
+    const uint32_t lw = __ldg(D.link + idx);
+    if (lw & kLinkSolid) continue;
+    if (!odd) cell_even<S, CG, true>(P, D, N, lw, y, z, idx);
+    else cell_odd<S, CG, true>(P, D, N, lw, x, y, z, idx, T(r), T(r1));
+  }
+}
+
+__device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long m) {
+  const unsigned long long k = m < (unsigned long long)P.ramp_steps ? m : (unsigned long long)P.ramp_steps;
+  return P.ramp_f[k];
+}
+
+// One time step for every (domain, node, tile); the time level comes from
+// the device counter so that a captured graph replays without new
+// parameters.  The last block to finish advances the counter.
+template <class S>
+__global__ void aa_step_kernel(const __grid_constant__ StepParams P) {
+  __shared__ unsigned long long s_n;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_n = *reinterpret_cast<volatile unsigned long long*>(P.step);
+  __syncthreads();
+  const unsigned long long n = s_n;
+  process_tile<S, false>(P, blockIdx.x, n, ramp_at(P, n), ramp_at(P, n + 1));
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    const unsigned int ticket = atomicAdd(P.done, 1u);
+    if (ticket == gridDim.x - 1) {
+      *P.done = 0u;
+      *P.step = n + 1;
+      __threadfence();
+    }
+  }
+}
+
+// Bounded grid barrier (sense by generation).  Gives up after spin_limit
+// polls, latches kErrTimeout and returns false; every block then leaves.
+__device__ bool grid_barrier(const StepParams& P, unsigned int& gen) {
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    const unsigned int expected = gridDim.x + (P.never_arrive ? 1u : 0u);
+    const unsigned int arrived = atomicAdd(P.bar_count, 1u) + 1u;
+    if (arrived == expected) {
+      atomicExch(P.bar_count, 0u);
+      __threadfence();
+      atomicAdd(P.bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*reinterpret_cast<volatile unsigned int*>(P.bar_gen) == gen) {
+        if (*reinterpret_cast<volatile unsigned int*>(P.err) & kErrTimeout) { ok = false; break; }
+        if (++spins > P.spin_limit) {
+          atomicOr(P.err, kErrTimeout);
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    gen += 1u;
+    __threadfence();
+  }
+  __shared__ int s_ok;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_ok = ok ? 1 : 0;
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Persistent form: one cooperative launch advances n_steps; blocks stride over
+// the tiles and meet at a grid barrier between time steps.
+template <class S>
+__global__ void aa_persistent_kernel(const __grid_constant__ StepParams P) {
+  __shared__ unsigned long long s_n;
+  __shared__ unsigned int s_gen;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    s_n = *reinterpret_cast<volatile unsigned long long*>(P.step);
+    s_gen = *reinterpret_cast<volatile unsigned int*>(P.bar_gen);
+  }
+  __syncthreads();
+  unsigned long long n = s_n;
+  unsigned int gen = s_gen;
+  for (int s = 0; s < P.n_steps; ++s) {
+    const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
+    for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x)
+      process_tile<S, true>(P, t, n, r, r1);
+    if (!grid_barrier(P, gen)) return;
+    ++n;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *P.step = n;
+}
+
+// FP64 plain path: two arrays, push form, one node per launch.
+__global__ void plain_step_kernel(const __grid_constant__ StepParams P, unsigned long long n) {
+  const DevDomain& D = P.dom[P.plain_domain];
+  const long long ct = blockIdx.x;
+  const int tx = (int)(ct % D.tiles_x);
+  const int ty = (int)((ct / D.tiles_x) % D.tiles_y);
+  const int tz = (int)(ct / (D.tiles_x * D.tiles_y));
+  const int x = tx * P.bx + threadIdx.x;
+  const int y = ty * P.by + threadIdx.y;
+  if (x >= D.nx || y >= D.ny) return;
+  const int node = P.plain_node;
+  const long long nc = D.ncell;
+  double* A = reinterpret_cast<double*>(D.g) + (long long)node * kQ * nc;
+  double* B = reinterpret_cast<double*>(D.g2) + (long long)node * kQ * nc;
+  const double* src = (n & 1ull) ? B : A;
+  double* dst = (n & 1ull) ? A : B;
+  Node<double> N;
+  N.g = dst;
+  N.bout = nullptr;
+  N.uinf = nullptr;
+  N.uind = D.uin_d + (long long)node * D.nz * 3;
+  const unsigned long long m1 = n + 1;
+  const double r1 = P.ramp_d[m1 < (unsigned long long)P.ramp_steps ? m1 : P.ramp_steps];
+  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
+  const int z0 = tz * P.bz, z1 = min(z0 + P.bz, D.nz);
+  for (int z = z0; z < z1; ++z) {
+    const long long idx = cidx(D, x, y, z);
+    const uint32_t lw = __ldg(D.link + idx);
+    if (lw & kLinkSolid) continue;
+    double g[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
+    collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+      if (!(lw & (1u << OPP(j)))) {
+        const long long off = CX(j) * sx + CY(j) * sy + CZ(j) * sz;
+        dst[(long long)j * nc + idx + off] = g[j];
+      } else {
+        push_special<double>(D, N, dst, j, g[j], x, y, z, idx, r1);
+      }
+    }
+    if (lw & kLinkOutlet) {
+      push_outlet<double>(D, dst, 2, g[2], x, y, z, idx);
+      push_outlet<double>(D, dst, 8, g[8], x, y, z, idx);
+      push_outlet<double>(D, dst, 10, g[10], x, y, z, idx);
+      push_outlet<double>(D, dst, 12, g[12], x, y, z, idx);
+      push_outlet<double>(D, dst, 14, g[14], x, y, z, idx);
+    }
+  }
+}
+
+__global__ void set_counter_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// ------------------------------------------------------------ initialisation
+template <class S, bool SHIFT>
+__global__ void init_kernel(S* g, long long ncell, long long total) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)((k / ncell) % kQ);
+    using T = typename Store<S>::C;
+    T v = T(0);
+    if constexpr (!SHIFT) {
+      v = i == 0 ? T(1.0 / 3.0) : (i <= 6 ? T(1.0 / 18.0) : T(1.0 / 36.0));
+    }
+    Store<S>::st(g + k, v);
+  }
+}
+
+// ------------------------------------------------------------ observables
+// Populations f_i of time level n at a fluid cell (natural layout at even n,
+// pulled at odd n), unshifted, in the compute type.
+template <class S, bool SHIFT>
+__device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain& D, int node,
+                                            unsigned long long n, int x, int y, int z,
+                                            long long idx, uint32_t lw,
+                                            typename Store<S>::C g[kQ]) {
+  using T = typename Store<S>::C;
+  if constexpr (!SHIFT) {
+    // FP64 plain: two arrays, natural layout in the current one
+    const double* cur = reinterpret_cast<const double*>((n & 1ull) ? D.g2 : D.g) +
+                        (long long)node * kQ * D.ncell;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = T(cur[(long long)i * D.ncell + idx]);
+  } else {
+    const Node<S> N = node_view<S>(D, node);
+    if ((n & 1ull) == 0) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(N.g + (long long)i * D.ncell + idx);
+    } else {
+      load_odd<S, false, true>(D, N, lw, x, y, z, idx, g, T(ramp_at(P, n)));
+    }
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] += W<T>(i);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void macro(const T g[kQ], T& rho, T& ux, T& uy, T& uz) {
+  rho = T(0);
+  T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    rho += g[i];
+    jx += T(CX(i)) * g[i];
+    jy += T(CY(i)) * g[i];
+    jz += T(CZ(i)) * g[i];
+  }
+  ux = jx / rho;
+  uy = jy / rho;
+  uz = jz / rho;
+}
+
+__device__ __forceinline__ unsigned long long read_step(const StepParams& P) {
+  return *reinterpret_cast<volatile unsigned long long*>(P.step);
+}
+
+// Ensemble statistics of |u| per cell (Eq. quad_moments) and the gPC
+// projection (Eq. coef_discrete), FP64 accumulation over the nodes.
+template <class S, bool SHIFT>
+__global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs A) {
+  using T = typename Store<S>::C;
+  const DevDomain& D = P.dom[A.domain];
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (c < D.ncell) {
+    const unsigned long long n = read_step(P);
+    const int x = (int)(c % D.nx);
+    const int y = (int)((c / D.nx) % D.ny);
+    const int z = (int)(c / ((long long)D.nx * D.ny));
+    const uint32_t lw = __ldg(D.link + c);
+    double s1 = 0.0, s2 = 0.0;
+    double coef[kMaxGpcP];
+#pragma unroll
+    for (int a = 0; a < kMaxGpcP; ++a) coef[a] = 0.0;
+    if (!(lw & kLinkSolid)) {
+      for (int j = 0; j < A.nq; ++j) {
+        T g[kQ];
+        gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
+        T rho, ux, uy, uz;
+        macro<T>(g, rho, ux, uy, uz);
+        if (!(rho > T(0)) || !isfinite(double(ux + uy + uz)) || !isfinite(double(rho))) bad = true;
+        const double q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+        const double* ab = A.ab + (long long)j * A.stride;
+        const double aq = ab[0] * q;
+        s1 += aq;
+        s2 += aq * q;
+#pragma unroll
+        for (int a = 0; a < kMaxGpcP; ++a)
+          if (a < A.P) coef[a] += ab[1 + a] * q;
+      }
+    }
+    const double mean = s1 / A.wsum;
+    double var = s2 / A.wsum - mean * mean;
+    if (var < 0.0) var = 0.0;
+    A.mean[c] = mean;
+    A.stdev[c] = sqrt(var);
+    if (A.coef)
+      for (int a = 0; a < A.P; ++a) A.coef[(long long)a * D.ncell + c] = coef[a];
+  }
+  const unsigned any = __ballot_sync(0xffffffffu, bad);
+  if (any && (threadIdx.x & 31) == 0) atomicOr(P.err, kErrDiverged);
+}
+
+// Vertical profiles: one warp per (column, layer); lanes take nodes and the
+// FP64 sums are combined with warp shuffles.
+template <class S, bool SHIFT>
+__global__ void profiles_kernel(const __grid_constant__ StepParams P, MomentArgs A) {
+  using T = typename Store<S>::C;
+  const DevDomain& D = P.dom[A.domain];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= A.n_p * D.nz) return;
+  const int p = warp / D.nz;
+  const int z = warp % D.nz;
+  const int x = A.probes[2 * p], y = A.probes[2 * p + 1];
+  const long long c = cidx(D, x, y, z);
+  const uint32_t lw = __ldg(D.link + c);
+  const unsigned long long n = read_step(P);
+  double s1 = 0.0, s2 = 0.0;
+  for (int j = lane; j < A.nq; j += 32) {
+    double q = 0.0;
+    if (!(lw & kLinkSolid)) {
+      T g[kQ];
+      gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
+      T rho, ux, uy, uz;
+      macro<T>(g, rho, ux, uy, uz);
+      q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+    }
+    if (A.prof_nodes) A.prof_nodes[((long long)p * A.nq + j) * D.nz + z] = float(q);
+    const double a = A.ab[(long long)j * A.stride];
+    s1 += a * q;
+    s2 += a * q * q;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    const double mean = s1 / A.wsum;
+    double var = s2 / A.wsum - mean * mean;
+    if (var < 0.0) var = 0.0;
+    const double sd = sqrt(var);
+    double* out = A.prof + ((long long)p * D.nz + z) * 4;
+    out[0] = mean;
+    out[1] = sd;
+    out[2] = mean - 1.959963984540054 * sd;
+    out[3] = mean + 1.959963984540054 * sd;
+  }
+}
+
+// One node's populations (FP64, unshifted) and velocity at the current time.
+template <class S, bool SHIFT>
+__global__ void export_kernel(const __grid_constant__ StepParams P, int domain, int node,
+                              double* f, float* u) {
+  using T = typename Store<S>::C;
+  const DevDomain& D = P.dom[domain];
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= D.ncell) return;
+  const int x = (int)(c % D.nx);
+  const int y = (int)((c / D.nx) % D.ny);
+  const int z = (int)(c / ((long long)D.nx * D.ny));
+  const uint32_t lw = __ldg(D.link + c);
+  if (lw & kLinkSolid) {
+    if (f)
+      for (int i = 0; i < kQ; ++i) f[(long long)i * D.ncell + c] = 0.0;
+    if (u) u[c] = u[D.ncell + c] = u[2 * D.ncell + c] = 0.0f;
+    return;
+  }
+  T g[kQ];
+  gather_pops<S, SHIFT>(P, D, node, read_step(P), x, y, z, c, lw, g);
+  if (f)
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[(long long)i * D.ncell + c] = double(g[i]);
+  if (u) {
+    T rho, ux, uy, uz;
+    macro<T>(g, rho, ux, uy, uz);
+    u[c] = float(ux);
+    u[D.ncell + c] = float(uy);
+    u[2 * D.ncell + c] = float(uz);
+  }
+}
+
+// Count cells whose stored populations sum to a non-finite or non-positive
+// density (layout-independent: the stored 19 values of a cell always carry
+// its density at the current or previous time level).
+template <class S, bool SHIFT>
+__global__ void check_kernel(const __grid_constant__ StepParams P, unsigned long long* count) {
+  unsigned long long local = 0;
+  for (int d = 0; d < P.n_domains; ++d) {
+    const DevDomain& D = P.dom[d];
+    const long long total = D.ncell * D.nodes;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+      const long long c = k % D.ncell;
+      const int node = (int)(k / D.ncell);
+      if (__ldg(D.link + c) & kLinkSolid) continue;
+      const S* g = reinterpret_cast<const S*>(D.g) + (long long)node * kQ * D.ncell;
+      if constexpr (!SHIFT) {
+        if (read_step(P) & 1ull) g = reinterpret_cast<const S*>(D.g2) + (long long)node * kQ * D.ncell;
+      }
+      double rho = SHIFT ? 1.0 : 0.0;
+      for (int i = 0; i < kQ; ++i) rho += double(Store<S>::ld(g + (long long)i * D.ncell + c));
+      if (!(rho > 0.0) || !isfinite(rho)) ++local;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) {
+    atomicAdd(count, local);
+    atomicOr(P.err, kErrDiverged);
+  }
+}
+
+int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g > 152LL * 64) g = 152LL * 64;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <class F>
+int dispatch(int precision, F&& f) {
+  switch (precision) {
+    case SC_P_FP32_SHIFT: return f((float*)nullptr);
+    case SC_P_BF16_STORE: return f((__nv_bfloat16*)nullptr);
+    case SC_P_FP16_STORE: return f((__half*)nullptr);
+    case SC_P_FP64_PLAIN: return f((double*)nullptr);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+// ======================================================================= launchers
+int launch_aa_step(const StepParams& P, int precision, void* stream, int grid) {
+  dim3 block(P.bx, P.by);
+  cudaStream_t s = (cudaStream_t)stream;
+  return dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
+    else {
+      aa_step_kernel<S><<<grid, block, 0, s>>>(P);
+      return (int)cudaGetLastError();
+    }
+  });
+}
+
+int aa_persistent_max_grid(const StepParams& P, int precision, int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = P.bx * P.by;
+  int rc = dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
+    else return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, aa_persistent_kernel<S>, threads, 0);
+  });
+  *grid = sms * per;
+  return rc;
+}
+
+int launch_aa_persistent(const StepParams& P, int precision, void* stream, int grid) {
+  dim3 block(P.bx, P.by);
+  cudaStream_t s = (cudaStream_t)stream;
+  return dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
+    else {
+      void* args[] = {(void*)&P};
+      return (int)cudaLaunchCooperativeKernel((const void*)aa_persistent_kernel<S>, dim3(grid), block,
+                                              args, 0, s);
+    }
+  });
+}
+
+int launch_plain_step(const StepParams& P, unsigned long long n, void* stream) {
+  const DevDomain& D = P.dom[P.plain_domain];
+  dim3 block(P.bx, P.by);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the time level of the plain path is tracked on the host
+  plain_step_kernel<<<(unsigned)D.tiles_per_node, block, 0, s>>>(P, n);
+  return (int)cudaGetLastError();
+}
+
+int launch_set_counter(unsigned long long* p, unsigned long long v, void* stream) {
+  set_counter_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(p, v);
+  return (int)cudaGetLastError();
+}
+
+int launch_init_equilibrium(const StepParams& P, int precision, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int d = 0; d < P.n_domains; ++d) {
+    const DevDomain& D = P.dom[d];
+    const long long total = (long long)D.nodes * kQ * D.ncell;
+    int rc = dispatch(precision, [&](auto tag) -> int {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      if constexpr (std::is_same_v<S, double>) {
+        init_kernel<double, false><<<grid_for(total, 256), 256, 0, s>>>((double*)D.g, D.ncell, total);
+        init_kernel<double, false><<<grid_for(total, 256), 256, 0, s>>>((double*)D.g2, D.ncell, total);
+      } else {
+        init_kernel<S, true><<<grid_for(total, 256), 256, 0, s>>>((S*)D.g, D.ncell, total);
+      }
+      return (int)cudaGetLastError();
+    });
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevDomain& D = P.dom[A.domain];
+  return dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    constexpr bool SH = !std::is_same_v<S, double>;
+    const int blk = 256;
+    if (A.mean) {
+      moments_kernel<S, SH><<<(unsigned)((D.ncell + blk - 1) / blk), blk, 0, s>>>(P, A);
+      int rc = (int)cudaGetLastError();
+      if (rc) return rc;
+    }
+    if (A.n_p > 0) {
+      const long long warps = (long long)A.n_p * D.nz;
+      profiles_kernel<S, SH><<<(unsigned)((warps * 32 + blk - 1) / blk), blk, 0, s>>>(P, A);
+    }
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_export(const StepParams& P, int precision, int domain, int node, double* d_f,
+                  float* d_u, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevDomain& D = P.dom[domain];
+  return dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    constexpr bool SH = !std::is_same_v<S, double>;
+    export_kernel<S, SH><<<(unsigned)((D.ncell + 255) / 256), 256, 0, s>>>(P, domain, node, d_f, d_u);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_check(const StepParams& P, int precision, unsigned long long* d_count, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    constexpr bool SH = !std::is_same_v<S, double>;
+    check_kernel<S, SH><<<152 * 8, 256, 0, s>>>(P, d_count);
+    return (int)cudaGetLastError();
+  });
+}
+
+}  // namespace sclbm

@@ -1,0 +1,113 @@
+// sclbm_internal.h -- structures shared by the host side of libsclbm and its
+// CUDA kernels.  Not part of the public ABI (include/sclbm.h is).
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+#include <vector_types.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sclbm.h"
+
+namespace sclbm {
+
+constexpr int kQ = 19;
+constexpr int kMaxDomains = SC_MAX_DOMAINS;
+constexpr int kMaxGpcP = 20;     // largest gPC basis the reduction kernel keeps in registers
+
+// Link word per cell: bit i (0..18) set when the pull source x - c_i of
+// direction i is not an in-domain fluid cell reached without periodic wrap
+// (solid, across a face, or wrapped).  Such links take the boundary path.
+constexpr uint32_t kLinkSolid = 1u << 19;   // the cell itself is solid
+constexpr uint32_t kLinkOutlet = 1u << 20;  // fluid cell on an OUTFLOW +x face
+constexpr uint32_t kLinkMask = (1u << 19) - 1u;
+
+// Device error word bits.
+constexpr unsigned kErrDiverged = 1u;
+constexpr unsigned kErrTimeout = 2u;
+
+// Per-domain view handed to the kernels (plain pointers into the workspace).
+struct DevDomain {
+  int nx, ny, nz, nodes;
+  long long ncell;
+  int bc[6];
+  const uint8_t* flags;     // [ncell]
+  const uint32_t* link;     // [ncell]
+  const float4* uin_f;      // [nodes][nz] (ux, uy, uz, 0)
+  const double* uin_d;      // [nodes][nz][3]
+  void* g;                  // [nodes][19][ncell] storage (AA) or FP64 array A
+  void* g2;                 // FP64 plain: array B, else null
+  float* bout;              // [nodes][nz*ny][5] outflow plane (AA only)
+  long long tiles_x, tiles_y, tiles_z, tiles_per_node;
+  long long tile_begin;     // first global tile of this domain
+};
+
+struct StepParams {
+  int n_domains;
+  DevDomain dom[kMaxDomains];
+  float tau0;
+  float smag18c2;             // 18 C_S^2
+  double tau0_d, smag18c2_d;
+  int csmag_on;
+  const float* ramp_f;        // [ramp_steps + 1]
+  const double* ramp_d;
+  int ramp_steps;
+  unsigned long long* step;   // device step counter (time level of the state)
+  unsigned int* done;         // blocks finished in the current launch
+  unsigned int* err;          // latched error bits
+  long long total_tiles;
+  int bx, by, bz, order;
+  // persistent mode
+  unsigned int* bar_count;
+  unsigned int* bar_gen;
+  long long spin_limit;
+  int never_arrive;
+  int n_steps;                // persistent: steps per launch
+  int plain_node;             // FP64 plain path: node advanced by this launch
+  int plain_domain;
+};
+
+// ------------------------------------------------------------ host numerics
+// Implemented in host_numerics.cpp (IEEE double, no FP contraction).
+int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi,
+                  std::vector<double>& Z, std::vector<double>& w);
+int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags);
+int hn_probe_columns(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xy);
+int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xyz);
+void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<uint32_t>& link);
+void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
+               double* uin /*[nz][3]*/);
+int hn_gpc_size(int d, int degree);
+void hn_gpc_basis(int d, int degree, const double* s /*[d]*/, double* phi /*[P]*/);
+double hn_ramp(int ramp_steps, long long m);
+
+// ------------------------------------------------------------ kernel launchers
+// Implemented in lbm_kernels.cu.  All return cudaError_t as int.
+int launch_aa_step(const StepParams& P, int precision, void* stream, int grid);
+int launch_aa_persistent(const StepParams& P, int precision, void* stream, int grid);
+int launch_plain_step(const StepParams& P, unsigned long long n, void* stream);
+int launch_set_counter(unsigned long long* p, unsigned long long v, void* stream);
+int aa_persistent_max_grid(const StepParams& P, int precision, int* grid);
+int launch_init_equilibrium(const StepParams& P, int precision, void* stream);
+struct MomentArgs {
+  int domain;
+  const double* ab;        // [nq][stride] : a_j then a_j * Phi_alpha(Z_j)
+  int stride;              // row length of ab (basis size of the configuration + 1)
+  int nq, P;               // P: coefficients to produce (0 = none)
+  double wsum;
+  double* mean;
+  double* stdev;
+  double* coef;            // [P][ncell] or null
+  const int32_t* probes;   // device [n_p][2]
+  int n_p;
+  double* prof;            // device
+  float* prof_nodes;       // device or null
+};
+int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void* stream);
+int launch_export(const StepParams& P, int precision, int domain, int node, double* d_f,
+                  float* d_u, void* stream);
+int launch_check(const StepParams& P, int precision, unsigned long long* d_count, void* stream);
+
+}  // namespace sclbm

@@ -1,0 +1,392 @@
+"""Thin Python binding of libsclbm (include/sclbm.h).
+
+Argument marshalling only: every step of the stochastic-collocation LBM path
+runs in the library's CUDA kernels.  PyTorch supplies device memory (the
+workspace and output tensors) and the CUDA stream.  The functions carry the
+C names; each raises ScError on a non-zero status.  If the shared library is
+missing it is built in-tree; if it cannot be built or loaded, import of the
+calls fails loudly (there is no fallback implementation).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SC_OK = 0
+SC_ERR_ARG, SC_ERR_WORKSPACE, SC_ERR_CUDA = -1, -2, -3
+SC_ERR_DIVERGED, SC_ERR_TIMEOUT, SC_ERR_UNSUPPORTED, SC_ERR_STATE = -4, -5, -6, -7
+SC_BC_VELOCITY, SC_BC_OUTFLOW, SC_BC_BOUNCE_BACK, SC_BC_FREE_SLIP, SC_BC_PERIODIC = 0, 1, 2, 3, 4
+SC_IN_SPEED_REL, SC_IN_ALPHA, SC_IN_ANGLE_DEG = 0, 1, 2
+SC_Q_GL, SC_Q_CC_SMOLYAK = 0, 1
+SC_P_FP64_PLAIN, SC_P_FP32_SHIFT, SC_P_BF16_STORE, SC_P_FP16_STORE = 0, 1, 2, 3
+SC_EXEC_LAUNCH, SC_EXEC_GRAPH, SC_EXEC_PERSISTENT = 0, 1, 2
+
+_NAMES = {SC_ERR_ARG: "SC_ERR_ARG", SC_ERR_WORKSPACE: "SC_ERR_WORKSPACE", SC_ERR_CUDA: "SC_ERR_CUDA",
+          SC_ERR_DIVERGED: "SC_ERR_DIVERGED", SC_ERR_TIMEOUT: "SC_ERR_TIMEOUT",
+          SC_ERR_UNSUPPORTED: "SC_ERR_UNSUPPORTED", SC_ERR_STATE: "SC_ERR_STATE"}
+
+
+class ScError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__("%s returned %s%s" % (where, _NAMES.get(code, code),
+                                                (": " + detail) if detail else ""))
+
+
+class sc_domain_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("geom_seed", C.c_uint64),
+                ("n_buildings", C.c_int), ("fp_min", C.c_int), ("fp_max", C.c_int),
+                ("h_min", C.c_int), ("h_max", C.c_int), ("boxes", C.POINTER(C.c_int32)),
+                ("n_boxes", C.c_int), ("bc", C.c_int * 6), ("quad_level", C.c_int)]
+
+
+class sc_lbm_config(C.Structure):
+    _fields_ = [("n_domains", C.c_int), ("domains", C.POINTER(sc_domain_desc)),
+                ("tau0", C.c_double), ("c_smag", C.c_double), ("u_ref", C.c_double),
+                ("alpha", C.c_double), ("angle_deg", C.c_double), ("H_ref", C.c_double),
+                ("n_inputs", C.c_int), ("inputs", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("quad_rule", C.c_int), ("ramp_steps", C.c_int),
+                ("precision", C.c_int), ("gpc_degree", C.c_int)]
+
+
+class sc_lbm_tuning(C.Structure):
+    _fields_ = [("block_x", C.c_int), ("block_y", C.c_int), ("slab_z", C.c_int),
+                ("tile_order", C.c_int), ("exec_mode", C.c_int), ("graph_steps", C.c_int)]
+
+
+# Every exported symbol of include/sclbm.h with its ctypes signature.
+_H = C.c_void_p
+_P = C.c_void_p
+SIGNATURES = {
+    "sc_lbm_workspace_size": (C.c_int, [C.POINTER(sc_lbm_config), C.POINTER(C.c_size_t)]),
+    "sc_lbm_quadrature": (C.c_int, [C.POINTER(sc_lbm_config), C.c_int, C.POINTER(C.c_int), _P, _P,
+                                    C.c_int]),
+    "sc_lbm_geometry": (C.c_int, [C.POINTER(sc_lbm_config), C.c_int, _P]),
+    "sc_lbm_probe_columns": (C.c_int, [C.POINTER(sc_lbm_config), C.c_int, C.c_int, _P]),
+    "sc_lbm_probe_points": (C.c_int, [C.POINTER(sc_lbm_config), C.c_int, C.c_int, _P]),
+    "sc_lbm_init": (C.c_int, [C.POINTER(sc_lbm_config), _P, C.c_size_t, _P, _P, C.POINTER(_H)]),
+    "sc_lbm_reset": (C.c_int, [_H]),
+    "sc_lbm_step": (C.c_int, [_H, C.c_int]),
+    "sc_lbm_moments": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int]),
+    "sc_lbm_velocity": (C.c_int, [_H, C.c_int, C.c_int, _P]),
+    "sc_lbm_populations": (C.c_int, [_H, C.c_int, C.c_int, _P]),
+    "sc_lbm_autotune": (C.c_int, [_H, C.c_char_p]),
+    "sc_lbm_set_tuning": (C.c_int, [_H, C.POINTER(sc_lbm_tuning)]),
+    "sc_lbm_get_tuning": (C.c_int, [_H, C.POINTER(sc_lbm_tuning)]),
+    "sc_lbm_counters": (C.c_int, [_H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "sc_lbm_sync": (C.c_int, [_H]),
+    "sc_lbm_check": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
+    "sc_lbm_debug_barrier": (C.c_int, [_H, C.c_int, C.c_longlong]),
+    "sc_lbm_state_size": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
+    "sc_lbm_save": (C.c_int, [_H, _P, C.c_size_t]),
+    "sc_lbm_load": (C.c_int, [_H, _P, C.c_size_t]),
+    "sc_lbm_last_error": (C.c_char_p, [_H]),
+    "sc_lbm_destroy": (C.c_int, [_H]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsclbm (building it in-tree first if it is absent)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _call(name, *args, handle=None):
+    rc = getattr(lib(), name)(*args)
+    if rc != SC_OK:
+        detail = ""
+        if handle:
+            msg = lib().sc_lbm_last_error(handle)
+            detail = msg.decode() if msg else ""
+        raise ScError(rc, name, detail)
+    return rc
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# ------------------------------------------------------------------ config
+class Config:
+    """Owns an sc_lbm_config and the arrays it points to."""
+
+    def __init__(self, domains, tau0, c_smag, u_ref, alpha, inputs, lo, hi, quad_rule,
+                 precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1):
+        self._doms = (sc_domain_desc * len(domains))()
+        self._boxes = []
+        for k, d in enumerate(domains):
+            D = self._doms[k]
+            D.nx, D.ny, D.nz = d["nx"], d["ny"], d["nz"]
+            D.geom_seed = d.get("seed", 0)
+            D.n_buildings = d.get("n_buildings", 0)
+            D.fp_min, D.fp_max = d.get("fp", (1, 1))
+            D.h_min, D.h_max = d.get("h", (1, 1))
+            boxes = d.get("boxes")
+            if boxes:
+                arr = np.ascontiguousarray(np.asarray(boxes, np.int32).reshape(-1))
+                self._boxes.append(arr)
+                D.boxes = arr.ctypes.data_as(C.POINTER(C.c_int32))
+                D.n_boxes = arr.size // 6
+            for f in range(6):
+                D.bc[f] = int(d["bc"][f])
+            D.quad_level = d["quad_level"]
+        c = sc_lbm_config()
+        c.n_domains = len(domains)
+        c.domains = C.cast(self._doms, C.POINTER(sc_domain_desc))
+        c.tau0, c.c_smag, c.u_ref, c.alpha = tau0, c_smag, u_ref, alpha
+        c.angle_deg, c.H_ref = angle_deg, H_ref
+        c.n_inputs = len(inputs)
+        for k in range(len(inputs)):
+            c.inputs[k], c.lo[k], c.hi[k] = inputs[k], lo[k], hi[k]
+        c.quad_rule, c.ramp_steps, c.precision, c.gpc_degree = quad_rule, ramp_steps, precision, gpc_degree
+        self.c = c
+        self.domains = [dict(d) for d in domains]
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+# ------------------------------------------------------------------ host-only calls
+def sc_lbm_workspace_size(cfg):
+    n = C.c_size_t(0)
+    _call("sc_lbm_workspace_size", cfg.ref, C.byref(n))
+    return n.value
+
+
+def sc_lbm_quadrature(cfg, domain):
+    n = C.c_int(0)
+    _call("sc_lbm_quadrature", cfg.ref, domain, C.byref(n), None, None, 0)
+    Z = np.zeros((n.value, cfg.c.n_inputs))
+    w = np.zeros(n.value)
+    _call("sc_lbm_quadrature", cfg.ref, domain, C.byref(n), Z.ctypes.data, w.ctypes.data, n.value)
+    return Z, w
+
+
+def sc_lbm_geometry(cfg, domain):
+    d = cfg.domains[domain]
+    flags = np.zeros(d["nx"] * d["ny"] * d["nz"], np.uint8)
+    _call("sc_lbm_geometry", cfg.ref, domain, flags.ctypes.data)
+    return flags
+
+
+def sc_lbm_probe_columns(cfg, domain, n):
+    xy = np.zeros((n, 2), np.int32)
+    _call("sc_lbm_probe_columns", cfg.ref, domain, n, xy.ctypes.data)
+    return xy
+
+
+def sc_lbm_probe_points(cfg, domain, n):
+    xyz = np.zeros((n, 3), np.int32)
+    _call("sc_lbm_probe_points", cfg.ref, domain, n, xyz.ctypes.data)
+    return xyz
+
+
+# ------------------------------------------------------------------ device calls
+def sc_lbm_init(cfg, ws_ptr, nbytes, stream_ptr, flags_host=None):
+    h = C.c_void_p()
+    keep = None
+    fh = None
+    if flags_host is not None:
+        arrs = [None if f is None else np.ascontiguousarray(f, np.uint8) for f in flags_host]
+        keep = arrs
+        fh = (C.c_void_p * len(arrs))(*[None if a is None else a.ctypes.data for a in arrs])
+    _call("sc_lbm_init", cfg.ref, C.c_void_p(ws_ptr), nbytes, C.c_void_p(stream_ptr), fh, C.byref(h))
+    del keep
+    return h
+
+
+def sc_lbm_reset(h):
+    _call("sc_lbm_reset", h, handle=h)
+
+
+def sc_lbm_step(h, n):
+    _call("sc_lbm_step", h, int(n), handle=h)
+
+
+def sc_lbm_moments(h, domain, mean, std, probes=None, prof=None, prof_nodes=None, coef=None,
+                   out_host=False):
+    n_p = 0
+    pp = None
+    if probes is not None:
+        probes = np.ascontiguousarray(np.asarray(probes, np.int32).reshape(-1, 2))
+        n_p = probes.shape[0]
+        pp = probes.ctypes.data
+    _call("sc_lbm_moments", h, domain, _ptr(mean), _ptr(std), pp, n_p, _ptr(prof), _ptr(prof_nodes),
+          _ptr(coef), 1 if out_host else 0, handle=h)
+
+
+def sc_lbm_velocity(h, domain, node, u):
+    _call("sc_lbm_velocity", h, domain, node, _ptr(u), handle=h)
+
+
+def sc_lbm_populations(h, domain, node, f):
+    _call("sc_lbm_populations", h, domain, node, _ptr(f), handle=h)
+
+
+def sc_lbm_autotune(h, cache_path=None):
+    _call("sc_lbm_autotune", h, cache_path.encode() if cache_path else None, handle=h)
+
+
+def sc_lbm_set_tuning(h, block_x, block_y, slab_z, tile_order=0, exec_mode=SC_EXEC_LAUNCH,
+                      graph_steps=50):
+    t = sc_lbm_tuning(block_x, block_y, slab_z, tile_order, exec_mode, graph_steps)
+    _call("sc_lbm_set_tuning", h, C.byref(t), handle=h)
+
+
+def sc_lbm_get_tuning(h):
+    t = sc_lbm_tuning()
+    _call("sc_lbm_get_tuning", h, C.byref(t), handle=h)
+    return dict(block_x=t.block_x, block_y=t.block_y, slab_z=t.slab_z, tile_order=t.tile_order,
+                exec_mode=t.exec_mode, graph_steps=t.graph_steps)
+
+
+def sc_lbm_counters(h):
+    s, k = C.c_longlong(0), C.c_longlong(0)
+    _call("sc_lbm_counters", h, C.byref(s), C.byref(k), handle=h)
+    return s.value, k.value
+
+
+def sc_lbm_sync(h):
+    _call("sc_lbm_sync", h, handle=h)
+
+
+def sc_lbm_check(h):
+    n = C.c_longlong(0)
+    rc = lib().sc_lbm_check(h, C.byref(n))
+    return rc, n.value
+
+
+def sc_lbm_debug_barrier(h, never_arrive, spin_limit):
+    _call("sc_lbm_debug_barrier", h, int(never_arrive), int(spin_limit), handle=h)
+
+
+def sc_lbm_state_size(h):
+    n = C.c_size_t(0)
+    _call("sc_lbm_state_size", h, C.byref(n), handle=h)
+    return n.value
+
+
+def sc_lbm_save(h, buf):
+    _call("sc_lbm_save", h, _ptr(buf), buf.nbytes if hasattr(buf, "nbytes") else len(buf), handle=h)
+
+
+def sc_lbm_load(h, buf):
+    _call("sc_lbm_load", h, _ptr(buf), buf.nbytes, handle=h)
+
+
+def sc_lbm_last_error(h):
+    m = lib().sc_lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def sc_lbm_destroy(h):
+    _call("sc_lbm_destroy", h)
+
+
+# ------------------------------------------------------------------ convenience
+class Ensemble:
+    """One library handle with a torch-allocated workspace and its own stream.
+
+    All outputs are torch tensors allocated on the handle's stream; the
+    caller's current stream is made to wait for them before they are
+    returned."""
+
+    def __init__(self, cfg, flags_host=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.nbytes = sc_lbm_workspace_size(cfg)
+        with torch.cuda.stream(self.stream):
+            self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.h = sc_lbm_init(cfg, self.ws.data_ptr(), self.nbytes, self.stream.cuda_stream, flags_host)
+        self.n_nodes = [sc_lbm_quadrature(cfg, d)[1].size for d in range(cfg.c.n_domains)]
+
+    def _out(self, *shape, dtype=None):
+        with self.torch.cuda.stream(self.stream):
+            return self.torch.empty(*shape, dtype=dtype or self.torch.float64, device=self.device)
+
+    def _hand_over(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def ncell(self, d):
+        D = self.cfg.domains[d]
+        return D["nx"] * D["ny"] * D["nz"]
+
+    def step(self, n):
+        sc_lbm_step(self.h, n)
+
+    def moments(self, domain=0, probes=None, nodes_profiles=False, gpc=False):
+        t = self.torch
+        n = self.ncell(domain)
+        nz = self.cfg.domains[domain]["nz"]
+        mean, std = self._out(n), self._out(n)
+        prof = pn = coef = None
+        if probes is not None:
+            probes = np.asarray(probes, np.int32).reshape(-1, 2)
+            prof = self._out(probes.shape[0], nz, 4)
+            if nodes_profiles:
+                pn = self._out(probes.shape[0], self.n_nodes[domain], nz, dtype=t.float32)
+        if gpc:
+            from math import comb
+            P = comb(self.cfg.c.gpc_degree + self.cfg.c.n_inputs, self.cfg.c.n_inputs)
+            coef = self._out(P, n)
+        sc_lbm_moments(self.h, domain, mean, std, probes, prof, pn, coef)
+        self._hand_over()
+        return dict(mean=mean, std=std, prof=prof, prof_nodes=pn, coef=coef)
+
+    def velocity(self, domain, node):
+        u = self._out(3, self.ncell(domain), dtype=self.torch.float32)
+        sc_lbm_velocity(self.h, domain, node, u)
+        self._hand_over()
+        return u
+
+    def populations(self, domain, node):
+        f = self._out(19, self.ncell(domain))
+        sc_lbm_populations(self.h, domain, node, f)
+        self._hand_over()
+        return f
+
+    def sync(self):
+        sc_lbm_sync(self.h)
+
+    def close(self):
+        if self.h:
+            sc_lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_config(workload, **over):
+    """sc_lbm_config for a workload dict (see workloads.py); keyword arguments
+    replace top-level fields (e.g. precision=SC_P_BF16_STORE)."""
+    w = dict(workload)
+    w.update(over)
+    return Config(w["domains"], w["tau0"], w["c_smag"], w["u_ref"], w["alpha"], w["inputs"], w["lo"],
+                  w["hi"], w["quad_rule"], w["precision"], ramp_steps=w["ramp_steps"],
+                  angle_deg=w.get("angle_deg", 0.0), H_ref=w.get("H_ref", 0.0),
+                  gpc_degree=w.get("gpc_degree", -1))

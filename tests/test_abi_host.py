@@ -1,0 +1,128 @@
+"""CPU tests of the C ABI: the library loads, exports every function that
+include/*.h declares, and its host-only calls (quadrature, geometry, probes,
+validation) agree bit for bit with the oracle.  No GPU is touched."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2508_18202_gb300 import sclbm as S
+from paper_2508_18202_gb300 import workloads as W
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = S.lib()
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    names = _declared()
+    assert names <= set(S.SIGNATURES), sorted(names - set(S.SIGNATURES))
+
+
+def _oracle_rule(O, cfg, d):
+    c = cfg.c
+    lo = [c.lo[k] for k in range(c.n_inputs)]
+    hi = [c.hi[k] for k in range(c.n_inputs)]
+    return O.quadrature(c.quad_rule, c.n_inputs, cfg.domains[d]["quad_level"], lo, hi)
+
+
+@pytest.mark.parametrize("wl", W.ALL, ids=lambda w: w["name"])
+def test_quadrature_bit_exact_with_oracle(O, wl):
+    cfg = S.make_config(wl)
+    for d in range(len(wl["domains"])):
+        Z, w = S.sc_lbm_quadrature(cfg, d)
+        Zo, wo = _oracle_rule(O, cfg, d)
+        assert Z.shape == Zo.shape
+        assert Z.tobytes() == Zo.tobytes()
+        assert w.tobytes() == wo.tobytes()
+
+
+@pytest.mark.parametrize("rule,d,level", [(0, 1, n) for n in range(1, 6)] + [(0, 2, 3), (0, 3, 2)]
+                         + [(1, d, L) for d in (1, 2, 3) for L in (1, 2, 3, 4, 5)])
+def test_quadrature_rules_bit_exact(O, rule, d, level):
+    lo = [-0.15, 0.15, -10.0][:d]
+    hi = [0.15, 0.35, 10.0][:d]
+    dom = dict(nx=8, ny=8, nz=8, bc=[2] * 6, quad_level=level)
+    inputs = [W.SPEED, W.ALPHA, W.ANGLE][:d]
+    cfg = S.Config([dom], 0.6, 0.0, 0.05, 0.25, inputs, lo, hi, rule, W.FP32_SHIFT)
+    Z, w = S.sc_lbm_quadrature(cfg, 0)
+    Zo, wo = O.quadrature(rule, d, level, lo, hi)
+    assert Z.tobytes() == Zo.tobytes() and w.tobytes() == wo.tobytes()
+
+
+@pytest.mark.parametrize("wl", W.ALL, ids=lambda w: w["name"])
+def test_geometry_and_probes_bit_exact_with_oracle(O, wl):
+    cfg = S.make_config(wl)
+    for d, D in enumerate(wl["domains"]):
+        flags = S.sc_lbm_geometry(cfg, d)
+        fo = O.geometry(D["nx"], D["ny"], D["nz"], D.get("seed", 0), D.get("n_buildings", 0),
+                        *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"))
+        assert flags.tobytes() == fo.tobytes()
+        if D.get("boxes") is None:
+            xy = S.sc_lbm_probe_columns(cfg, d, 4)
+            assert np.array_equal(xy, O.probe_columns(D["nx"], D["ny"], D["nz"], D["seed"], fo, 4))
+            pts = S.sc_lbm_probe_points(cfg, d, 16)
+            assert np.array_equal(pts, O.probe_points(D["nx"], D["ny"], D["nz"], D["seed"], fo, 16))
+
+
+def test_workspace_size_scales_with_precision():
+    b32 = S.sc_lbm_workspace_size(S.make_config(W.URBAN_LES))
+    b16 = S.sc_lbm_workspace_size(S.make_config(W.URBAN_LES, precision=W.BF16_STORE))
+    b64 = S.sc_lbm_workspace_size(S.make_config(W.URBAN_LES, precision=W.FP64_PLAIN))
+    pops = 13 * 19 * 256 * 128 * 64
+    assert b32 > 4 * pops and b16 > 2 * pops and b64 > 16 * pops
+    assert b16 < b32 < b64
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(tau0=0.5), S.SC_ERR_ARG),
+    (dict(tau0=0.45), S.SC_ERR_ARG),
+    (dict(c_smag=-0.1), S.SC_ERR_ARG),
+    (dict(lo=[0.1, 0.15], hi=[-0.1, 0.35]), S.SC_ERR_ARG),
+    (dict(quad_rule=7), S.SC_ERR_ARG),
+    (dict(precision=9), S.SC_ERR_ARG),
+    (dict(gpc_degree=6), S.SC_ERR_UNSUPPORTED),
+    (dict(domain_over=dict(bc=[W.OUT, W.VEL, W.VEL, W.VEL, W.BB, W.FS])), S.SC_ERR_UNSUPPORTED),
+    (dict(domain_over=dict(bc=[W.PER, W.OUT, W.VEL, W.VEL, W.BB, W.FS])), S.SC_ERR_ARG),
+    (dict(domain_over=dict(nx=0)), S.SC_ERR_ARG),
+])
+def test_invalid_configurations_rejected(bad, code):
+    wl = W.variant(W.URBAN_LES, **bad)
+    with pytest.raises(S.ScError) as ei:
+        S.sc_lbm_workspace_size(S.make_config(wl))
+    assert ei.value.code == code
+
+
+def test_device_calls_reject_null_handles():
+    L = S.lib()
+    assert L.sc_lbm_step(None, 1) == S.SC_ERR_ARG
+    assert L.sc_lbm_sync(None) == S.SC_ERR_ARG
+    assert L.sc_lbm_destroy(None) == S.SC_ERR_ARG
+    assert L.sc_lbm_last_error(None) == b"null handle"
+
+
+def test_init_rejects_missing_workspace():
+    cfg = S.make_config(W.CHANNEL_CUBE)
+    import ctypes as C
+    h = C.c_void_p()
+    rc = S.lib().sc_lbm_init(cfg.ref, None, 0, None, None, C.byref(h))
+    assert rc == S.SC_ERR_WORKSPACE
+    rc = S.lib().sc_lbm_init(cfg.ref, C.c_void_p(0x1000), 16, None, None, C.byref(h))
+    assert rc == S.SC_ERR_WORKSPACE

@@ -1,0 +1,347 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Small ragged domains (several tiles plus a ragged tail in x, y and z) cover
+every boundary kind on both parities of the AA pattern, FP64 plain and FP32
+shifted storage; full-size checks run in the launch shape the benchmark
+times.  Tolerances (relative L2 over fluid cells and all components, per the
+accuracy targets of the method): FP32 laminar velocity <= 1e-5 after 1000
+steps, LES <= 1e-3 after 100 steps, ensemble mean / std <= 1e-3; FP64 plain
+<= 1e-12; one FP32 step from an exported state <= 2e-6 max abs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import oracle_domain, oracle_nodes, oracle_run_node, oracle_uin, rel_l2
+from paper_2508_18202_gb300 import sclbm as S
+from paper_2508_18202_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VEL, OUT, BB, FS, PER = W.VEL, W.OUT, W.BB, W.FS, W.PER
+
+# A ragged domain (37 x 19 x 13) with blocks touching the outlet, the lid and a
+# side face, so that every link rule (including two-face edges) is exercised.
+RAGGED_BOXES = [[6, 3, 0, 10, 8, 5], [14, 0, 0, 17, 4, 13], [33, 9, 0, 37, 13, 6],
+                [24, 14, 0, 28, 19, 9], [20, 7, 3, 23, 11, 7]]
+
+BC_SETS = {
+    "urban": [VEL, OUT, VEL, VEL, BB, FS],
+    "channel": [VEL, OUT, BB, BB, BB, BB],
+    "periodic_y_freeslip": [VEL, OUT, PER, PER, FS, FS],
+    "closed_box": [BB, BB, BB, BB, BB, FS],
+    "velocity_both_x": [VEL, VEL, FS, FS, BB, FS],
+    "periodic_all": [PER, PER, PER, PER, PER, PER],
+}
+
+
+def ragged(bc, precision=W.FP32_SHIFT, c_smag=0.14, tau0=0.56, ramp=8, nx=37, ny=19, nz=13,
+           angle=12.0, quad_level=3, boxes=RAGGED_BOXES):
+    return dict(
+        name="ragged", domains=[dict(nx=nx, ny=ny, nz=nz, boxes=boxes, bc=bc, quad_level=quad_level)],
+        tau0=tau0, c_smag=c_smag, u_ref=0.05, alpha=0.25, angle_deg=angle, H_ref=0.0,
+        inputs=[W.SPEED], lo=[-0.1], hi=[0.1], quad_rule=W.GL, ramp_steps=ramp,
+        precision=precision, gpc_degree=2)
+
+
+def fluid_mask(flags):
+    return np.asarray(flags) == 0
+
+
+def gpu_state(ens, d, j):
+    return ens.populations(d, j).cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    S.lib()
+    return torch.device("cuda")
+
+
+@pytest.mark.parametrize("bcname", list(BC_SETS))
+@pytest.mark.parametrize("precision,tol", [(W.FP32_SHIFT, 2e-6), (W.FP64_PLAIN, 1e-13)])
+def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol):
+    """Populations after 1..6 and 31 steps (both AA parities) at every fluid
+    cell and node, max abs difference."""
+    wl = ragged(BC_SETS[bcname], precision=precision)
+    ens = S.Ensemble(S.make_config(wl))
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    fl = fluid_mask(flags)
+    fo = [O.init_equilibrium(p, flags) for _ in range(len(a))]
+    done = 0
+    for target in (1, 2, 3, 4, 5, 6, 31):
+        ens.step(target - done)
+        for j in range(len(a)):
+            O.run(p, flags, oracle_uin(O, wl, 0, Z[j]), fo[j], done, target - done)
+        done = target
+        for j in range(len(a)):
+            fg = gpu_state(ens, 0, j)
+            err = np.max(np.abs(fg[:, fl] - fo[j][:, fl]))
+            assert err < tol, (bcname, target, j, err)
+    ens.sync()
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", [W.BF16_STORE, W.FP16_STORE])
+def test_reduced_storage_tracks_oracle(O, cuda, precision):
+    """BF16 / FP16 storage of the shifted populations: error report against
+    FP64 after 40 steps (bounded, not bit-level)."""
+    wl = ragged(BC_SETS["urban"], precision=precision)
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(40)
+    p, flags, f = oracle_run_node(O, wl, 0, 1, 40)
+    _, uo = O.macros(p, flags, f)
+    ug = ens.velocity(0, 1).cpu().numpy()
+    fl = fluid_mask(flags)
+    err = rel_l2(ug[:, fl], uo[:, fl])
+    bound = 5e-2 if precision == W.BF16_STORE else 5e-3
+    assert err < bound, err
+    ens.close()
+
+
+def test_laminar_channel_1000_steps(O, cuda):
+    """Cube in a channel, BGK tau = 0.6, FP32 shifted vs FP64: velocity relative
+    L2 <= 1e-5 after 1000 steps (first and last collocation nodes)."""
+    wl = dict(W.CHANNEL_CUBE, precision=W.FP32_SHIFT)
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(1000)
+    for j in (0, 4):
+        p, flags, f = oracle_run_node(O, wl, 0, j, 1000)
+        _, uo = O.macros(p, flags, f)
+        ug = ens.velocity(0, j).cpu().numpy()
+        fl = fluid_mask(flags)
+        assert rel_l2(ug[:, fl], uo[:, fl]) <= 1e-5
+    ens.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(W.FP64_PLAIN, 1e-11), (W.FP32_SHIFT, 1e-5)])
+def test_channel_ensemble_statistics(O, cuda, precision, tol):
+    """Five Gauss-Legendre nodes, 300 steps: mean / std of |u| (Eq.
+    quad_moments), the profile band behind the cube and the gPC coefficients
+    (Eq. coef_discrete) against the oracle's two-pass reduction."""
+    wl = dict(W.CHANNEL_CUBE, precision=precision)
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(wl["steps"])
+    out = ens.moments(0, probes=wl["columns"], nodes_profiles=True, gpc=True)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    Qv = O.ensemble(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, wl["steps"])
+    mean, std, _ = O.moments_two_pass(a, Qv)
+    fl = fluid_mask(flags)
+    assert rel_l2(out["mean"].cpu().numpy()[fl], mean[fl]) <= tol
+    assert rel_l2(out["std"].cpu().numpy()[fl], std[fl]) <= tol * 10
+    prof, pn = O.profiles(a, Qv, p.nx, p.ny, p.nz, wl["columns"])
+    assert rel_l2(out["prof"].cpu().numpy(), prof) <= tol * 10
+    assert rel_l2(out["prof_nodes"].cpu().numpy(), pn) <= 1e-6
+    s = O.legendre_s(Z, wl["lo"], wl["hi"])
+    coef = O.gpc_project(a, Qv, O.gpc_basis(1, wl["gpc_degree"], s))
+    cg = out["coef"].cpu().numpy()
+    assert rel_l2(cg[0][fl], coef[0][fl]) <= tol
+    assert rel_l2(cg[1][fl], coef[1][fl]) <= tol * 10
+    # gPC mean equals the quadrature mean (Eq. gPC with orthonormal basis)
+    assert np.max(np.abs(cg[0] - out["mean"].cpu().numpy())) < 1e-12
+    ens.close()
+
+
+def test_batched_uneven_domains_match_oracle(O, cuda):
+    """Three domains of different sizes and node counts advance in one launch;
+    each matches its own oracle run."""
+    doms = [dict(nx=40, ny=18, nz=12, seed=1, n_buildings=2, fp=(4, 6), h=(3, 7), bc=W.URBAN_BC, quad_level=2),
+            dict(nx=29, ny=23, nz=14, seed=2, n_buildings=3, fp=(3, 5), h=(3, 9), bc=W.URBAN_BC, quad_level=3),
+            dict(nx=52, ny=11, nz=9, seed=3, n_buildings=1, fp=(3, 4), h=(2, 4), bc=W.URBAN_BC, quad_level=1)]
+    wl = dict(W.URBAN_BATCHED, domains=doms, ramp_steps=5, tau0=0.56)
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(27)
+    for d in range(3):
+        Z, a = oracle_nodes(O, wl, d)
+        assert len(a) == ens.n_nodes[d]
+        for j in sorted({0, len(a) - 1}):
+            p, flags, f = oracle_run_node(O, wl, d, j, 27)
+            fg = gpu_state(ens, d, j)
+            fl = fluid_mask(flags)
+            assert np.max(np.abs(fg[:, fl] - f[:, fl])) < 2e-6
+    ens.close()
+
+
+def _states(ens):
+    return [gpu_state(ens, d, j) for d in range(len(ens.n_nodes)) for j in range(ens.n_nodes[d])]
+
+
+@pytest.mark.parametrize("shape", [(32, 1, 1, 0), (64, 4, 2, 1), (128, 2, 4, 0), (256, 1, 3, 1)])
+def test_launch_shapes_and_modes_are_bitwise_identical(cuda, shape):
+    wl = ragged(BC_SETS["urban"])
+    ref = S.Ensemble(S.make_config(wl))
+    ref.step(17)
+    want = _states(ref)
+    ref.close()
+    for mode in (S.SC_EXEC_LAUNCH, S.SC_EXEC_GRAPH, S.SC_EXEC_PERSISTENT):
+        ens = S.Ensemble(S.make_config(wl))
+        S.sc_lbm_set_tuning(ens.h, *shape, exec_mode=mode, graph_steps=4)
+        ens.step(17)
+        got = _states(ens)
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b), (shape, mode)
+        ens.sync()
+        ens.close()
+
+
+def test_les_full_size_100_steps(O, cuda):
+    """Synthetic urban LES at full size (256x128x64, BGK + Smagorinsky): the
+    first and last node after 100 steps, relative L2 of u <= 1e-3."""
+    wl = W.URBAN_LES
+    ens = S.Ensemble(S.make_config(wl))
+    S.sc_lbm_autotune(ens.h, None)
+    ens.step(100)
+    for j in (0, ens.n_nodes[0] - 1):
+        p, flags, f = oracle_run_node(O, wl, 0, j, 100)
+        _, uo = O.macros(p, flags, f)
+        ug = ens.velocity(0, j).cpu().numpy()
+        fl = fluid_mask(flags)
+        assert rel_l2(ug[:, fl], uo[:, fl]) <= 1e-3
+    ens.close()
+
+
+def test_full_size_single_step_from_exported_state(O, cuda):
+    """At full size and in the benchmark's launch shape, one GPU step from any
+    state equals one oracle step from the exported populations (both parities,
+    after the ramp has started so that every boundary carries flow)."""
+    wl = W.URBAN_LES
+    ens = S.Ensemble(S.make_config(wl))
+    S.sc_lbm_autotune(ens.h, None)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    fl = fluid_mask(flags)
+    ens.step(300)
+    for n in (300, 301):
+        j = n % len(a)
+        f0 = gpu_state(ens, 0, j)
+        ens.step(1)
+        f1 = gpu_state(ens, 0, j)
+        O.run(p, flags, oracle_uin(O, wl, 0, Z[j]), f0, n, 1)
+        assert np.max(np.abs(f1[:, fl] - f0[:, fl])) < 2e-6
+    ens.close()
+
+
+def test_ensemble_moments_match_exported_fields(O, cuda):
+    """Property at full size: the on-device FP64 reduction equals the oracle's
+    two-pass moments of the per-node |u| fields the GPU exports."""
+    wl = W.URBAN_LES
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(60)
+    cfg = S.make_config(wl)
+    Z, a = S.sc_lbm_quadrature(cfg, 0)
+    flags = S.sc_lbm_geometry(cfg, 0)
+    Qv = np.stack([np.sqrt((ens.velocity(0, j).double().cpu().numpy() ** 2).sum(0)) for j in range(len(a))])
+    Qv[:, flags != 0] = 0.0
+    mean, std, _ = O.moments_two_pass(a, Qv)
+    cols = S.sc_lbm_probe_columns(cfg, 0, 4)
+    out = ens.moments(0, probes=cols, gpc=True)
+    assert np.max(np.abs(out["mean"].cpu().numpy() - mean)) < 1e-12
+    assert np.max(np.abs(out["std"].cpu().numpy() - std)) < 1e-9
+    prof, _ = O.profiles(a, Qv, 256, 128, 64, cols)
+    assert np.max(np.abs(out["prof"].cpu().numpy() - prof)) < 1e-9
+    ens.close()
+
+
+def test_host_outputs_match_device_outputs(cuda):
+    wl = ragged(BC_SETS["urban"])
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(9)
+    dev = ens.moments(0, probes=[[30, 4]], nodes_profiles=True, gpc=True)
+    n = 37 * 19 * 13
+    mean, std = np.zeros(n), np.zeros(n)
+    prof, pn = np.zeros((1, 13, 4)), np.zeros((1, 3, 13), np.float32)
+    coef = np.zeros((3, n))
+    S.sc_lbm_moments(ens.h, 0, mean, std, [[30, 4]], prof, pn, coef, out_host=True)
+    assert np.array_equal(mean, dev["mean"].cpu().numpy())
+    assert np.array_equal(std, dev["std"].cpu().numpy())
+    assert np.array_equal(prof, dev["prof"].cpu().numpy())
+    assert np.array_equal(pn, dev["prof_nodes"].cpu().numpy())
+    assert np.array_equal(coef, dev["coef"].cpu().numpy())
+    ens.close()
+
+
+def test_bounded_barrier_wait_times_out_and_recovers(cuda):
+    """A grid-barrier arrival that never comes: the wait gives up after its
+    poll limit, the call reports SC_ERR_TIMEOUT and the device stays usable."""
+    wl = ragged(BC_SETS["urban"])
+    ens = S.Ensemble(S.make_config(wl))
+    S.sc_lbm_set_tuning(ens.h, 64, 2, 1, exec_mode=S.SC_EXEC_PERSISTENT)
+    S.sc_lbm_debug_barrier(ens.h, 1, 20000)
+    ens.step(3)
+    with pytest.raises(S.ScError) as ei:
+        ens.sync()
+    assert ei.value.code == S.SC_ERR_TIMEOUT
+    S.sc_lbm_debug_barrier(ens.h, 0, 1 << 26)
+    S.sc_lbm_reset(ens.h)
+    ens.step(5)
+    ens.sync()
+    ref = S.Ensemble(S.make_config(wl))
+    ref.step(5)
+    assert np.array_equal(gpu_state(ens, 0, 0), gpu_state(ref, 0, 0))
+    ens.close()
+    ref.close()
+
+
+def test_non_finite_state_is_detected(cuda):
+    """Host-side fault injection: a NaN written into one population is
+    reported by sc_lbm_check and by the moments reduction."""
+    wl = ragged(BC_SETS["urban"])
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(4)
+    rc, nbad = S.sc_lbm_check(ens.h)
+    assert rc == S.SC_OK and nbad == 0
+    # locate node 1's populations inside the workspace via an exported copy
+    f = ens.populations(0, 1)
+    ws = ens.ws.view(torch.uint8)
+    ens.stream.synchronize()
+    # poison: overwrite the whole state region of the domain by scanning for it
+    S.sc_lbm_step(ens.h, 1)
+    torch.cuda.synchronize()
+    # inject through a snapshot: save, corrupt one value, load
+    buf = np.zeros(S.sc_lbm_state_size(ens.h), np.uint8)
+    S.sc_lbm_save(ens.h, buf)
+    hdr = 48
+    vals = buf[hdr:].view(np.float32)
+    vals[19 * 37 * 19 * 13 + 1234] = np.nan
+    with pytest.raises(S.ScError):      # checksum catches the corrupted snapshot
+        S.sc_lbm_load(ens.h, buf)
+    # a consistent snapshot with a NaN: recompute the checksum through a reload
+    import ctypes
+    payload = buf[hdr:].tobytes()
+    h = 1469598103934665603
+    for byte in payload:
+        h ^= byte
+        h = (h * 1099511628211) & ((1 << 64) - 1)
+    buf[24:32] = np.frombuffer(np.uint64(h).tobytes(), np.uint8)
+    S.sc_lbm_load(ens.h, buf)
+    rc, nbad = S.sc_lbm_check(ens.h)
+    assert rc == S.SC_ERR_DIVERGED and nbad >= 1
+    with pytest.raises(S.ScError) as ei:
+        S.sc_lbm_moments(ens.h, 0, np.zeros(37 * 19 * 13), np.zeros(37 * 19 * 13), out_host=True)
+    assert ei.value.code == S.SC_ERR_DIVERGED
+    ens.close()
+
+
+def test_save_load_resume(cuda):
+    wl = ragged(BC_SETS["urban"])
+    a = S.Ensemble(S.make_config(wl))
+    a.step(7)
+    buf = np.zeros(S.sc_lbm_state_size(a.h), np.uint8)
+    S.sc_lbm_save(a.h, buf)
+    a.step(6)
+    want = _states(a)
+    b = S.Ensemble(S.make_config(wl))
+    S.sc_lbm_load(b.h, buf)
+    assert S.sc_lbm_counters(b.h)[0] == 7
+    b.step(6)
+    for x, y in zip(_states(b), want):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
