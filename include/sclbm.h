@@ -119,9 +119,9 @@ typedef struct {
 } sc_lbm_config;
 
 /* Launch shape of the stream-collide kernels (chosen by sc_lbm_autotune or
- * set by the caller).  block_x (multiple of 32) by block_y threads cover a
- * block_x * block_y patch of an x-y plane; each thread walks slab_z cells in
- * z.  tile_order 0 runs the nodes of one patch back to back (shared geometry
+ * set by the caller).  block_x (multiple of 32) by block_y threads, at most
+ * 256, cover a block_x * block_y patch of an x-y plane; each thread walks
+ * slab_z cells in z.  tile_order 0 runs the nodes of one patch back to back (shared geometry
  * stays in L2), 1 runs all patches of one node first.  graph_steps: time
  * steps per captured graph (SC_EXEC_GRAPH).                                 */
 typedef struct {

@@ -35,7 +35,7 @@ size_t storage_bytes(int precision) {
 struct DomLayout {
   int nq = 0, P = 0;
   long long ncell = 0;
-  size_t flags = 0, link = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
+  size_t flags = 0, link = 0, bcell = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
 };
 struct Layout {
   size_t hdr = 0, ramp_f = 0, ramp_d = 0, probes = 0;
@@ -80,7 +80,10 @@ int validate(const sc_lbm_config* c, std::string& why) {
   for (int d = 0; d < c->n_domains; ++d) {
     const sc_domain_desc& D = c->domains[d];
     if (D.nx < 1 || D.ny < 1 || D.nz < 1) { why = "domain sizes must be positive"; return SC_ERR_ARG; }
-    if ((long long)D.nx * D.ny * D.nz > (1LL << 31)) { why = "domain too large"; return SC_ERR_UNSUPPORTED; }
+    if ((long long)D.nx * D.ny * D.nz * 19 >= (1LL << 31)) {
+      why = "domain too large (19 populations per node must stay below 2^31)";
+      return SC_ERR_UNSUPPORTED;
+    }
     for (int a = 0; a < 3; ++a) {
       const bool lo = D.bc[2 * a] == SC_BC_PERIODIC, hi = D.bc[2 * a + 1] == SC_BC_PERIODIC;
       if (lo != hi) { why = "periodic faces come in pairs"; return SC_ERR_ARG; }
@@ -133,6 +136,7 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     M.ncell = (long long)D.nx * D.ny * D.nz;
     M.flags = take((size_t)M.ncell);
     M.link = take(sizeof(uint32_t) * (size_t)M.ncell);
+    M.bcell = take(sizeof(int32_t) * (size_t)M.ncell);  // boundary list, at most every cell
     M.uin_f = take(16 * (size_t)M.nq * D.nz);
     M.uin_d = take(24 * (size_t)M.nq * D.nz);
     M.g = take(sb * kQ * (size_t)M.ncell * M.nq);
@@ -275,7 +279,7 @@ void apply_tiling(sc_lbm_t h) {
   P.by = h->tune.block_y;
   P.bz = h->tune.slab_z;
   P.order = h->tune.tile_order;
-  long long begin = 0;
+  long long begin = 0, bbegin = 0;
   for (int d = 0; d < P.n_domains; ++d) {
     DevDomain& D = P.dom[d];
     D.tiles_x = (D.nx + P.bx - 1) / P.bx;
@@ -284,8 +288,11 @@ void apply_tiling(sc_lbm_t h) {
     D.tiles_per_node = D.tiles_x * D.tiles_y * D.tiles_z;
     D.tile_begin = begin;
     begin += D.tiles_per_node * D.nodes;
+    D.bitem_begin = bbegin;
+    bbegin += D.nb * D.nodes;
   }
   P.total_tiles = begin;
+  P.total_bitems = bbegin;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -295,7 +302,8 @@ void apply_tiling(sc_lbm_t h) {
 }
 
 int check_tuning(const sc_lbm_tuning& t) {
-  if (t.block_x < 32 || t.block_x % 32 || t.block_y < 1 || t.block_x * t.block_y > 1024) return SC_ERR_ARG;
+  // the step kernels are compiled for at most 256 threads per block
+  if (t.block_x < 32 || t.block_x % 32 || t.block_y < 1 || t.block_x * t.block_y > 256) return SC_ERR_ARG;
   if (t.slab_z < 1 || t.slab_z > 4096) return SC_ERR_ARG;
   if (t.tile_order < 0 || t.tile_order > 1) return SC_ERR_ARG;
   if (t.exec_mode < SC_EXEC_LAUNCH || t.exec_mode > SC_EXEC_PERSISTENT) return SC_ERR_ARG;
@@ -312,28 +320,36 @@ int reset_state(sc_lbm_t h) {
   return SC_OK;
 }
 
-// n steps with one launch each
-int run_launches(sc_lbm_t h, int n) {
-  const int grid = (int)h->P.total_tiles;
+// n steps with one launch each, starting at time level `start`
+int run_launches(sc_lbm_t h, long long start, int n) {
   for (int s = 0; s < n; ++s) {
-    int rc = launch_aa_step(h->P, h->cfg.precision, h->stream, grid);
+    const int parity = (int)((start + s) & 1);
+    int rc = launch_aa_step(h->P, h->cfg.precision, h->stream, parity);
     if (rc) return cuda_fail(h, (cudaError_t)rc, "aa_step launch");
-    ++h->launches;
+    h->launches += parity ? 2 : 1;  // odd levels: bulk + boundary kernels
   }
   return SC_OK;
 }
 
+// Replays of a captured graph of G steps (even/odd pairs, G even) starting
+// at an even time level.
 int run_graph(sc_lbm_t h, int n) {
-  const int G = h->tune.graph_steps;
-  if (!h->stream) return run_launches(h, n);  // capture needs a non-default stream
+  const int G = h->tune.graph_steps + (h->tune.graph_steps & 1);
+  if (!h->stream) return run_launches(h, h->steps, n);  // capture needs a non-default stream
+  long long t = h->steps;
+  if (t & 1) {
+    int rc = run_launches(h, t, 1);
+    if (rc) return rc;
+    ++t;
+    --n;
+  }
   if (!h->graph || h->graph_len != G) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
-    for (int s = 0; s < G && !rc; ++s)
-      rc = launch_aa_step(h->P, h->cfg.precision, h->stream, (int)h->P.total_tiles);
+    for (int s = 0; s < G && !rc; ++s) rc = launch_aa_step(h->P, h->cfg.precision, h->stream, s & 1);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
       if (g) cudaGraphDestroy(g);
@@ -348,9 +364,9 @@ int run_graph(sc_lbm_t h, int n) {
   const int reps = n / G;
   for (int r = 0; r < reps; ++r) {
     CK(cudaGraphLaunch(h->graph, h->stream));
-    h->launches += G;
+    h->launches += G + G / 2;  // G/2 odd levels of two kernels each
   }
-  return run_launches(h, n - reps * G);
+  return run_launches(h, t + (long long)reps * G, n - reps * G);
 }
 
 int run_persistent(sc_lbm_t h, int n) {
@@ -400,7 +416,7 @@ int do_steps(sc_lbm_t h, int n) {
   if (h->cfg.precision == SC_P_FP64_PLAIN) rc = run_plain(h, n);
   else if (h->tune.exec_mode == SC_EXEC_GRAPH) rc = run_graph(h, n);
   else if (h->tune.exec_mode == SC_EXEC_PERSISTENT) rc = run_persistent(h, n);
-  else rc = run_launches(h, n);
+  else rc = run_launches(h, h->steps, n);
   if (rc == SC_OK) h->steps += n;
   return rc;
 }
@@ -530,6 +546,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   // host tables (kept alive until the stream is synchronised below)
   std::vector<std::vector<uint8_t>> flags(c.n_domains);
   std::vector<std::vector<uint32_t>> links(c.n_domains);
+  std::vector<std::vector<int32_t>> bcells(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
   std::vector<float> rampf(c.ramp_steps + 1);
@@ -551,6 +568,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
       if (rc) { delete h; return rc; }
     }
     hn_link_words(D, flags[d].data(), links[d]);
+    hn_boundary_cells(links[d], bcells[d]);
     std::vector<double> Z, w;
     node_count(&c, d, &Z, &w);
     const int nq = (int)w.size();
@@ -592,6 +610,8 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     for (int f = 0; f < 6; ++f) V.bc[f] = D.bc[f];
     V.flags = (const uint8_t*)(h->ws + M.flags);
     V.link = (const uint32_t*)(h->ws + M.link);
+    V.bcell = (const int32_t*)(h->ws + M.bcell);
+    V.nb = (long long)bcells[d].size();
     V.uin_f = (const float4*)(h->ws + M.uin_f);
     V.uin_d = (const double*)(h->ws + M.uin_d);
     V.g = h->ws + M.g;
@@ -617,6 +637,8 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     const DomLayout& M = L.dom[d];
     e = up(M.flags, flags[d].data(), flags[d].size());
     if (e == cudaSuccess) e = up(M.link, links[d].data(), sizeof(uint32_t) * links[d].size());
+    if (e == cudaSuccess && !bcells[d].empty())
+      e = up(M.bcell, bcells[d].data(), sizeof(int32_t) * bcells[d].size());
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
     if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
     if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());
@@ -750,14 +772,14 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   int maxnx = 0;
   for (int d = 0; d < h->P.n_domains; ++d) maxnx = std::max(maxnx, h->P.dom[d].nx);
   std::vector<sc_lbm_tuning> cand;
-  const int bxs[] = {32, 64, 128, 256, 512};
+  const int bxs[] = {32, 64, 128, 256};
   const int bys[] = {1, 2, 4, 8};
   const int bzs[] = {1, 2, 4};
   for (int bx : bxs) {
     if (bx > 32 && bx / 2 >= maxnx) continue;
     for (int by : bys)
       for (int bz : bzs) {
-        if (bx * by > 512 || bx * by < 64) continue;
+        if (bx * by > 256 || bx * by < 64) continue;
         for (int order = 0; order < 2; ++order) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50});
       }
   }

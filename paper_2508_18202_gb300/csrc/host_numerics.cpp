@@ -339,6 +339,14 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<ui
       }
 }
 
+// Fluid cells that need the boundary path of the odd AA level: any link
+// whose source is not a plain in-domain fluid cell, or a cell on the outlet.
+void hn_boundary_cells(const std::vector<uint32_t>& link, std::vector<int32_t>& cells) {
+  cells.clear();
+  for (size_t c = 0; c < link.size(); ++c)
+    if (!(link[c] & kLinkSolid) && (link[c] & (kLinkMask | kLinkOutlet))) cells.push_back((int32_t)c);
+}
+
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin) {
   const double theta = theta_deg * M_PI / 180.0;

@@ -237,7 +237,7 @@ __device__ __forceinline__ T vel_term(const Node<S>& N, int i, int z, T r) {
 
 // f_i of time level n (odd, AA swapped layout) for a boundary link.
 template <class S, bool CG>
-__device__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
+__device__ __forceinline__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
                                              int y, int z, long long idx,
                                              typename Store<S>::C r) {
   using T = typename Store<S>::C;
@@ -278,7 +278,7 @@ __device__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& 
 
 // Deliver f*_j of cell x for a boundary link into dst (AA: dst == src array).
 template <class S>
-__device__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
+__device__ __forceinline__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
                              typename Store<S>::C v, int x, int y, int z, long long idx,
                              typename Store<S>::C r1) {
   using T = typename Store<S>::C;
@@ -323,7 +323,7 @@ __device__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j
 // Outlet cell (x = nx-1, +x OUTFLOW): deliver f*_j (c_jx = -1) to the outlet
 // links that read it.
 template <class S>
-__device__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x,
+__device__ __forceinline__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x,
                             int y, int z, long long idx) {
   const long long nc = D.ncell;
   // (1) transverse neighbour on the outlet plane copies it
@@ -371,7 +371,18 @@ __device__ __forceinline__ void load_odd(const DevDomain& D, const Node<S>& N, u
   }
 }
 
-template <class S, bool CG, bool SHIFT>
+template <class T, bool SHIFT>
+__device__ __forceinline__ void collide_p(const StepParams& P, T g[kQ]) {
+  if constexpr (sizeof(T) == 8)
+    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
+  else
+    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+}
+
+// Even time level: every fluid cell reads its own 19 slots and writes the
+// post-collision populations to the opposite slots; outlet cells also save
+// their five populations with c_x = -1 into the outflow plane.
+template <class S, bool CG>
 __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& D,
                                           const Node<S>& N, uint32_t lw, int y, int z,
                                           long long idx) {
@@ -380,10 +391,7 @@ __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& 
   T g[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(N.g + (long long)i * nc + idx);
-  if constexpr (sizeof(T) == 8)
-    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
-  else
-    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+  collide_p<T, true>(P, g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) Store<S>::st(N.g + (long long)OPP(i) * nc + idx, g[i]);
   if (lw & kLinkOutlet) {
@@ -396,7 +404,28 @@ __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& 
   }
 }
 
-template <class S, bool CG, bool SHIFT>
+// Odd time level, cell whose 19 links all stream between in-domain fluid
+// cells: branch-free pull from the upstream neighbours, collide, push to the
+// downstream neighbours.
+template <class S, bool CG>
+__device__ __forceinline__ void cell_odd_bulk(const StepParams& P, const DevDomain& D,
+                                              const Node<S>& N, long long idx) {
+  using T = typename Store<S>::C;
+  // 32-bit element offsets from the cell's own slot 0 (one node holds fewer
+  // than 2^31 populations, checked at init)
+  const int nc = (int)D.ncell;
+  const int sy = D.nx, sz = D.nx * D.ny;
+  S* base = N.g + idx;
+  T g[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(base + (OPP(i) * nc - (CX(i) + CY(i) * sy + CZ(i) * sz)));
+  collide_p<T, true>(P, g);
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * nc + (CX(j) + CY(j) * sy + CZ(j) * sz)), g[j]);
+}
+
+// Odd time level, boundary cell: the general per-link rules.
+template <class S, bool CG>
 __device__ __forceinline__ void cell_odd(const StepParams& P, const DevDomain& D,
                                          const Node<S>& N, uint32_t lw, int x, int y, int z,
                                          long long idx, typename Store<S>::C r,
@@ -405,11 +434,8 @@ __device__ __forceinline__ void cell_odd(const StepParams& P, const DevDomain& D
   const long long nc = D.ncell;
   const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
   T g[kQ];
-  load_odd<S, CG, SHIFT>(D, N, lw, x, y, z, idx, g, r);
-  if constexpr (sizeof(T) == 8)
-    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
-  else
-    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+  load_odd<S, CG, true>(D, N, lw, x, y, z, idx, g, r);
+  collide_p<T, true>(P, g);
 #pragma unroll
   for (int j = 0; j < kQ; ++j) {
     if (!(lw & (1u << OPP(j)))) {
@@ -429,13 +455,6 @@ __device__ __forceinline__ void cell_odd(const StepParams& P, const DevDomain& D
 }
 
 // ------------------------------------------------------------ step driver
-__device__ __forceinline__ int find_domain(const StepParams& P, long long t) {
-  int d = 0;
-  for (int k = 1; k < P.n_domains; ++k)
-    if (t >= P.dom[k].tile_begin) d = k;
-  return d;
-}
-
 template <class S>
 __device__ __forceinline__ Node<S> node_view(const DevDomain& D, int node) {
   Node<S> N;
@@ -446,39 +465,85 @@ __device__ __forceinline__ Node<S> node_view(const DevDomain& D, int node) {
   return N;
 }
 
-template <class S, bool CG>
-__device__ __forceinline__ void process_tile(const StepParams& P, long long t, unsigned long long n,
-                                             float r, float r1) {
-  using T = typename Store<S>::C;
-  const int d = find_domain(P, t);
+// A tile is a block_x * block_y patch of one x-y plane range, slab_z deep,
+// of one node of one domain.
+struct TileRef {
+  int d, node, x, y, z0, z1;
+  bool valid;
+};
+
+__device__ __forceinline__ TileRef decode_tile(const StepParams& P, long long t) {
+  TileRef R;
+  int d = 0;
+  for (int k = 1; k < P.n_domains; ++k)
+    if (t >= P.dom[k].tile_begin) d = k;
   const DevDomain& D = P.dom[d];
   const long long local = t - D.tile_begin;
-  int node;
   long long ct;
   if (P.order == 0) {
-    node = (int)(local % D.nodes);
+    R.node = (int)(local % D.nodes);
     ct = local / D.nodes;
   } else {
-    node = (int)(local / D.tiles_per_node);
+    R.node = (int)(local / D.tiles_per_node);
     ct = local % D.tiles_per_node;
   }
   const int tx = (int)(ct % D.tiles_x);
   const int ty = (int)((ct / D.tiles_x) % D.tiles_y);
   const int tz = (int)(ct / (D.tiles_x * D.tiles_y));
-  const int x = tx * P.bx + threadIdx.x;
-  const int y = ty * P.by + threadIdx.y;
-  if (x >= D.nx || y >= D.ny) return;
-  const Node<S> N = node_view<S>(D, node);
-  const int z0 = tz * P.bz;
-  const int z1 = min(z0 + P.bz, D.nz);
-  const bool odd = (n & 1ull) != 0;
-  for (int z = z0; z < z1; ++z) {
-    const long long idx = cidx(D, x, y, z);
+  R.d = d;
+  R.x = tx * P.bx + threadIdx.x;
+  R.y = ty * P.by + threadIdx.y;
+  R.z0 = tz * P.bz;
+  R.z1 = min(R.z0 + P.bz, D.nz);
+  R.valid = R.x < D.nx && R.y < D.ny;
+  return R;
+}
+
+template <class S, bool CG>
+__device__ __forceinline__ void even_tile(const StepParams& P, long long t) {
+  const TileRef R = decode_tile(P, t);
+  if (!R.valid) return;
+  const DevDomain& D = P.dom[R.d];
+  const Node<S> N = node_view<S>(D, R.node);
+  for (int z = R.z0; z < R.z1; ++z) {
+    const long long idx = cidx(D, R.x, R.y, z);
     const uint32_t lw = __ldg(D.link + idx);
     if (lw & kLinkSolid) continue;
-    if (!odd) cell_even<S, CG, true>(P, D, N, lw, y, z, idx);
-    else cell_odd<S, CG, true>(P, D, N, lw, x, y, z, idx, T(r), T(r1));
+    cell_even<S, CG>(P, D, N, lw, R.y, z, idx);
   }
+}
+
+template <class S, bool CG>
+__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, long long t) {
+  const TileRef R = decode_tile(P, t);
+  if (!R.valid) return;
+  const DevDomain& D = P.dom[R.d];
+  const Node<S> N = node_view<S>(D, R.node);
+  for (int z = R.z0; z < R.z1; ++z) {
+    const long long idx = cidx(D, R.x, R.y, z);
+    if (__ldg(D.link + idx) != 0u) continue;   // solid, boundary or outlet cell
+    cell_odd_bulk<S, CG>(P, D, N, idx);
+  }
+}
+
+// Boundary cells of the odd level: one thread per (node, listed cell).
+template <class S, bool CG>
+__device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long item, float r,
+                                                  float r1) {
+  using T = typename Store<S>::C;
+  if (item >= P.total_bitems) return;
+  int d = 0;
+  for (int k = 1; k < P.n_domains; ++k)
+    if (item >= P.dom[k].bitem_begin) d = k;
+  const DevDomain& D = P.dom[d];
+  const long long k = item - D.bitem_begin;
+  const int node = (int)(k / D.nb);
+  const long long idx = __ldg(D.bcell + (k % D.nb));
+  const int x = (int)(idx % D.nx);
+  const int y = (int)((idx / D.nx) % D.ny);
+  const int z = (int)(idx / ((long long)D.nx * D.ny));
+  const uint32_t lw = __ldg(D.link + idx);
+  cell_odd<S, CG>(P, D, node_view<S>(D, node), lw, x, y, z, idx, T(r), T(r1));
 }
 
 __device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long m) {
@@ -486,16 +551,15 @@ __device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long
   return P.ramp_f[k];
 }
 
-// One time step for every (domain, node, tile); the time level comes from
-// the device counter so that a captured graph replays without new
-// parameters.  The last block to finish advances the counter.
-template <class S>
-__global__ void aa_step_kernel(const __grid_constant__ StepParams P) {
+__device__ __forceinline__ unsigned long long begin_step(const StepParams& P) {
   __shared__ unsigned long long s_n;
   if (threadIdx.x == 0 && threadIdx.y == 0) s_n = *reinterpret_cast<volatile unsigned long long*>(P.step);
   __syncthreads();
-  const unsigned long long n = s_n;
-  process_tile<S, false>(P, blockIdx.x, n, ramp_at(P, n), ramp_at(P, n + 1));
+  return s_n;
+}
+
+// The last block to finish advances the device time-level counter.
+__device__ __forceinline__ void end_step(const StepParams& P, unsigned long long n) {
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     __threadfence();
@@ -506,6 +570,33 @@ __global__ void aa_step_kernel(const __grid_constant__ StepParams P) {
       __threadfence();
     }
   }
+}
+
+// Even time level for every (domain, node, tile).  The time level comes from
+// the device counter so that a captured graph replays without new
+// parameters.
+template <class S>
+__global__ void __launch_bounds__(256, 4) aa_even_kernel(const __grid_constant__ StepParams P) {
+  const unsigned long long n = begin_step(P);
+  even_tile<S, false>(P, blockIdx.x);
+  end_step(P, n);
+}
+
+// Odd time level, bulk cells of every tile.  Needs no time level: the bulk
+// links carry no boundary term.
+template <class S>
+__global__ void __launch_bounds__(256, 4) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
+  odd_bulk_tile<S, false>(P, blockIdx.x);
+}
+
+// Odd time level, listed boundary cells (launched after the bulk kernel of the
+// same level; the two touch disjoint slots).  Advances the time level.
+template <class S>
+__global__ void __launch_bounds__(256) aa_odd_boundary_kernel(const __grid_constant__ StepParams P) {
+  const unsigned long long n = begin_step(P);
+  const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
+  odd_boundary_item<S, false>(P, item, ramp_at(P, n), ramp_at(P, n + 1));
+  end_step(P, n);
 }
 
 // Bounded grid barrier (sense by generation).  Gives up after spin_limit
@@ -543,9 +634,9 @@ __device__ bool grid_barrier(const StepParams& P, unsigned int& gen) {
 }
 
 // Persistent form: one cooperative launch advances n_steps; blocks stride over
-// the tiles and meet at a grid barrier between time steps.
+// the work of each level and meet at a grid barrier between time steps.
 template <class S>
-__global__ void aa_persistent_kernel(const __grid_constant__ StepParams P) {
+__global__ void __launch_bounds__(256) aa_persistent_kernel(const __grid_constant__ StepParams P) {
   __shared__ unsigned long long s_n;
   __shared__ unsigned int s_gen;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -555,32 +646,64 @@ __global__ void aa_persistent_kernel(const __grid_constant__ StepParams P) {
   __syncthreads();
   unsigned long long n = s_n;
   unsigned int gen = s_gen;
+  const long long threads = (long long)P.bx * P.by;
+  const long long bblocks = (P.total_bitems + threads - 1) / threads;
   for (int s = 0; s < P.n_steps; ++s) {
-    const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
-    for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x)
-      process_tile<S, true>(P, t, n, r, r1);
+    if ((n & 1ull) == 0) {
+      for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) even_tile<S, true>(P, t);
+    } else {
+      const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
+      for (long long b = blockIdx.x; b < P.total_tiles + bblocks; b += gridDim.x) {
+        if (b < P.total_tiles) odd_bulk_tile<S, true>(P, b);
+        else odd_boundary_item<S, true>(P, (b - P.total_tiles) * threads + threadIdx.y * P.bx + threadIdx.x, r, r1);
+      }
+    }
     if (!grid_barrier(P, gen)) return;
     ++n;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *P.step = n;
 }
 
-// FP64 plain path: two arrays, push form, one node per launch.
-__global__ void plain_step_kernel(const __grid_constant__ StepParams P, unsigned long long n) {
+// FP64 plain path: two arrays, push form, one node per launch.  Blocks
+// [0, tiles_per_node) take the bulk cells, the rest the listed boundary cells.
+__global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__ StepParams P,
+                                                         unsigned long long n) {
   const DevDomain& D = P.dom[P.plain_domain];
-  const long long ct = blockIdx.x;
-  const int tx = (int)(ct % D.tiles_x);
-  const int ty = (int)((ct / D.tiles_x) % D.tiles_y);
-  const int tz = (int)(ct / (D.tiles_x * D.tiles_y));
-  const int x = tx * P.bx + threadIdx.x;
-  const int y = ty * P.by + threadIdx.y;
-  if (x >= D.nx || y >= D.ny) return;
   const int node = P.plain_node;
   const long long nc = D.ncell;
   double* A = reinterpret_cast<double*>(D.g) + (long long)node * kQ * nc;
   double* B = reinterpret_cast<double*>(D.g2) + (long long)node * kQ * nc;
   const double* src = (n & 1ull) ? B : A;
   double* dst = (n & 1ull) ? A : B;
+  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
+  const long long b = blockIdx.x;
+  if (b < D.tiles_per_node) {
+    const int tx = (int)(b % D.tiles_x);
+    const int ty = (int)((b / D.tiles_x) % D.tiles_y);
+    const int tz = (int)(b / (D.tiles_x * D.tiles_y));
+    const int x = tx * P.bx + threadIdx.x;
+    const int y = ty * P.by + threadIdx.y;
+    if (x >= D.nx || y >= D.ny) return;
+    const int z0 = tz * P.bz, z1 = min(z0 + P.bz, D.nz);
+    for (int z = z0; z < z1; ++z) {
+      const long long idx = cidx(D, x, y, z);
+      if (__ldg(D.link + idx) != 0u) continue;
+      double g[kQ];
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
+      collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) dst[(long long)j * nc + idx + (CX(j) * sx + CY(j) * sy + CZ(j) * sz)] = g[j];
+    }
+    return;
+  }
+  const long long item = (b - D.tiles_per_node) * (long long)(P.bx * P.by) + threadIdx.y * P.bx + threadIdx.x;
+  if (item >= D.nb) return;
+  const long long idx = __ldg(D.bcell + item);
+  const int x = (int)(idx % D.nx);
+  const int y = (int)((idx / D.nx) % D.ny);
+  const int z = (int)(idx / ((long long)D.nx * D.ny));
+  const uint32_t lw = __ldg(D.link + idx);
   Node<double> N;
   N.g = dst;
   N.bout = nullptr;
@@ -588,32 +711,25 @@ __global__ void plain_step_kernel(const __grid_constant__ StepParams P, unsigned
   N.uind = D.uin_d + (long long)node * D.nz * 3;
   const unsigned long long m1 = n + 1;
   const double r1 = P.ramp_d[m1 < (unsigned long long)P.ramp_steps ? m1 : P.ramp_steps];
-  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
-  const int z0 = tz * P.bz, z1 = min(z0 + P.bz, D.nz);
-  for (int z = z0; z < z1; ++z) {
-    const long long idx = cidx(D, x, y, z);
-    const uint32_t lw = __ldg(D.link + idx);
-    if (lw & kLinkSolid) continue;
-    double g[kQ];
+  double g[kQ];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
-    collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
+  for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
+  collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
 #pragma unroll
-    for (int j = 0; j < kQ; ++j) {
-      if (!(lw & (1u << OPP(j)))) {
-        const long long off = CX(j) * sx + CY(j) * sy + CZ(j) * sz;
-        dst[(long long)j * nc + idx + off] = g[j];
-      } else {
-        push_special<double>(D, N, dst, j, g[j], x, y, z, idx, r1);
-      }
+  for (int j = 0; j < kQ; ++j) {
+    if (!(lw & (1u << OPP(j)))) {
+      const long long off = CX(j) * sx + CY(j) * sy + CZ(j) * sz;
+      dst[(long long)j * nc + idx + off] = g[j];
+    } else {
+      push_special<double>(D, N, dst, j, g[j], x, y, z, idx, r1);
     }
-    if (lw & kLinkOutlet) {
-      push_outlet<double>(D, dst, 2, g[2], x, y, z, idx);
-      push_outlet<double>(D, dst, 8, g[8], x, y, z, idx);
-      push_outlet<double>(D, dst, 10, g[10], x, y, z, idx);
-      push_outlet<double>(D, dst, 12, g[12], x, y, z, idx);
-      push_outlet<double>(D, dst, 14, g[14], x, y, z, idx);
-    }
+  }
+  if (lw & kLinkOutlet) {
+    push_outlet<double>(D, dst, 2, g[2], x, y, z, idx);
+    push_outlet<double>(D, dst, 8, g[8], x, y, z, idx);
+    push_outlet<double>(D, dst, 10, g[10], x, y, z, idx);
+    push_outlet<double>(D, dst, 12, g[12], x, y, z, idx);
+    push_outlet<double>(D, dst, 14, g[14], x, y, z, idx);
   }
 }
 
@@ -859,14 +975,20 @@ int dispatch(int precision, F&& f) {
 }  // namespace
 
 // ======================================================================= launchers
-int launch_aa_step(const StepParams& P, int precision, void* stream, int grid) {
+int launch_aa_step(const StepParams& P, int precision, void* stream, int parity) {
   dim3 block(P.bx, P.by);
   cudaStream_t s = (cudaStream_t)stream;
   return dispatch(precision, [&](auto tag) -> int {
     using S = std::remove_pointer_t<decltype(tag)>;
     if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
     else {
-      aa_step_kernel<S><<<grid, block, 0, s>>>(P);
+      if (parity == 0) {
+        aa_even_kernel<S><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+      } else {
+        aa_odd_bulk_kernel<S><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+        const long long grid = (P.total_bitems + 255) / 256;
+        aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
+      }
       return (int)cudaGetLastError();
     }
   });
@@ -904,8 +1026,10 @@ int launch_plain_step(const StepParams& P, unsigned long long n, void* stream) {
   const DevDomain& D = P.dom[P.plain_domain];
   dim3 block(P.bx, P.by);
   cudaStream_t s = (cudaStream_t)stream;
+  const long long threads = (long long)P.bx * P.by;
+  const long long grid = D.tiles_per_node + (D.nb + threads - 1) / threads;
   // the time level of the plain path is tracked on the host
-  plain_step_kernel<<<(unsigned)D.tiles_per_node, block, 0, s>>>(P, n);
+  plain_step_kernel<<<(unsigned)grid, block, 0, s>>>(P, n);
   return (int)cudaGetLastError();
 }
 

@@ -40,8 +40,11 @@ struct DevDomain {
   void* g;                  // [nodes][19][ncell] storage (AA) or FP64 array A
   void* g2;                 // FP64 plain: array B, else null
   float* bout;              // [nodes][nz*ny][5] outflow plane (AA only)
+  const int32_t* bcell;     // [nb] fluid cells with a boundary link or on the outlet
+  long long nb;
   long long tiles_x, tiles_y, tiles_z, tiles_per_node;
   long long tile_begin;     // first global tile of this domain
+  long long bitem_begin;    // first global boundary item (node-major) of this domain
 };
 
 struct StepParams {
@@ -57,7 +60,8 @@ struct StepParams {
   unsigned long long* step;   // device step counter (time level of the state)
   unsigned int* done;         // blocks finished in the current launch
   unsigned int* err;          // latched error bits
-  long long total_tiles;
+  long long total_tiles;       // bulk tiles of all domains and nodes
+  long long total_bitems;      // boundary (node, cell) items of all domains
   int bx, by, bz, order;
   // persistent mode
   unsigned int* bar_count;
@@ -77,6 +81,7 @@ int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags);
 int hn_probe_columns(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xy);
 int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xyz);
 void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<uint32_t>& link);
+void hn_boundary_cells(const std::vector<uint32_t>& link, std::vector<int32_t>& cells);
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin /*[nz][3]*/);
 int hn_gpc_size(int d, int degree);
@@ -85,7 +90,7 @@ double hn_ramp(int ramp_steps, long long m);
 
 // ------------------------------------------------------------ kernel launchers
 // Implemented in lbm_kernels.cu.  All return cudaError_t as int.
-int launch_aa_step(const StepParams& P, int precision, void* stream, int grid);
+int launch_aa_step(const StepParams& P, int precision, void* stream, int parity);
 int launch_aa_persistent(const StepParams& P, int precision, void* stream, int grid);
 int launch_plain_step(const StepParams& P, unsigned long long n, void* stream);
 int launch_set_counter(unsigned long long* p, unsigned long long v, void* stream);
