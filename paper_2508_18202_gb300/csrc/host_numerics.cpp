@@ -313,6 +313,11 @@ int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_
   return SC_OK;
 }
 
+// Per-cell link word: bit i when the pull source x - c_i of direction i is not
+// an in-domain fluid cell reached without a periodic wrap; kLinkComplex when
+// one of those links resolves to anything but plain bounce-back (a solid
+// source, a BOUNCE_BACK face, two faces one of which is BOUNCE_BACK, or two
+// FREE_SLIP faces, whose double reflection is bounce-back).
 void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<uint32_t>& link) {
   const long long n = (long long)D.nx * D.ny * D.nz;
   link.assign((size_t)n, 0u);
@@ -321,30 +326,56 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<ui
     for (int y = 0; y < D.ny; ++y)
       for (int x = 0; x < D.nx; ++x) {
         const size_t c = (size_t)x + (size_t)D.nx * ((size_t)y + (size_t)D.ny * z);
-        uint32_t word = 0;
         if (flags[c]) {
           link[c] = kLinkSolid;
           continue;
         }
+        uint32_t word = 0;
+        bool complex_link = false;
         for (int i = 0; i < kQ; ++i) {
-          const int p[3] = {x - kCx[i], y - kCy[i], z - kCz[i]};
-          bool special = false;
-          for (int a = 0; a < 3; ++a)
-            if (p[a] < 0 || p[a] >= dims[a]) special = true;
-          if (!special) special = flags[(size_t)p[0] + (size_t)D.nx * ((size_t)p[1] + (size_t)D.ny * p[2])] != 0;
-          if (special) word |= 1u << i;
+          int p[3] = {x - kCx[i], y - kCy[i], z - kCz[i]};
+          int faces[3], nf = 0;
+          bool wrapped = false;
+          for (int a = 0; a < 3; ++a) {
+            if (p[a] >= 0 && p[a] < dims[a]) continue;
+            if (D.bc[2 * a] == SC_BC_PERIODIC) {
+              p[a] = (p[a] + dims[a]) % dims[a];
+              wrapped = true;
+            } else {
+              faces[nf++] = 2 * a + (p[a] >= dims[a] ? 1 : 0);
+            }
+          }
+          if (nf == 0) {
+            const bool solid = flags[(size_t)p[0] + (size_t)D.nx * ((size_t)p[1] + (size_t)D.ny * p[2])] != 0;
+            if (!solid && !wrapped) continue;          // plain streaming link
+            word |= 1u << i;
+            if (!solid) complex_link = true;             // streaming across a periodic face
+            continue;
+          }
+          word |= 1u << i;
+          bool bb = false, other = false, all_fs = true;
+          for (int k = 0; k < nf; ++k) {
+            const int kind = D.bc[faces[k]];
+            if (kind == SC_BC_BOUNCE_BACK) bb = true;
+            else other = true;
+            if (kind != SC_BC_FREE_SLIP) all_fs = false;
+          }
+          const bool plain_bb = bb || (nf == 2 && all_fs);
+          (void)other;
+          if (!plain_bb) complex_link = true;
         }
+        if (complex_link) word |= kLinkComplex;
         if (x == D.nx - 1 && D.bc[1] == SC_BC_OUTFLOW) word |= kLinkOutlet;
         link[c] = word;
       }
 }
 
-// Fluid cells that need the boundary path of the odd AA level: any link
-// whose source is not a plain in-domain fluid cell, or a cell on the outlet.
+// Fluid cells that need the general boundary path of the odd AA level: a
+// link that is not plain streaming or bounce-back, or a cell on the outlet.
 void hn_boundary_cells(const std::vector<uint32_t>& link, std::vector<int32_t>& cells) {
   cells.clear();
   for (size_t c = 0; c < link.size(); ++c)
-    if (!(link[c] & kLinkSolid) && (link[c] & (kLinkMask | kLinkOutlet))) cells.push_back((int32_t)c);
+    if (!(link[c] & kLinkSolid) && (link[c] & (kLinkOutlet | kLinkComplex))) cells.push_back((int32_t)c);
 }
 
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,

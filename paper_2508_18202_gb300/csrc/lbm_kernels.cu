@@ -70,16 +70,17 @@ __host__ __device__ constexpr int KOUT(int i) {
   return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1;
 }
 __device__ __forceinline__ int comp(int i, int a) { return a == 0 ? CX(i) : (a == 1 ? CY(i) : CZ(i)); }
-__device__ __forceinline__ int find_dir(int x, int y, int z) {
-#pragma unroll
+__host__ __device__ constexpr int DIR(int x, int y, int z) {
   for (int i = 0; i < kQ; ++i)
     if (CX(i) == x && CY(i) == y && CZ(i) == z) return i;
   return 0;
 }
+// direction i with its component along axis a negated (specular reflection)
+__host__ __device__ constexpr int REFL(int i, int a) {
+  return DIR(a == 0 ? -CX(i) : CX(i), a == 1 ? -CY(i) : CY(i), a == 2 ? -CZ(i) : CZ(i));
+}
 __device__ __forceinline__ int refl(int i, int a) {
-  int c[3] = {CX(i), CY(i), CZ(i)};
-  c[a] = -c[a];
-  return find_dir(c[0], c[1], c[2]);
+  return a == 0 ? REFL(i, 0) : (a == 1 ? REFL(i, 1) : REFL(i, 2));
 }
 
 // ------------------------------------------------------------ storage
@@ -404,12 +405,14 @@ __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& 
   }
 }
 
-// Odd time level, cell whose 19 links all stream between in-domain fluid
-// cells: branch-free pull from the upstream neighbours, collide, push to the
-// downstream neighbours.
+// Odd time level, cell whose boundary links (if any) are all plain
+// bounce-back: pull each f_i from slot opp(i) of the upstream neighbour, or
+// from the cell's own slot i where the link bounces back; push each f*_j to
+// slot j of the downstream neighbour, or to the own slot opp(j).  The choice
+// is an address select, so a warp stays converged.
 template <class S, bool CG>
 __device__ __forceinline__ void cell_odd_bulk(const StepParams& P, const DevDomain& D,
-                                              const Node<S>& N, long long idx) {
+                                              const Node<S>& N, uint32_t lw, long long idx) {
   using T = typename Store<S>::C;
   // 32-bit element offsets from the cell's own slot 0 (one node holds fewer
   // than 2^31 populations, checked at init)
@@ -418,10 +421,16 @@ __device__ __forceinline__ void cell_odd_bulk(const StepParams& P, const DevDoma
   S* base = N.g + idx;
   T g[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(base + (OPP(i) * nc - (CX(i) + CY(i) * sy + CZ(i) * sz)));
+  for (int i = 0; i < kQ; ++i) {
+    const int stream = OPP(i) * nc - (CX(i) + CY(i) * sy + CZ(i) * sz);
+    g[i] = LD<S, CG>(base + ((lw >> i) & 1u ? i * nc : stream));
+  }
   collide_p<T, true>(P, g);
 #pragma unroll
-  for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * nc + (CX(j) + CY(j) * sy + CZ(j) * sz)), g[j]);
+  for (int j = 0; j < kQ; ++j) {
+    const int stream = j * nc + (CX(j) + CY(j) * sy + CZ(j) * sz);
+    Store<S>::st(base + ((lw >> OPP(j)) & 1u ? OPP(j) * nc : stream), g[j]);
+  }
 }
 
 // Odd time level, boundary cell: the general per-link rules.
@@ -521,8 +530,9 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, long long t) 
   const Node<S> N = node_view<S>(D, R.node);
   for (int z = R.z0; z < R.z1; ++z) {
     const long long idx = cidx(D, R.x, R.y, z);
-    if (__ldg(D.link + idx) != 0u) continue;   // solid, boundary or outlet cell
-    cell_odd_bulk<S, CG>(P, D, N, idx);
+    const uint32_t lw = __ldg(D.link + idx);
+    if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
+    cell_odd_bulk<S, CG>(P, D, N, lw, idx);
   }
 }
 
@@ -687,13 +697,17 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
     const int z0 = tz * P.bz, z1 = min(z0 + P.bz, D.nz);
     for (int z = z0; z < z1; ++z) {
       const long long idx = cidx(D, x, y, z);
-      if (__ldg(D.link + idx) != 0u) continue;
+      const uint32_t lw = __ldg(D.link + idx);
+      if (lw & kLinkSlow) continue;
       double g[kQ];
 #pragma unroll
       for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
       collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
 #pragma unroll
-      for (int j = 0; j < kQ; ++j) dst[(long long)j * nc + idx + (CX(j) * sx + CY(j) * sy + CZ(j) * sz)] = g[j];
+      for (int j = 0; j < kQ; ++j) {
+        const long long stream = (long long)j * nc + idx + (CX(j) * sx + CY(j) * sy + CZ(j) * sz);
+        dst[((lw >> OPP(j)) & 1u) ? (long long)OPP(j) * nc + idx : stream] = g[j];
+      }
     }
     return;
   }

@@ -20,9 +20,12 @@ constexpr int kMaxGpcP = 20;     // largest gPC basis the reduction kernel keeps
 // Link word per cell: bit i (0..18) set when the pull source x - c_i of
 // direction i is not an in-domain fluid cell reached without periodic wrap
 // (solid, across a face, or wrapped).  Such links take the boundary path.
-constexpr uint32_t kLinkSolid = 1u << 19;   // the cell itself is solid
-constexpr uint32_t kLinkOutlet = 1u << 20;  // fluid cell on an OUTFLOW +x face
+constexpr uint32_t kLinkSolid = 1u << 19;    // the cell itself is solid
+constexpr uint32_t kLinkOutlet = 1u << 20;   // fluid cell on an OUTFLOW +x face
+constexpr uint32_t kLinkComplex = 1u << 21;  // some boundary link is not plain bounce-back
 constexpr uint32_t kLinkMask = (1u << 19) - 1u;
+// Cells without these bits take the fast path (boundary links = bounce-back).
+constexpr uint32_t kLinkSlow = kLinkSolid | kLinkOutlet | kLinkComplex;
 
 // Device error word bits.
 constexpr unsigned kErrDiverged = 1u;
