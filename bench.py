@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--nodes", type=int, default=0,
                     help="profiling case: keep only this many Smolyak levels' worth of nodes (0 = all)")
     ap.add_argument("--skip", default="", help="comma list of extra legs to skip: plain,storage,cpu,e2e,tune")
+    ap.add_argument("--tuning", default="",
+                    help="fixed launch shape block_x,block_y,slab_z,tile_order,exec_mode,graph_steps,variant "
+                         "instead of the autotuner")
     return ap.parse_args()
 
 
@@ -244,7 +247,10 @@ def main():
     flags = S.sc_lbm_geometry(cfg, 0)
     fluid = int((flags == 0).sum())
     columns = S.sc_lbm_probe_columns(cfg, 0, wl.get("n_columns", 4))
-    if "tune" not in skip:
+    if args.tuning:
+        bx, by, bz, order, mode, gsteps, variant = (int(v) for v in args.tuning.split(","))
+        S.sc_lbm_set_tuning(h, bx, by, bz, order, mode, gsteps, variant)
+    elif "tune" not in skip:
         S.sc_lbm_autotune(h, os.path.join(ROOT, "paper_2508_18202_gb300", "_build", "tuning_cache.json"))
     tuning = S.sc_lbm_get_tuning(h)
     S.sc_lbm_reset(h)

@@ -123,9 +123,13 @@ typedef struct {
  * 256, cover a block_x * block_y patch of an x-y plane; each thread walks
  * slab_z cells in z.  tile_order 0 runs the nodes of one patch back to back (shared geometry
  * stays in L2), 1 runs all patches of one node first.  graph_steps: time
- * steps per captured graph (SC_EXEC_GRAPH).                                 */
+ * steps per captured graph (SC_EXEC_GRAPH).  variant 0 loads per thread
+ * with a register budget for 4 resident blocks of 256 threads, 2 the same
+ * for 3 blocks, 1 streams runs of 256 consecutive cells through shared
+ * memory with TMA bulk copies (needs nx a multiple of 16 bytes of
+ * populations; launch and graph modes only).                                */
 typedef struct {
-  int block_x, block_y, slab_z, tile_order, exec_mode, graph_steps;
+  int block_x, block_y, slab_z, tile_order, exec_mode, graph_steps, variant;
 } sc_lbm_tuning;
 
 typedef struct sc_lbm_s* sc_lbm_t;

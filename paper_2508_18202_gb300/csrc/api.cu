@@ -34,7 +34,8 @@ size_t storage_bytes(int precision) {
 // Offsets of every buffer inside the caller's workspace.
 struct DomLayout {
   int nq = 0, P = 0;
-  long long ncell = 0;
+  long long ncell = 0, pitch = 0;
+  size_t guard = 0;
   size_t flags = 0, link = 0, bcell = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
 };
 struct Layout {
@@ -45,9 +46,7 @@ struct Layout {
 };
 
 struct Header {  // first 256 bytes of the workspace
-  unsigned long long step;
   unsigned long long check_count;
-  unsigned int done;
   unsigned int err;
   unsigned int bar_count;
   unsigned int bar_gen;
@@ -80,7 +79,7 @@ int validate(const sc_lbm_config* c, std::string& why) {
   for (int d = 0; d < c->n_domains; ++d) {
     const sc_domain_desc& D = c->domains[d];
     if (D.nx < 1 || D.ny < 1 || D.nz < 1) { why = "domain sizes must be positive"; return SC_ERR_ARG; }
-    if ((long long)D.nx * D.ny * D.nz * 19 >= (1LL << 31)) {
+    if (((long long)D.nx * D.ny * D.nz + kRun) * 19 >= (1LL << 31)) {
       why = "domain too large (19 populations per node must stay below 2^31)";
       return SC_ERR_UNSUPPORTED;
     }
@@ -139,8 +138,14 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     M.bcell = take(sizeof(int32_t) * (size_t)M.ncell);  // boundary list, at most every cell
     M.uin_f = take(16 * (size_t)M.nq * D.nz);
     M.uin_d = take(24 * (size_t)M.nq * D.nz);
-    M.g = take(sb * kQ * (size_t)M.ncell * M.nq);
-    if (c->precision == SC_P_FP64_PLAIN) M.g2 = take(sb * kQ * (size_t)M.ncell * M.nq);
+    M.pitch = (M.ncell + kRun - 1) / kRun * kRun;
+    // guard zones around the population array: the staged odd-level loads
+    // read row windows up to nx*ny + nx + 16 bytes outside a row
+    M.guard = align_up(sb * ((size_t)D.nx * D.ny + D.nx + kRun + 64));
+    off = align_up(off + M.guard);
+    M.g = take(sb * kQ * (size_t)M.pitch * M.nq);
+    off = align_up(off + M.guard);
+    if (c->precision == SC_P_FP64_PLAIN) M.g2 = take(sb * kQ * (size_t)M.pitch * M.nq);
     else M.bout = take(sizeof(float) * 5 * (size_t)D.nz * D.ny * M.nq);
     M.ab = take(sizeof(double) * (size_t)M.nq * (P + 1));
     max_cell = std::max(max_cell, M.ncell);
@@ -252,6 +257,7 @@ struct sc_lbm_s {
   int persist_grid = 0;
   int never_arrive = 0;
   long long spin_limit = kSpinLimit;
+  int tma_ok = 0;  // every domain's rows meet the 16-byte alignment of bulk copies
   Header* hdr() const { return reinterpret_cast<Header*>(ws + L.hdr); }
 };
 
@@ -279,7 +285,7 @@ void apply_tiling(sc_lbm_t h) {
   P.by = h->tune.block_y;
   P.bz = h->tune.slab_z;
   P.order = h->tune.tile_order;
-  long long begin = 0, bbegin = 0;
+  long long begin = 0, bbegin = 0, rbegin = 0;
   for (int d = 0; d < P.n_domains; ++d) {
     DevDomain& D = P.dom[d];
     D.tiles_x = (D.nx + P.bx - 1) / P.bx;
@@ -290,9 +296,15 @@ void apply_tiling(sc_lbm_t h) {
     begin += D.tiles_per_node * D.nodes;
     D.bitem_begin = bbegin;
     bbegin += D.nb * D.nodes;
+    D.runs_per_node = D.pitch / kRun;
+    D.run_begin = rbegin;
+    rbegin += D.runs_per_node * D.nodes;
   }
   P.total_tiles = begin;
   P.total_bitems = bbegin;
+  P.total_runs = rbegin;
+  P.tma = (h->tune.variant == 1 && h->tma_ok && h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
+  P.regs85 = h->tune.variant == 2 ? 1 : 0;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -308,6 +320,7 @@ int check_tuning(const sc_lbm_tuning& t) {
   if (t.tile_order < 0 || t.tile_order > 1) return SC_ERR_ARG;
   if (t.exec_mode < SC_EXEC_LAUNCH || t.exec_mode > SC_EXEC_PERSISTENT) return SC_ERR_ARG;
   if (t.graph_steps < 1 || t.graph_steps > 100000) return SC_ERR_ARG;
+  if (t.variant < 0 || t.variant > 2) return SC_ERR_ARG;
   return SC_OK;
 }
 
@@ -320,11 +333,17 @@ int reset_state(sc_lbm_t h) {
   return SC_OK;
 }
 
+float ramp_f(const sc_lbm_t h, long long m) { return (float)hn_ramp(h->cfg.ramp_steps, m); }
+
 // n steps with one launch each, starting at time level `start`
 int run_launches(sc_lbm_t h, long long start, int n) {
   for (int s = 0; s < n; ++s) {
-    const int parity = (int)((start + s) & 1);
-    int rc = launch_aa_step(h->P, h->cfg.precision, h->stream, parity);
+    const long long lvl = start + s;
+    const int parity = (int)(lvl & 1);
+    StepParams P = h->P;
+    P.r_pull = ramp_f(h, lvl);
+    P.r_push = ramp_f(h, lvl + 1);
+    int rc = launch_aa_step(P, h->cfg.precision, h->stream, parity);
     if (rc) return cuda_fail(h, (cudaError_t)rc, "aa_step launch");
     h->launches += parity ? 2 : 1;  // odd levels: bulk + boundary kernels
   }
@@ -333,15 +352,21 @@ int run_launches(sc_lbm_t h, long long start, int n) {
 
 // Replays of a captured graph of G steps (even/odd pairs, G even) starting
 // at an even time level.
+// The graph is captured once with the ramp complete (r = 1 on every level),
+// so levels inside the start-up ramp are launched one by one.
 int run_graph(sc_lbm_t h, int n) {
   const int G = h->tune.graph_steps + (h->tune.graph_steps & 1);
   if (!h->stream) return run_launches(h, h->steps, n);  // capture needs a non-default stream
   long long t = h->steps;
-  if (t & 1) {
-    int rc = run_launches(h, t, 1);
+  const long long ramp_done = h->cfg.ramp_steps;  // r(m) = 1 for every m >= ramp_steps
+  long long head = 0;
+  if (t < ramp_done) head = std::min<long long>(n, ramp_done - t);
+  if (((t + head) & 1) && head < n) ++head;
+  if (head > 0) {
+    int rc = run_launches(h, t, (int)head);
     if (rc) return rc;
-    ++t;
-    --n;
+    t += head;
+    n -= (int)head;
   }
   if (!h->graph || h->graph_len != G) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -349,7 +374,10 @@ int run_graph(sc_lbm_t h, int n) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
-    for (int s = 0; s < G && !rc; ++s) rc = launch_aa_step(h->P, h->cfg.precision, h->stream, s & 1);
+    StepParams P = h->P;
+    P.r_pull = 1.0f;
+    P.r_push = 1.0f;
+    for (int s = 0; s < G && !rc; ++s) rc = launch_aa_step(P, h->cfg.precision, h->stream, s & 1);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
       if (g) cudaGraphDestroy(g);
@@ -381,6 +409,7 @@ int run_persistent(sc_lbm_t h, int n) {
     const int k = std::min(chunk, n - done);
     StepParams P = h->P;
     P.n_steps = k;
+    P.n_host = (unsigned long long)(h->steps + done);
     P.never_arrive = h->never_arrive;
     P.spin_limit = h->spin_limit;
     CK(cudaMemsetAsync(&h->hdr()->bar_count, 0, sizeof(unsigned int), h->stream));
@@ -404,9 +433,6 @@ int run_plain(sc_lbm_t h, int n) {
         ++h->launches;
       }
     }
-  int rc = launch_set_counter(&h->hdr()->step, (unsigned long long)(h->steps + n), h->stream);
-  if (rc) return cuda_fail(h, (cudaError_t)rc, "set counter");
-  ++h->launches;
   return SC_OK;
 }
 
@@ -428,6 +454,13 @@ int read_err(sc_lbm_t h, unsigned* bits) {
   if (v) CK(cudaMemset(&h->hdr()->err, 0, sizeof(unsigned)));
   *bits = v;
   return SC_OK;
+}
+
+// Kernel parameters with the host's time level (observables need its parity).
+StepParams params_now(sc_lbm_t h) {
+  StepParams P = h->P;
+  P.n_host = (unsigned long long)h->steps;
+  return P;
 }
 
 int err_status(sc_lbm_t h, unsigned bits) {
@@ -535,8 +568,6 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   P.ramp_f = (const float*)(h->ws + L.ramp_f);
   P.ramp_d = (const double*)(h->ws + L.ramp_d);
   Header* H = h->hdr();
-  P.step = &H->step;
-  P.done = &H->done;
   P.err = &H->err;
   P.bar_count = &H->bar_count;
   P.bar_gen = &H->bar_gen;
@@ -614,11 +645,16 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     V.nb = (long long)bcells[d].size();
     V.uin_f = (const float4*)(h->ws + M.uin_f);
     V.uin_d = (const double*)(h->ws + M.uin_d);
+    V.pitch = M.pitch;
     V.g = h->ws + M.g;
     V.g2 = c.precision == SC_P_FP64_PLAIN ? (void*)(h->ws + M.g2) : nullptr;
     V.bout = c.precision == SC_P_FP64_PLAIN ? nullptr : (float*)(h->ws + M.bout);
   }
+  h->tma_ok = c.precision != SC_P_FP64_PLAIN;
+  for (int d = 0; d < c.n_domains; ++d)
+    if (c.domains[d].nx % (int)(16 / storage_bytes(c.precision)) != 0) h->tma_ok = 0;
   // default launch shape
+  h->tune.variant = h->tma_ok ? 1 : 0;
   h->tune.block_x = 128;
   h->tune.block_y = 2;
   h->tune.slab_z = 1;
@@ -702,7 +738,7 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   if (n_p > 0)
     CK(cudaMemcpyAsync(h->ws + L.probes, probe_xy, sizeof(int32_t) * 2 * n_p, cudaMemcpyHostToDevice,
                        h->stream));
-  int rc = launch_moments(h->P, h->cfg.precision, A, h->stream);
+  int rc = launch_moments(params_now(h), h->cfg.precision, A, h->stream);
   if (rc) return cuda_fail(h, (cudaError_t)rc, "moments launch");
   h->launches += (A.mean ? 1 : 0) + (n_p > 0 ? 1 : 0);
   if (!out_host) return SC_OK;
@@ -726,7 +762,7 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
 int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u) {
   if (!h || !d_u || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
   if (node < 0 || node >= h->P.dom[domain].nodes) return SC_ERR_ARG;
-  int rc = launch_export(h->P, h->cfg.precision, domain, node, nullptr, d_u, h->stream);
+  int rc = launch_export(params_now(h), h->cfg.precision, domain, node, nullptr, d_u, h->stream);
   if (rc) return cuda_fail(h, (cudaError_t)rc, "export launch");
   ++h->launches;
   return SC_OK;
@@ -735,7 +771,7 @@ int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u) {
 int sc_lbm_populations(sc_lbm_t h, int domain, int node, double* d_f) {
   if (!h || !d_f || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
   if (node < 0 || node >= h->P.dom[domain].nodes) return SC_ERR_ARG;
-  int rc = launch_export(h->P, h->cfg.precision, domain, node, d_f, nullptr, h->stream);
+  int rc = launch_export(params_now(h), h->cfg.precision, domain, node, d_f, nullptr, h->stream);
   if (rc) return cuda_fail(h, (cudaError_t)rc, "export launch");
   ++h->launches;
   return SC_OK;
@@ -765,8 +801,9 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   const std::string key = tune_key(&h->cfg, prop.name);
   auto cache = read_cache(cache_path);
   auto it = cache.find(key);
-  if (it != cache.end() && it->second.size() == 6) {
-    sc_lbm_tuning t{it->second[0], it->second[1], it->second[2], it->second[3], it->second[4], it->second[5]};
+  if (it != cache.end() && it->second.size() == 7) {
+    sc_lbm_tuning t{it->second[0], it->second[1], it->second[2], it->second[3],
+                    it->second[4], it->second[5], it->second[6]};
     if (check_tuning(t) == SC_OK) return sc_lbm_set_tuning(h, &t);
   }
   int maxnx = 0;
@@ -774,15 +811,18 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   std::vector<sc_lbm_tuning> cand;
   const int bxs[] = {32, 64, 128, 256};
   const int bys[] = {1, 2, 4, 8};
-  const int bzs[] = {1, 2, 4};
+  const int bzs[] = {1, 2, 4, 8};
   for (int bx : bxs) {
     if (bx > 32 && bx / 2 >= maxnx) continue;
     for (int by : bys)
       for (int bz : bzs) {
         if (bx * by > 256 || bx * by < 64) continue;
-        for (int order = 0; order < 2; ++order) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50});
+        for (int order = 0; order < 2; ++order)
+          for (int v : {0, 2}) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50, v});
       }
   }
+  if (h->tma_ok)
+    for (int order = 0; order < 2; ++order) cand.push_back({128, 2, 1, order, SC_EXEC_LAUNCH, 50, 1});
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -814,6 +854,11 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   for (int mode : {SC_EXEC_GRAPH, SC_EXEC_PERSISTENT}) {
     sc_lbm_tuning t = best_t;
     t.exec_mode = mode;
+    if (mode == SC_EXEC_PERSISTENT && t.variant == 1) {
+      t.variant = 0;  // the persistent form loads per thread
+      t.block_x = 64;
+      t.block_y = 2;
+    }
     float ms = 0;
     int rc = time_it(t, &ms);
     if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
@@ -830,7 +875,7 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   if (rc) return rc;
   if (cache_path) {
     cache[key] = {best_t.block_x, best_t.block_y, best_t.slab_z, best_t.tile_order, best_t.exec_mode,
-                  best_t.graph_steps};
+                  best_t.graph_steps, best_t.variant};
     write_cache(cache_path, cache);
   }
   return err_status(h, bits);
@@ -855,7 +900,7 @@ int sc_lbm_check(sc_lbm_t h, long long* n_bad) {
   if (!h) return SC_ERR_ARG;
   unsigned long long* cnt = &h->hdr()->check_count;
   CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->stream));
-  int rc = launch_check(h->P, h->cfg.precision, cnt, h->stream);
+  int rc = launch_check(params_now(h), h->cfg.precision, cnt, h->stream);
   if (rc) return cuda_fail(h, (cudaError_t)rc, "check launch");
   ++h->launches;
   unsigned long long v = 0;
@@ -894,7 +939,7 @@ static size_t payload_bytes(sc_lbm_t h) {
   const size_t sb = storage_bytes(h->cfg.precision);
   for (int d = 0; d < h->P.n_domains; ++d) {
     const DevDomain& D = h->P.dom[d];
-    b += sb * kQ * (size_t)D.ncell * D.nodes * (h->cfg.precision == SC_P_FP64_PLAIN ? 2 : 1);
+    b += sb * kQ * (size_t)D.pitch * D.nodes * (h->cfg.precision == SC_P_FP64_PLAIN ? 2 : 1);
     if (D.bout) b += sizeof(float) * 5 * (size_t)D.nz * D.ny * D.nodes;
   }
   return b;
@@ -914,7 +959,7 @@ int sc_lbm_save(sc_lbm_t h, void* host_buf, size_t bytes) {
   const size_t sb = storage_bytes(h->cfg.precision);
   for (int d = 0; d < h->P.n_domains; ++d) {
     const DevDomain& D = h->P.dom[d];
-    size_t n = sb * kQ * (size_t)D.ncell * D.nodes;
+    size_t n = sb * kQ * (size_t)D.pitch * D.nodes;
     CK(cudaMemcpyAsync(out, D.g, n, cudaMemcpyDeviceToHost, h->stream));
     out += n;
     if (D.g2) {
@@ -953,7 +998,7 @@ int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes) {
   const size_t sb = storage_bytes(h->cfg.precision);
   for (int d = 0; d < h->P.n_domains; ++d) {
     const DevDomain& D = h->P.dom[d];
-    size_t n = sb * kQ * (size_t)D.ncell * D.nodes;
+    size_t n = sb * kQ * (size_t)D.pitch * D.nodes;
     CK(cudaMemcpyAsync(D.g, in, n, cudaMemcpyHostToDevice, h->stream));
     in += n;
     if (D.g2) {
@@ -966,9 +1011,6 @@ int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes) {
       in += nb;
     }
   }
-  int rc = launch_set_counter(&h->hdr()->step, hd.steps, h->stream);
-  if (rc) return cuda_fail(h, (cudaError_t)rc, "set counter");
-  ++h->launches;
   CK(cudaStreamSynchronize(h->stream));
   h->steps = (long long)hd.steps;
   return SC_OK;

@@ -7,18 +7,22 @@
 // of Sec. 2.3 (Eqs. quad_moments, coef_discrete).
 //
 // Layout (structure of arrays, x fastest): population i of node j of a
-// domain lives at g[(j*19 + i)*ncell + c], c = x + nx*(y + ny*z).  The
-// in-place precisions store g_i = f_i - w_i (the shift keeps the FP32/BF16/
-// FP16 mantissa for the deviation from rest) and advance with the AA access
-// pattern: at an even time level a cell reads its own 19 slots and writes
-// the post-collision values back to the opposite slots of the same cell; at
-// an odd level it pulls f_i from slot opp(i) of the upstream neighbour
-// x - c_i and pushes f*_i into slot i of the downstream neighbour x + c_i.
-// Every slot is then read and written by exactly one thread per step, so one
-// array suffices (152 B per fluid cell update in FP32).
+// domain lives at g[(j*19 + i)*pitch + c], c = x + nx*(y + ny*z), with the
+// row pitch a multiple of 256 cells and guard zones before and after the
+// array.  The in-place precisions store g_i = f_i - w_i (the shift keeps the
+// FP32/BF16/FP16 mantissa for the deviation from rest) and advance with the
+// AA access pattern: at an even time level a cell reads its own 19 slots and
+// writes the post-collision values back to the opposite slots of the same
+// cell; at an odd level it pulls f_i from slot opp(i) of the upstream
+// neighbour x - c_i and pushes f*_i into slot i of the downstream neighbour
+// x + c_i.  Every slot is then read and written by exactly one thread per
+// step, so one array suffices (152 B per fluid cell update in FP32).
 //
-// Boundary links (bit i of the cell's link word) take a slow path that
-// applies the same per-link rules as the pull formulation:
+// Links whose source is solid or lies across a bounce-back face use the own
+// slot instead of the neighbour's (an address select in the bulk kernels).
+// Cells with any other boundary link (inflow, outflow, free slip, periodic)
+// are listed on the host and updated by a compact general kernel that
+// applies the per-link rules of the pull formulation:
 //   source inside and solid            -> bounce-back
 //   one face crossed: BOUNCE_BACK      -> bounce-back
 //                     VELOCITY         -> bounce-back + 6 w_i (c_i . u_in(z)) r(t)
@@ -34,6 +38,13 @@
 // odd step overwrites in place, so even steps also save the five f*_i with
 // c_ix = -1 of every outlet cell into a small per-node plane (bout) that the
 // odd step reads.
+//
+// Two forms of the bulk kernels: per-thread loads (one cell per thread, a
+// z-slab per thread), and TMA-staged ones in which a CTA streams runs of 256
+// consecutive cells through a 4-stage shared-memory pipeline filled by 1-D
+// bulk copies (cp.async.bulk + mbarrier).  The even level stores back with
+// bulk copies too; the odd level loads the 19 shifted row windows (widened
+// by 16 bytes on each side for alignment) and stores per thread.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -65,11 +76,6 @@ template <class T>
 __host__ __device__ constexpr T W(int i) {
   return C2(i) == 0 ? T(1.0 / 3.0) : (C2(i) == 1 ? T(1.0 / 18.0) : T(1.0 / 36.0));
 }
-// slot in the outflow plane of the five directions with c_x = -1
-__host__ __device__ constexpr int KOUT(int i) {
-  return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1;
-}
-__device__ __forceinline__ int comp(int i, int a) { return a == 0 ? CX(i) : (a == 1 ? CY(i) : CZ(i)); }
 __host__ __device__ constexpr int DIR(int x, int y, int z) {
   for (int i = 0; i < kQ; ++i)
     if (CX(i) == x && CY(i) == y && CZ(i) == z) return i;
@@ -79,9 +85,46 @@ __host__ __device__ constexpr int DIR(int x, int y, int z) {
 __host__ __device__ constexpr int REFL(int i, int a) {
   return DIR(a == 0 ? -CX(i) : CX(i), a == 1 ? -CY(i) : CY(i), a == 2 ? -CZ(i) : CZ(i));
 }
-__device__ __forceinline__ int refl(int i, int a) {
-  return a == 0 ? REFL(i, 0) : (a == 1 ? REFL(i, 1) : REFL(i, 2));
+// slot in the outflow plane of the five directions with c_x = -1
+__host__ __device__ constexpr int KOUT(int i) {
+  return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1;
 }
+
+// The same tables for run-time directions (compact boundary code).
+struct LatticeTables {
+  int cx[kQ], cy[kQ], cz[kQ], opp[kQ], kout[kQ], refl[kQ][3];
+  float wf[kQ];
+  double wd[kQ];
+};
+__constant__ LatticeTables c_lat = {
+    {CX(0), CX(1), CX(2), CX(3), CX(4), CX(5), CX(6), CX(7), CX(8), CX(9), CX(10), CX(11), CX(12),
+     CX(13), CX(14), CX(15), CX(16), CX(17), CX(18)},
+    {CY(0), CY(1), CY(2), CY(3), CY(4), CY(5), CY(6), CY(7), CY(8), CY(9), CY(10), CY(11), CY(12),
+     CY(13), CY(14), CY(15), CY(16), CY(17), CY(18)},
+    {CZ(0), CZ(1), CZ(2), CZ(3), CZ(4), CZ(5), CZ(6), CZ(7), CZ(8), CZ(9), CZ(10), CZ(11), CZ(12),
+     CZ(13), CZ(14), CZ(15), CZ(16), CZ(17), CZ(18)},
+    {OPP(0), OPP(1), OPP(2), OPP(3), OPP(4), OPP(5), OPP(6), OPP(7), OPP(8), OPP(9), OPP(10),
+     OPP(11), OPP(12), OPP(13), OPP(14), OPP(15), OPP(16), OPP(17), OPP(18)},
+    {KOUT(0), KOUT(1), KOUT(2), KOUT(3), KOUT(4), KOUT(5), KOUT(6), KOUT(7), KOUT(8), KOUT(9),
+     KOUT(10), KOUT(11), KOUT(12), KOUT(13), KOUT(14), KOUT(15), KOUT(16), KOUT(17), KOUT(18)},
+    {{REFL(0, 0), REFL(0, 1), REFL(0, 2)},    {REFL(1, 0), REFL(1, 1), REFL(1, 2)},
+     {REFL(2, 0), REFL(2, 1), REFL(2, 2)},    {REFL(3, 0), REFL(3, 1), REFL(3, 2)},
+     {REFL(4, 0), REFL(4, 1), REFL(4, 2)},    {REFL(5, 0), REFL(5, 1), REFL(5, 2)},
+     {REFL(6, 0), REFL(6, 1), REFL(6, 2)},    {REFL(7, 0), REFL(7, 1), REFL(7, 2)},
+     {REFL(8, 0), REFL(8, 1), REFL(8, 2)},    {REFL(9, 0), REFL(9, 1), REFL(9, 2)},
+     {REFL(10, 0), REFL(10, 1), REFL(10, 2)}, {REFL(11, 0), REFL(11, 1), REFL(11, 2)},
+     {REFL(12, 0), REFL(12, 1), REFL(12, 2)}, {REFL(13, 0), REFL(13, 1), REFL(13, 2)},
+     {REFL(14, 0), REFL(14, 1), REFL(14, 2)}, {REFL(15, 0), REFL(15, 1), REFL(15, 2)},
+     {REFL(16, 0), REFL(16, 1), REFL(16, 2)}, {REFL(17, 0), REFL(17, 1), REFL(17, 2)},
+     {REFL(18, 0), REFL(18, 1), REFL(18, 2)}},
+    {W<float>(0), W<float>(1), W<float>(2), W<float>(3), W<float>(4), W<float>(5), W<float>(6),
+     W<float>(7), W<float>(8), W<float>(9), W<float>(10), W<float>(11), W<float>(12), W<float>(13),
+     W<float>(14), W<float>(15), W<float>(16), W<float>(17), W<float>(18)},
+    {W<double>(0), W<double>(1), W<double>(2), W<double>(3), W<double>(4), W<double>(5),
+     W<double>(6), W<double>(7), W<double>(8), W<double>(9), W<double>(10), W<double>(11),
+     W<double>(12), W<double>(13), W<double>(14), W<double>(15), W<double>(16), W<double>(17),
+     W<double>(18)},
+};
 
 // ------------------------------------------------------------ storage
 template <class S>
@@ -124,6 +167,10 @@ __device__ __forceinline__ typename Store<S>::C LD(const S* p) {
 }
 
 // ------------------------------------------------------------ collision
+// Correctly rounded reciprocal (the same value as 1 / x in IEEE arithmetic).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
 // BGK with the Smagorinsky effective relaxation time (Sec. 2.2).  SHIFT:
 // populations are g = f - w.  The non-equilibrium stress uses the exact
 // second moment of the D3Q19 second-order equilibrium, rho/3 I + rho u u.
@@ -145,7 +192,7 @@ __device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_o
     if (CY(i) * CZ(i)) pyz += CY(i) * CZ(i) > 0 ? g[i] : -g[i];
   }
   const T rho = SHIFT ? T(1) + m0 : m0;
-  const T inv = T(1) / rho;
+  const T inv = recip(rho);
   const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
   const T usq = ux * ux + uy * uy + uz * uz;
   T tau = tau0;
@@ -162,7 +209,7 @@ __device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_o
     const T pin = sqrt(T(2) * pipi + T(1e-30));
     tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + smag18c2 * pin * inv));
   }
-  const T omega = T(1) / tau;
+  const T omega = recip(tau);
   const T base = m0;  // shifted: w (rho - 1) part; plain: w rho part
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -170,6 +217,14 @@ __device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_o
     const T geq = W<T>(i) * (base + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
     g[i] = g[i] - omega * (g[i] - geq);
   }
+}
+
+template <class T, bool SHIFT>
+__device__ __forceinline__ void collide_p(const StepParams& P, T g[kQ]) {
+  if constexpr (sizeof(T) == 8)
+    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
+  else
+    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
 }
 
 // ------------------------------------------------------------ boundary helpers
@@ -208,46 +263,42 @@ __device__ __forceinline__ long long cidx(const DevDomain& D, int x, int y, int 
   return (long long)x + (long long)D.nx * ((long long)y + (long long)D.ny * z);
 }
 
-template <class T>
-__device__ __forceinline__ T ladd(int i, float4 u, T r) {
-  // 6 w_i rho_w (c_i . u_w) r, rho_w = 1
-  const T cu = T(CX(i)) * T(u.x) + T(CY(i)) * T(u.y) + T(CZ(i)) * T(u.z);
-  return T(6) * W<T>(i) * cu * r;
-}
-template <class T>
-__device__ __forceinline__ T ladd_d(int i, const double* u, T r) {
-  const T cu = T(CX(i)) * T(u[0]) + T(CY(i)) * T(u[1]) + T(CZ(i)) * T(u[2]);
-  return T(6) * W<T>(i) * cu * r;
-}
-
 // Per-node pointers.
 template <class S>
 struct Node {
-  S* g;                // [19][ncell]
+  S* g;                // [19][pitch]
   float* bout;         // [nz*ny][5]
   const float4* uinf;  // [nz]
   const double* uind;  // [nz][3]
 };
 
-// Inflow correction of direction i at layer z.
+// Inflow correction 6 w_i rho_w (c_i . u_w(z)) r of direction i (rho_w = 1).
 template <class S, class T>
 __device__ __forceinline__ T vel_term(const Node<S>& N, int i, int z, T r) {
-  if constexpr (sizeof(T) == 8) return ladd_d<T>(i, N.uind + 3 * z, r);
-  else return ladd<T>(i, N.uinf[z], r);
+  if constexpr (sizeof(T) == 8) {
+    const double* u = N.uind + 3 * z;
+    const T cu = T(c_lat.cx[i]) * T(u[0]) + T(c_lat.cy[i]) * T(u[1]) + T(c_lat.cz[i]) * T(u[2]);
+    return T(6) * T(c_lat.wd[i]) * cu * r;
+  } else {
+    const float4 u = N.uinf[z];
+    const T cu = T(c_lat.cx[i]) * T(u.x) + T(c_lat.cy[i]) * T(u.y) + T(c_lat.cz[i]) * T(u.z);
+    return T(6) * T(c_lat.wf[i]) * cu * r;
+  }
 }
 
 // f_i of time level n (odd, AA swapped layout) for a boundary link.
 template <class S, bool CG>
-__device__ __forceinline__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
+__device__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
                                              int y, int z, long long idx,
                                              typename Store<S>::C r) {
   using T = typename Store<S>::C;
-  const long long nc = D.ncell;
-  const Cross c = classify(D, x - CX(i), y - CY(i), z - CZ(i));
-  const T own = LD<S, CG>(N.g + (long long)i * nc + idx);  // f*_opp(i)(x)
+  const long long pc = D.pitch;
+  const int cx = c_lat.cx[i], cy = c_lat.cy[i], cz = c_lat.cz[i];
+  const Cross c = classify(D, x - cx, y - cy, z - cz);
+  const T own = LD<S, CG>(N.g + (long long)i * pc + idx);  // f*_opp(i)(x)
   if (c.n == 0) {
     const long long p = cidx(D, c.p[0], c.p[1], c.p[2]);
-    if (D.flags[p] == 0) return LD<S, CG>(N.g + (long long)OPP(i) * nc + p);
+    if (D.flags[p] == 0) return LD<S, CG>(N.g + (long long)c_lat.opp[i] * pc + p);
     return own;
   }
   if (c.n == 1) {
@@ -255,18 +306,18 @@ __device__ __forceinline__ typename Store<S>::C pull_special(const DevDomain& D,
     if (kind == SC_BC_BOUNCE_BACK) return own;
     if (kind == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
     const int a = c.f[0] >> 1;
-    int s[3] = {x - CX(i), y - CY(i), z - CZ(i)};
+    int s[3] = {x - cx, y - cy, z - cz};
     s[a] = a == 0 ? x : (a == 1 ? y : z);
     const Cross cs = classify(D, s[0], s[1], s[2]);
     const long long sp = cidx(D, cs.p[0], cs.p[1], cs.p[2]);
     if (kind == SC_BC_FREE_SLIP) {
-      if (D.flags[sp] == 0) return LD<S, CG>(N.g + (long long)OPP(refl(i, a)) * nc + sp);
+      if (D.flags[sp] == 0) return LD<S, CG>(N.g + (long long)c_lat.opp[c_lat.refl[i][a]] * pc + sp);
       return own;
     }
     // OUTFLOW on +x: transverse source on the outlet plane
     if (D.flags[sp] == 0)
-      return T(__ldcg(N.bout + ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + KOUT(i)));
-    return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + KOUT(i)));
+      return T(__ldcg(N.bout + ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + c_lat.kout[i]));
+    return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + c_lat.kout[i]));
   }
   const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
   if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) return own;
@@ -274,21 +325,22 @@ __device__ __forceinline__ typename Store<S>::C pull_special(const DevDomain& D,
   if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) return own;
   // outflow + free slip: own population reflected across the free-slip face
   const int fs = (k0 == SC_BC_FREE_SLIP) ? c.f[0] : c.f[1];
-  return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + KOUT(refl(i, fs >> 1))));
+  return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + c_lat.kout[c_lat.refl[i][fs >> 1]]));
 }
 
 // Deliver f*_j of cell x for a boundary link into dst (AA: dst == src array).
 template <class S>
-__device__ __forceinline__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
+__device__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
                              typename Store<S>::C v, int x, int y, int z, long long idx,
                              typename Store<S>::C r1) {
   using T = typename Store<S>::C;
-  const long long nc = D.ncell;
-  const Cross c = classify(D, x + CX(j), y + CY(j), z + CZ(j));
-  S* own = dst + (long long)OPP(j) * nc + idx;
+  const long long pc = D.pitch;
+  const int cx = c_lat.cx[j], cy = c_lat.cy[j], cz = c_lat.cz[j], oj = c_lat.opp[j];
+  const Cross c = classify(D, x + cx, y + cy, z + cz);
+  S* own = dst + (long long)oj * pc + idx;
   if (c.n == 0) {
     const long long q = cidx(D, c.p[0], c.p[1], c.p[2]);
-    if (D.flags[q] == 0) Store<S>::st(dst + (long long)j * nc + q, v);
+    if (D.flags[q] == 0) Store<S>::st(dst + (long long)j * pc + q, v);
     else Store<S>::st(own, v);
     return;
   }
@@ -297,14 +349,14 @@ __device__ __forceinline__ void push_special(const DevDomain& D, const Node<S>& 
     if (kind == SC_BC_BOUNCE_BACK) {
       Store<S>::st(own, v);
     } else if (kind == SC_BC_VELOCITY) {
-      Store<S>::st(own, v + vel_term<S, T>(N, OPP(j), z, r1));
+      Store<S>::st(own, v + vel_term<S, T>(N, oj, z, r1));
     } else if (kind == SC_BC_FREE_SLIP) {
       const int a = c.f[0] >> 1;
-      int t[3] = {x + CX(j), y + CY(j), z + CZ(j)};
+      int t[3] = {x + cx, y + cy, z + cz};
       t[a] = a == 0 ? x : (a == 1 ? y : z);
       const Cross ct = classify(D, t[0], t[1], t[2]);
       const long long tp = cidx(D, ct.p[0], ct.p[1], ct.p[2]);
-      if (D.flags[tp] == 0) Store<S>::st(dst + (long long)refl(j, a) * nc + tp, v);
+      if (D.flags[tp] == 0) Store<S>::st(dst + (long long)c_lat.refl[j][a] * pc + tp, v);
       else Store<S>::st(own, v);
     }
     // OUTFLOW: the population leaves the domain
@@ -314,7 +366,7 @@ __device__ __forceinline__ void push_special(const DevDomain& D, const Node<S>& 
   if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) {
     Store<S>::st(own, v);
   } else if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) {
-    Store<S>::st(own, v + vel_term<S, T>(N, OPP(j), z, r1));
+    Store<S>::st(own, v + vel_term<S, T>(N, oj, z, r1));
   } else if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) {
     Store<S>::st(own, v);
   }
@@ -324,85 +376,105 @@ __device__ __forceinline__ void push_special(const DevDomain& D, const Node<S>& 
 // Outlet cell (x = nx-1, +x OUTFLOW): deliver f*_j (c_jx = -1) to the outlet
 // links that read it.
 template <class S>
-__device__ __forceinline__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x,
-                            int y, int z, long long idx) {
-  const long long nc = D.ncell;
+__device__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x, int y,
+                            int z, long long idx) {
+  const long long pc = D.pitch;
+  const int cy = c_lat.cy[j], cz = c_lat.cz[j];
   // (1) transverse neighbour on the outlet plane copies it
   {
-    const Cross c = classify(D, x, y + CY(j), z + CZ(j));
+    const Cross c = classify(D, x, y + cy, z + cz);
     if (c.n == 0) {
       const long long t = cidx(D, c.p[0], c.p[1], c.p[2]);
-      if (D.flags[t] == 0) Store<S>::st(dst + (long long)j * nc + t, v);
+      if (D.flags[t] == 0) Store<S>::st(dst + (long long)j * pc + t, v);
     }
   }
   // (2) own link j whose transverse source is solid falls back to own value
   {
-    const Cross c = classify(D, x, y - CY(j), z - CZ(j));
+    const Cross c = classify(D, x, y - cy, z - cz);
     if (c.n == 0 && D.flags[cidx(D, c.p[0], c.p[1], c.p[2])] != 0)
-      Store<S>::st(dst + (long long)j * nc + idx, v);
+      Store<S>::st(dst + (long long)j * pc + idx, v);
   }
   // (3) outflow + free-slip edge: reflected copy into the own cell
-#pragma unroll
   for (int a = 1; a < 3; ++a) {
-    const int cj = comp(j, a);
+    const int cj = a == 1 ? cy : cz;
     if (cj == 0) continue;
     const int face = 2 * a + (cj > 0 ? 1 : 0);
     const int pos = (a == 1 ? y : z) + cj;
     const int lim = a == 1 ? D.ny : D.nz;
     if (D.bc[face] == SC_BC_FREE_SLIP && (pos < 0 || pos >= lim))
-      Store<S>::st(dst + (long long)refl(j, a) * nc + idx, v);
+      Store<S>::st(dst + (long long)c_lat.refl[j][a] * pc + idx, v);
+  }
+}
+
+__device__ __forceinline__ long long link_offset(const DevDomain& D, int i) {
+  return (long long)c_lat.cx[i] + (long long)c_lat.cy[i] * D.nx + (long long)c_lat.cz[i] * D.nx * D.ny;
+}
+
+// f_i of the odd time level at a cell, any link kind (run-time loop, compact).
+template <class S, bool CG>
+__device__ void load_odd_general(const DevDomain& D, const Node<S>& N, uint32_t lw, int x, int y,
+                                 int z, long long idx, typename Store<S>::C g[kQ],
+                                 typename Store<S>::C r) {
+#pragma unroll 1
+  for (int i = 0; i < kQ; ++i) {
+    if (!((lw >> i) & 1u))
+      g[i] = LD<S, CG>(N.g + (long long)c_lat.opp[i] * D.pitch + idx - link_offset(D, i));
+    else
+      g[i] = pull_special<S, CG>(D, N, i, x, y, z, idx, r);
+  }
+}
+
+// Push of the odd level (or of the FP64 two-array path) for a cell with
+// boundary links, any link kind.
+template <class S>
+__device__ void push_general(const DevDomain& D, const Node<S>& N, S* dst, uint32_t lw, int x, int y,
+                             int z, long long idx, const typename Store<S>::C g[kQ],
+                             typename Store<S>::C r1) {
+#pragma unroll 1
+  for (int j = 0; j < kQ; ++j) {
+    if (!((lw >> c_lat.opp[j]) & 1u))
+      Store<S>::st(dst + (long long)j * D.pitch + idx + link_offset(D, j), g[j]);
+    else
+      push_special<S>(D, N, dst, j, g[j], x, y, z, idx, r1);
+  }
+  if (lw & kLinkOutlet) {
+    push_outlet<S>(D, dst, 2, g[2], x, y, z, idx);
+    push_outlet<S>(D, dst, 8, g[8], x, y, z, idx);
+    push_outlet<S>(D, dst, 10, g[10], x, y, z, idx);
+    push_outlet<S>(D, dst, 12, g[12], x, y, z, idx);
+    push_outlet<S>(D, dst, 14, g[14], x, y, z, idx);
   }
 }
 
 // ------------------------------------------------------------ per-cell updates
-template <class S, bool CG, bool SHIFT>
-__device__ __forceinline__ void load_odd(const DevDomain& D, const Node<S>& N, uint32_t lw, int x,
-                                         int y, int z, long long idx,
-                                         typename Store<S>::C g[kQ], typename Store<S>::C r) {
-  const long long nc = D.ncell;
-  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    if (!(lw & (1u << i))) {
-      const long long off = CX(i) * sx + CY(i) * sy + CZ(i) * sz;
-      g[i] = LD<S, CG>(N.g + (long long)OPP(i) * nc + idx - off);
-    } else {
-      g[i] = pull_special<S, CG>(D, N, i, x, y, z, idx, r);
-    }
-  }
-}
-
-template <class T, bool SHIFT>
-__device__ __forceinline__ void collide_p(const StepParams& P, T g[kQ]) {
-  if constexpr (sizeof(T) == 8)
-    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
-  else
-    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
-}
-
-// Even time level: every fluid cell reads its own 19 slots and writes the
+// Even time level: a fluid cell reads its own 19 slots and writes the
 // post-collision populations to the opposite slots; outlet cells also save
 // their five populations with c_x = -1 into the outflow plane.
+template <class S>
+__device__ __forceinline__ void save_outlet(const DevDomain& D, const Node<S>& N, int y, int z,
+                                            const typename Store<S>::C g[kQ]) {
+  float* b = N.bout + ((long long)z * D.ny + y) * 5;
+  b[0] = float(g[2]);
+  b[1] = float(g[8]);
+  b[2] = float(g[10]);
+  b[3] = float(g[12]);
+  b[4] = float(g[14]);
+}
+
 template <class S, bool CG>
 __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& D,
                                           const Node<S>& N, uint32_t lw, int y, int z,
                                           long long idx) {
   using T = typename Store<S>::C;
-  const long long nc = D.ncell;
+  const int pc = (int)D.pitch;
+  S* base = N.g + idx;
   T g[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(N.g + (long long)i * nc + idx);
+  for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(base + i * pc);
   collide_p<T, true>(P, g);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) Store<S>::st(N.g + (long long)OPP(i) * nc + idx, g[i]);
-  if (lw & kLinkOutlet) {
-    float* b = N.bout + ((long long)z * D.ny + y) * 5;
-    b[0] = float(g[2]);
-    b[1] = float(g[8]);
-    b[2] = float(g[10]);
-    b[3] = float(g[12]);
-    b[4] = float(g[14]);
-  }
+  for (int i = 0; i < kQ; ++i) Store<S>::st(base + OPP(i) * pc, g[i]);
+  if (lw & kLinkOutlet) save_outlet<S>(D, N, y, z, g);
 }
 
 // Odd time level, cell whose boundary links (if any) are all plain
@@ -416,58 +488,40 @@ __device__ __forceinline__ void cell_odd_bulk(const StepParams& P, const DevDoma
   using T = typename Store<S>::C;
   // 32-bit element offsets from the cell's own slot 0 (one node holds fewer
   // than 2^31 populations, checked at init)
-  const int nc = (int)D.ncell;
+  const int pc = (int)D.pitch;
   const int sy = D.nx, sz = D.nx * D.ny;
   S* base = N.g + idx;
   T g[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const int stream = OPP(i) * nc - (CX(i) + CY(i) * sy + CZ(i) * sz);
-    g[i] = LD<S, CG>(base + ((lw >> i) & 1u ? i * nc : stream));
+    const int stream = OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz);
+    g[i] = LD<S, CG>(base + ((lw >> i) & 1u ? i * pc : stream));
   }
   collide_p<T, true>(P, g);
 #pragma unroll
   for (int j = 0; j < kQ; ++j) {
-    const int stream = j * nc + (CX(j) + CY(j) * sy + CZ(j) * sz);
-    Store<S>::st(base + ((lw >> OPP(j)) & 1u ? OPP(j) * nc : stream), g[j]);
+    const int stream = j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz);
+    Store<S>::st(base + ((lw >> OPP(j)) & 1u ? OPP(j) * pc : stream), g[j]);
   }
 }
 
-// Odd time level, boundary cell: the general per-link rules.
+// Odd time level, listed boundary cell: the general per-link rules.
 template <class S, bool CG>
-__device__ __forceinline__ void cell_odd(const StepParams& P, const DevDomain& D,
-                                         const Node<S>& N, uint32_t lw, int x, int y, int z,
-                                         long long idx, typename Store<S>::C r,
-                                         typename Store<S>::C r1) {
+__device__ void cell_odd_general(const StepParams& P, const DevDomain& D, const Node<S>& N,
+                                 uint32_t lw, int x, int y, int z, long long idx,
+                                 typename Store<S>::C r, typename Store<S>::C r1) {
   using T = typename Store<S>::C;
-  const long long nc = D.ncell;
-  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
   T g[kQ];
-  load_odd<S, CG, true>(D, N, lw, x, y, z, idx, g, r);
+  load_odd_general<S, CG>(D, N, lw, x, y, z, idx, g, r);
   collide_p<T, true>(P, g);
-#pragma unroll
-  for (int j = 0; j < kQ; ++j) {
-    if (!(lw & (1u << OPP(j)))) {
-      const long long off = CX(j) * sx + CY(j) * sy + CZ(j) * sz;
-      Store<S>::st(N.g + (long long)j * nc + idx + off, g[j]);
-    } else {
-      push_special<S>(D, N, N.g, j, g[j], x, y, z, idx, r1);
-    }
-  }
-  if (lw & kLinkOutlet) {
-    push_outlet<S>(D, N.g, 2, g[2], x, y, z, idx);
-    push_outlet<S>(D, N.g, 8, g[8], x, y, z, idx);
-    push_outlet<S>(D, N.g, 10, g[10], x, y, z, idx);
-    push_outlet<S>(D, N.g, 12, g[12], x, y, z, idx);
-    push_outlet<S>(D, N.g, 14, g[14], x, y, z, idx);
-  }
+  push_general<S>(D, N, N.g, lw, x, y, z, idx, g, r1);
 }
 
 // ------------------------------------------------------------ step driver
 template <class S>
 __device__ __forceinline__ Node<S> node_view(const DevDomain& D, int node) {
   Node<S> N;
-  N.g = reinterpret_cast<S*>(D.g) + (long long)node * kQ * D.ncell;
+  N.g = reinterpret_cast<S*>(D.g) + (long long)node * kQ * D.pitch;
   N.bout = D.bout ? D.bout + (long long)node * D.nz * D.ny * 5 : nullptr;
   N.uinf = D.uin_f + (long long)node * D.nz;
   N.uind = D.uin_d + (long long)node * D.nz * 3;
@@ -475,47 +529,69 @@ __device__ __forceinline__ Node<S> node_view(const DevDomain& D, int node) {
 }
 
 // A tile is a block_x * block_y patch of one x-y plane range, slab_z deep,
-// of one node of one domain.
+// of one node of one domain.  Decoded once per block (32-bit arithmetic; tile
+// counts stay below 2^31) and shared with the block's threads.
 struct TileRef {
   int d, node, x, y, z0, z1;
   bool valid;
 };
 
-__device__ __forceinline__ TileRef decode_tile(const StepParams& P, long long t) {
-  TileRef R;
+struct TileHead {
+  int d, node, x0, y0, z0;
+};
+
+__device__ __forceinline__ TileHead decode_tile_head(const StepParams& P, unsigned t) {
+  TileHead H;
   int d = 0;
   for (int k = 1; k < P.n_domains; ++k)
-    if (t >= P.dom[k].tile_begin) d = k;
+    if ((long long)t >= P.dom[k].tile_begin) d = k;
   const DevDomain& D = P.dom[d];
-  const long long local = t - D.tile_begin;
-  long long ct;
+  const unsigned local = t - (unsigned)D.tile_begin;
+  const unsigned nodes = (unsigned)D.nodes, tpn = (unsigned)D.tiles_per_node;
+  unsigned ct;
   if (P.order == 0) {
-    R.node = (int)(local % D.nodes);
-    ct = local / D.nodes;
+    H.node = (int)(local % nodes);
+    ct = local / nodes;
   } else {
-    R.node = (int)(local / D.tiles_per_node);
-    ct = local % D.tiles_per_node;
+    H.node = (int)(local / tpn);
+    ct = local % tpn;
   }
-  const int tx = (int)(ct % D.tiles_x);
-  const int ty = (int)((ct / D.tiles_x) % D.tiles_y);
-  const int tz = (int)(ct / (D.tiles_x * D.tiles_y));
-  R.d = d;
-  R.x = tx * P.bx + threadIdx.x;
-  R.y = ty * P.by + threadIdx.y;
-  R.z0 = tz * P.bz;
-  R.z1 = min(R.z0 + P.bz, D.nz);
+  const unsigned tx = (unsigned)D.tiles_x, txy = tx * (unsigned)D.tiles_y;
+  const unsigned tz = ct / txy, rem = ct - tz * txy;
+  const unsigned ty = rem / tx;
+  H.d = d;
+  H.x0 = (int)(rem - ty * tx) * P.bx;
+  H.y0 = (int)ty * P.by;
+  H.z0 = (int)tz * P.bz;
+  return H;
+}
+
+// Block-wide decode of tile t: thread (0,0) decodes, the block reads it.
+__device__ __forceinline__ TileRef block_tile(const StepParams& P, unsigned t) {
+  __shared__ TileHead s_head;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_head = decode_tile_head(P, t);
+  __syncthreads();
+  const TileHead H = s_head;
+  TileRef R;
+  const DevDomain& D = P.dom[H.d];
+  R.d = H.d;
+  R.node = H.node;
+  R.x = H.x0 + threadIdx.x;
+  R.y = H.y0 + threadIdx.y;
+  R.z0 = H.z0;
+  R.z1 = min(H.z0 + P.bz, D.nz);
   R.valid = R.x < D.nx && R.y < D.ny;
   return R;
 }
 
 template <class S, bool CG>
-__device__ __forceinline__ void even_tile(const StepParams& P, long long t) {
-  const TileRef R = decode_tile(P, t);
+__device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R) {
   if (!R.valid) return;
   const DevDomain& D = P.dom[R.d];
   const Node<S> N = node_view<S>(D, R.node);
-  for (int z = R.z0; z < R.z1; ++z) {
-    const long long idx = cidx(D, R.x, R.y, z);
+  const int plane = D.nx * D.ny;
+  int idx = R.x + D.nx * (R.y + D.ny * R.z0);
+  for (int z = R.z0; z < R.z1; ++z, idx += plane) {
     const uint32_t lw = __ldg(D.link + idx);
     if (lw & kLinkSolid) continue;
     cell_even<S, CG>(P, D, N, lw, R.y, z, idx);
@@ -523,13 +599,13 @@ __device__ __forceinline__ void even_tile(const StepParams& P, long long t) {
 }
 
 template <class S, bool CG>
-__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, long long t) {
-  const TileRef R = decode_tile(P, t);
+__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R) {
   if (!R.valid) return;
   const DevDomain& D = P.dom[R.d];
   const Node<S> N = node_view<S>(D, R.node);
-  for (int z = R.z0; z < R.z1; ++z) {
-    const long long idx = cidx(D, R.x, R.y, z);
+  const int plane = D.nx * D.ny;
+  int idx = R.x + D.nx * (R.y + D.ny * R.z0);
+  for (int z = R.z0; z < R.z1; ++z, idx += plane) {
     const uint32_t lw = __ldg(D.link + idx);
     if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
     cell_odd_bulk<S, CG>(P, D, N, lw, idx);
@@ -553,7 +629,7 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   const int y = (int)((idx / D.nx) % D.ny);
   const int z = (int)(idx / ((long long)D.nx * D.ny));
   const uint32_t lw = __ldg(D.link + idx);
-  cell_odd<S, CG>(P, D, node_view<S>(D, node), lw, x, y, z, idx, T(r), T(r1));
+  cell_odd_general<S, CG>(P, D, node_view<S>(D, node), lw, x, y, z, idx, T(r), T(r1));
 }
 
 __device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long m) {
@@ -561,54 +637,307 @@ __device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long
   return P.ramp_f[k];
 }
 
-__device__ __forceinline__ unsigned long long begin_step(const StepParams& P) {
-  __shared__ unsigned long long s_n;
-  if (threadIdx.x == 0 && threadIdx.y == 0) s_n = *reinterpret_cast<volatile unsigned long long*>(P.step);
-  __syncthreads();
-  return s_n;
-}
-
-// The last block to finish advances the device time-level counter.
-__device__ __forceinline__ void end_step(const StepParams& P, unsigned long long n) {
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    __threadfence();
-    const unsigned int ticket = atomicAdd(P.done, 1u);
-    if (ticket == gridDim.x - 1) {
-      *P.done = 0u;
-      *P.step = n + 1;
-      __threadfence();
-    }
-  }
-}
-
-// Even time level for every (domain, node, tile).  The time level comes from
-// the device counter so that a captured graph replays without new
-// parameters.
-template <class S>
-__global__ void __launch_bounds__(256, 4) aa_even_kernel(const __grid_constant__ StepParams P) {
-  const unsigned long long n = begin_step(P);
-  even_tile<S, false>(P, blockIdx.x);
-  end_step(P, n);
+// Even time level for every (domain, node, tile).  The even level carries no
+// boundary term, so its launches have no time-dependent parameter.
+// MINB: resident blocks of 256 threads the register budget is sized for
+// (4: at most 64 registers; 3: at most 85), chosen by the autotuner.
+template <class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constant__ StepParams P) {
+  even_tile<S, false>(P, block_tile(P, blockIdx.x));
 }
 
 // Odd time level, bulk cells of every tile.  Needs no time level: the bulk
 // links carry no boundary term.
-template <class S>
-__global__ void __launch_bounds__(256, 4) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
-  odd_bulk_tile<S, false>(P, blockIdx.x);
+template <class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
+  odd_bulk_tile<S, false>(P, block_tile(P, blockIdx.x));
 }
 
 // Odd time level, listed boundary cells (launched after the bulk kernel of the
-// same level; the two touch disjoint slots).  Advances the time level.
+// same level; the two touch disjoint slots).  The inflow ramp factors of the
+// odd level n (pulls, r(n)) and of level n + 1 (pushes) come with the launch.
 template <class S>
 __global__ void __launch_bounds__(256) aa_odd_boundary_kernel(const __grid_constant__ StepParams P) {
-  const unsigned long long n = begin_step(P);
   const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-  odd_boundary_item<S, false>(P, item, ramp_at(P, n), ramp_at(P, n + 1));
-  end_step(P, n);
+  odd_boundary_item<S, false>(P, item, P.r_pull, P.r_push);
 }
 
+// ------------------------------------------------------------ TMA-staged bulk kernels
+// Warp-specialised pipeline: 8 consumer warps (one cell of a 256-cell run per
+// thread) compute from shared memory while one producer warp keeps kStages
+// runs in flight with 1-D bulk copies.  full[s] completes when the bytes of
+// stage s have landed (transaction count); empty[s] when the 8 consumer warps
+// are done with it.
+constexpr int kStages = 4;
+constexpr int kConsumerWarps = kRun / 32;
+constexpr int kTmaThreads = kRun + 32;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr long long kMbarPolls = 1LL << 22;  // bounded mbarrier polls (each may suspend briefly)
+
+// Bounded wait for a phase of an mbarrier; latches kErrTimeout on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, const StepParams& P) {
+  const long long limit = P.spin_limit < kMbarPolls ? P.spin_limit : kMbarPolls;
+  for (long long k = 0; k < limit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(P.err, kErrTimeout);
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"(smem_u32(ssrc)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// A run is kRun consecutive cells of one node of one domain.
+struct RunRef {
+  int d, node;
+  long long c0;
+};
+__device__ __forceinline__ RunRef decode_run(const StepParams& P, long long r) {
+  RunRef R;
+  int d = 0;
+  for (int k = 1; k < P.n_domains; ++k)
+    if (r >= P.dom[k].run_begin) d = k;
+  const DevDomain& D = P.dom[d];
+  const unsigned local = (unsigned)(r - D.run_begin);
+  unsigned k;
+  if (P.order == 0) {
+    R.node = (int)(local % (unsigned)D.nodes);
+    k = local / (unsigned)D.nodes;
+  } else {
+    R.node = (int)(local / (unsigned)D.runs_per_node);
+    k = local % (unsigned)D.runs_per_node;
+  }
+  R.d = d;
+  R.c0 = (long long)k * kRun;
+  return R;
+}
+
+template <class S>
+__device__ __forceinline__ S* run_rows(const StepParams& P, const RunRef& R) {
+  const DevDomain& D = P.dom[R.d];
+  return reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + R.c0;
+}
+
+// Producer: after an expired wait, wait (bounded) for the loads still in
+// flight before the CTA leaves.
+__device__ __forceinline__ void drain_loads(uint64_t* full, long long from, long long to) {
+  for (long long j = from; j < to; ++j)
+    for (long long k = 0; k < kMbarPolls; ++k)
+      if (mbar_try_wait(&full[j % kStages], (unsigned)((j / kStages) & 1))) break;
+}
+
+template <class S>
+__device__ __forceinline__ void even_issue_load(const StepParams& P, long long r, S* stage, uint64_t* full) {
+  const RunRef R = decode_run(P, r);
+  const DevDomain& D = P.dom[R.d];
+  const S* src = run_rows<S>(P, R);
+  mbar_expect_tx(full, kQ * kRun * sizeof(S));
+  for (int k = 0; k < kQ; ++k) bulk_load(stage + k * kRun, src + (long long)k * D.pitch, kRun * sizeof(S), full);
+}
+
+template <class S>
+__device__ __forceinline__ void even_issue_store(const StepParams& P, long long r, const S* stage) {
+  const RunRef R = decode_run(P, r);
+  const DevDomain& D = P.dom[R.d];
+  S* dst = run_rows<S>(P, R);
+  for (int k = 0; k < kQ; ++k) bulk_store(dst + (long long)k * D.pitch, stage + k * kRun, kRun * sizeof(S));
+  bulk_commit();
+}
+
+// Even level, TMA-staged.  The consumers collide in place in the stage
+// (opposite rows) and the producer streams the stage back with bulk stores.
+template <class S>
+__global__ void __launch_bounds__(kTmaThreads, 2) aa_even_tma_kernel(const __grid_constant__ StepParams P) {
+  using T = typename Store<S>::C;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S* buf = reinterpret_cast<S*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kQ * kRun * sizeof(S));
+  uint64_t* empty = full + kStages;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long first = blockIdx.x, stride = gridDim.x;
+  const long long iters = P.total_runs > first ? (P.total_runs - first + stride - 1) / stride : 0;
+  if (warp == kConsumerWarps) {
+    if (lane != 0) return;
+    long long loaded = 0;
+    for (; loaded < iters && loaded < kStages; ++loaded)
+      even_issue_load<S>(P, first + loaded * stride, buf + (loaded % kStages) * kQ * kRun, &full[loaded % kStages]);
+    for (long long k = 0; k < iters; ++k) {
+      const int s = (int)(k % kStages);
+      if (!mbar_wait(&empty[s], (unsigned)((k / kStages) & 1), P)) {
+        drain_loads(full, k, loaded);
+        break;
+      }
+      even_issue_store<S>(P, first + k * stride, buf + s * kQ * kRun);
+      // refill the stage of iteration k - 1 once its stores have read it
+      if (k >= 1 && loaded < iters) {
+        bulk_wait_read_le1();
+        const int sp = (int)((k - 1) % kStages);
+        even_issue_load<S>(P, first + loaded * stride, buf + sp * kQ * kRun, &full[sp]);
+        ++loaded;
+      }
+    }
+    bulk_wait_all();
+    return;
+  }
+  for (long long k = 0; k < iters; ++k) {
+    const int s = (int)(k % kStages);
+    if (!mbar_wait(&full[s], (unsigned)((k / kStages) & 1), P)) break;
+    const RunRef R = decode_run(P, first + k * stride);
+    const DevDomain& D = P.dom[R.d];
+    S* sb = buf + s * kQ * kRun;
+    const long long c = R.c0 + tid;
+    T g[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(sb + i * kRun + tid);
+    const uint32_t lw = c < D.ncell ? __ldg(D.link + c) : kLinkSolid;
+    if (!(lw & kLinkSolid)) {
+      collide_p<T, true>(P, g);
+      if (lw & kLinkOutlet) {
+        const int y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
+        save_outlet<S>(D, node_view<S>(D, R.node), y, z, g);
+      }
+    }
+    // solid and padding cells only swap their (never read) slots
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) Store<S>::st(sb + OPP(i) * kRun + tid, g[i]);
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void odd_issue_load(const StepParams& P, long long r, S* stage, uint64_t* full) {
+  constexpr int PADE = 16 / sizeof(S);
+  constexpr int RW = kRun + 2 * PADE;
+  const RunRef R = decode_run(P, r);
+  const DevDomain& D = P.dom[R.d];
+  const S* src = run_rows<S>(P, R);
+  const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+  mbar_expect_tx(full, kQ * RW * sizeof(S));
+#pragma unroll
+  for (int k = 0; k < kQ; ++k)
+    bulk_load(stage + k * RW, src + (long long)k * D.pitch + CY(k) * sy + CZ(k) * sz - PADE, RW * sizeof(S), full);
+}
+
+// Odd level bulk cells, TMA-staged loads: row k of a run is read at the
+// window c0 + off(k) - c_kx - PADE .. + kRun + 2 PADE (16-byte aligned), the
+// value for cell t sits at t + PADE + c_kx.  Bounce-back links read the own
+// slot from global memory; stores go straight to global memory.
+template <class S>
+__global__ void __launch_bounds__(kTmaThreads, 2) aa_odd_tma_kernel(const __grid_constant__ StepParams P) {
+  using T = typename Store<S>::C;
+  constexpr int PADE = 16 / sizeof(S);
+  constexpr int RW = kRun + 2 * PADE;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S* buf = reinterpret_cast<S*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kQ * RW * sizeof(S));
+  uint64_t* empty = full + kStages;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long first = blockIdx.x, stride = gridDim.x;
+  const long long iters = P.total_runs > first ? (P.total_runs - first + stride - 1) / stride : 0;
+  if (warp == kConsumerWarps) {
+    if (lane != 0) return;
+    long long loaded = 0;
+    for (; loaded < iters && loaded < kStages; ++loaded)
+      odd_issue_load<S>(P, first + loaded * stride, buf + (loaded % kStages) * kQ * RW, &full[loaded % kStages]);
+    for (long long k = 0; loaded < iters; ++k) {
+      const int s = (int)(k % kStages);
+      if (!mbar_wait(&empty[s], (unsigned)((k / kStages) & 1), P)) {
+        drain_loads(full, k, loaded);
+        return;
+      }
+      odd_issue_load<S>(P, first + loaded * stride, buf + s * kQ * RW, &full[s]);
+      ++loaded;
+    }
+    return;
+  }
+  for (long long k = 0; k < iters; ++k) {
+    const int s = (int)(k % kStages);
+    if (!mbar_wait(&full[s], (unsigned)((k / kStages) & 1), P)) break;
+    const RunRef R = decode_run(P, first + k * stride);
+    const DevDomain& D = P.dom[R.d];
+    const S* sb = buf + s * kQ * RW;
+    const long long c = R.c0 + tid;
+    const uint32_t lw = c < D.ncell ? __ldg(D.link + c) : kLinkSlow;
+    T g[kQ];
+    const bool bulk = !(lw & kLinkSlow);
+    if (bulk) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(sb + OPP(i) * RW + tid + PADE + CX(OPP(i)));
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);  // stage s is no longer read
+    if (bulk) {
+      S* base = reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + c;
+      const int pc = (int)D.pitch, sy = D.nx, sz = D.nx * D.ny;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i)
+        if ((lw >> i) & 1u) g[i] = Store<S>::ld(base + i * pc);
+      collide_p<T, true>(P, g);
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) {
+        const int stream = j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz);
+        Store<S>::st(base + ((lw >> OPP(j)) & 1u ? OPP(j) * pc : stream), g[j]);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ persistent form
 // Bounded grid barrier (sense by generation).  Gives up after spin_limit
 // polls, latches kErrTimeout and returns false; every block then leaves.
 __device__ bool grid_barrier(const StepParams& P, unsigned int& gen) {
@@ -643,14 +972,14 @@ __device__ bool grid_barrier(const StepParams& P, unsigned int& gen) {
   return s_ok != 0;
 }
 
-// Persistent form: one cooperative launch advances n_steps; blocks stride over
-// the work of each level and meet at a grid barrier between time steps.
+// One cooperative launch advances n_steps; blocks stride over the work of
+// each level and meet at a grid barrier between time steps.
 template <class S>
 __global__ void __launch_bounds__(256) aa_persistent_kernel(const __grid_constant__ StepParams P) {
   __shared__ unsigned long long s_n;
   __shared__ unsigned int s_gen;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    s_n = *reinterpret_cast<volatile unsigned long long*>(P.step);
+    s_n = P.n_host;
     s_gen = *reinterpret_cast<volatile unsigned int*>(P.bar_gen);
   }
   __syncthreads();
@@ -660,29 +989,35 @@ __global__ void __launch_bounds__(256) aa_persistent_kernel(const __grid_constan
   const long long bblocks = (P.total_bitems + threads - 1) / threads;
   for (int s = 0; s < P.n_steps; ++s) {
     if ((n & 1ull) == 0) {
-      for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) even_tile<S, true>(P, t);
-    } else {
-      const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
-      for (long long b = blockIdx.x; b < P.total_tiles + bblocks; b += gridDim.x) {
-        if (b < P.total_tiles) odd_bulk_tile<S, true>(P, b);
-        else odd_boundary_item<S, true>(P, (b - P.total_tiles) * threads + threadIdx.y * P.bx + threadIdx.x, r, r1);
+      for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) {
+        even_tile<S, true>(P, block_tile(P, (unsigned)t));
+        __syncthreads();  // the shared tile head is rewritten next iteration
       }
+    } else {
+      for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) {
+        odd_bulk_tile<S, true>(P, block_tile(P, (unsigned)t));
+        __syncthreads();
+      }
+      // bulk and boundary cells touch disjoint slots: no barrier between them
+      const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
+      for (long long b = blockIdx.x; b < bblocks; b += gridDim.x)
+        odd_boundary_item<S, true>(P, b * threads + threadIdx.y * P.bx + threadIdx.x, r, r1);
     }
     if (!grid_barrier(P, gen)) return;
     ++n;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *P.step = n;
 }
 
-// FP64 plain path: two arrays, push form, one node per launch.  Blocks
-// [0, tiles_per_node) take the bulk cells, the rest the listed boundary cells.
+// ------------------------------------------------------------ FP64 plain path
+// Two arrays, push form, one node per launch.  Blocks [0, tiles_per_node)
+// take the bulk cells, the rest the listed boundary cells.
 __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__ StepParams P,
                                                          unsigned long long n) {
   const DevDomain& D = P.dom[P.plain_domain];
   const int node = P.plain_node;
-  const long long nc = D.ncell;
-  double* A = reinterpret_cast<double*>(D.g) + (long long)node * kQ * nc;
-  double* B = reinterpret_cast<double*>(D.g2) + (long long)node * kQ * nc;
+  const long long pc = D.pitch;
+  double* A = reinterpret_cast<double*>(D.g) + (long long)node * kQ * pc;
+  double* B = reinterpret_cast<double*>(D.g2) + (long long)node * kQ * pc;
   const double* src = (n & 1ull) ? B : A;
   double* dst = (n & 1ull) ? A : B;
   const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
@@ -701,12 +1036,12 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
       if (lw & kLinkSlow) continue;
       double g[kQ];
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
+      for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
       collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
 #pragma unroll
       for (int j = 0; j < kQ; ++j) {
-        const long long stream = (long long)j * nc + idx + (CX(j) * sx + CY(j) * sy + CZ(j) * sz);
-        dst[((lw >> OPP(j)) & 1u) ? (long long)OPP(j) * nc + idx : stream] = g[j];
+        const long long stream = (long long)j * pc + idx + (CX(j) * sx + CY(j) * sy + CZ(j) * sz);
+        dst[((lw >> OPP(j)) & 1u) ? (long long)OPP(j) * pc + idx : stream] = g[j];
       }
     }
     return;
@@ -727,34 +1062,18 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   const double r1 = P.ramp_d[m1 < (unsigned long long)P.ramp_steps ? m1 : P.ramp_steps];
   double g[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * nc + idx];
+  for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
   collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
-#pragma unroll
-  for (int j = 0; j < kQ; ++j) {
-    if (!(lw & (1u << OPP(j)))) {
-      const long long off = CX(j) * sx + CY(j) * sy + CZ(j) * sz;
-      dst[(long long)j * nc + idx + off] = g[j];
-    } else {
-      push_special<double>(D, N, dst, j, g[j], x, y, z, idx, r1);
-    }
-  }
-  if (lw & kLinkOutlet) {
-    push_outlet<double>(D, dst, 2, g[2], x, y, z, idx);
-    push_outlet<double>(D, dst, 8, g[8], x, y, z, idx);
-    push_outlet<double>(D, dst, 10, g[10], x, y, z, idx);
-    push_outlet<double>(D, dst, 12, g[12], x, y, z, idx);
-    push_outlet<double>(D, dst, 14, g[14], x, y, z, idx);
-  }
+  push_general<double>(D, N, dst, lw, x, y, z, idx, g, r1);
 }
 
-__global__ void set_counter_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
-
 // ------------------------------------------------------------ initialisation
+// Every slot of every row (padding included): g = 0 (shifted) or f = w.
 template <class S, bool SHIFT>
-__global__ void init_kernel(S* g, long long ncell, long long total) {
+__global__ void init_kernel(S* g, long long pitch, long long total) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)((k / ncell) % kQ);
+    const int i = (int)((k / pitch) % kQ);
     using T = typename Store<S>::C;
     T v = T(0);
     if constexpr (!SHIFT) {
@@ -776,16 +1095,16 @@ __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain
   if constexpr (!SHIFT) {
     // FP64 plain: two arrays, natural layout in the current one
     const double* cur = reinterpret_cast<const double*>((n & 1ull) ? D.g2 : D.g) +
-                        (long long)node * kQ * D.ncell;
+                        (long long)node * kQ * D.pitch;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) g[i] = T(cur[(long long)i * D.ncell + idx]);
+    for (int i = 0; i < kQ; ++i) g[i] = T(cur[(long long)i * D.pitch + idx]);
   } else {
     const Node<S> N = node_view<S>(D, node);
     if ((n & 1ull) == 0) {
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(N.g + (long long)i * D.ncell + idx);
+      for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(N.g + (long long)i * D.pitch + idx);
     } else {
-      load_odd<S, false, true>(D, N, lw, x, y, z, idx, g, T(ramp_at(P, n)));
+      load_odd_general<S, false>(D, N, lw, x, y, z, idx, g, T(ramp_at(P, n)));
     }
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] += W<T>(i);
@@ -808,10 +1127,6 @@ __device__ __forceinline__ void macro(const T g[kQ], T& rho, T& ux, T& uy, T& uz
   uz = jz / rho;
 }
 
-__device__ __forceinline__ unsigned long long read_step(const StepParams& P) {
-  return *reinterpret_cast<volatile unsigned long long*>(P.step);
-}
-
 // Ensemble statistics of |u| per cell (Eq. quad_moments) and the gPC
 // projection (Eq. coef_discrete), FP64 accumulation over the nodes.
 template <class S, bool SHIFT>
@@ -821,7 +1136,7 @@ __global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs 
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool bad = false;
   if (c < D.ncell) {
-    const unsigned long long n = read_step(P);
+    const unsigned long long n = P.n_host;
     const int x = (int)(c % D.nx);
     const int y = (int)((c / D.nx) % D.ny);
     const int z = (int)(c / ((long long)D.nx * D.ny));
@@ -873,7 +1188,7 @@ __global__ void profiles_kernel(const __grid_constant__ StepParams P, MomentArgs
   const int x = A.probes[2 * p], y = A.probes[2 * p + 1];
   const long long c = cidx(D, x, y, z);
   const uint32_t lw = __ldg(D.link + c);
-  const unsigned long long n = read_step(P);
+  const unsigned long long n = P.n_host;
   double s1 = 0.0, s2 = 0.0;
   for (int j = lane; j < A.nq; j += 32) {
     double q = 0.0;
@@ -926,7 +1241,7 @@ __global__ void export_kernel(const __grid_constant__ StepParams P, int domain, 
     return;
   }
   T g[kQ];
-  gather_pops<S, SHIFT>(P, D, node, read_step(P), x, y, z, c, lw, g);
+  gather_pops<S, SHIFT>(P, D, node, P.n_host, x, y, z, c, lw, g);
   if (f)
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[(long long)i * D.ncell + c] = double(g[i]);
@@ -953,12 +1268,12 @@ __global__ void check_kernel(const __grid_constant__ StepParams P, unsigned long
       const long long c = k % D.ncell;
       const int node = (int)(k / D.ncell);
       if (__ldg(D.link + c) & kLinkSolid) continue;
-      const S* g = reinterpret_cast<const S*>(D.g) + (long long)node * kQ * D.ncell;
+      const S* g = reinterpret_cast<const S*>(D.g) + (long long)node * kQ * D.pitch;
       if constexpr (!SHIFT) {
-        if (read_step(P) & 1ull) g = reinterpret_cast<const S*>(D.g2) + (long long)node * kQ * D.ncell;
+        if (P.n_host & 1ull) g = reinterpret_cast<const S*>(D.g2) + (long long)node * kQ * D.pitch;
       }
       double rho = SHIFT ? 1.0 : 0.0;
-      for (int i = 0; i < kQ; ++i) rho += double(Store<S>::ld(g + (long long)i * D.ncell + c));
+      for (int i = 0; i < kQ; ++i) rho += double(Store<S>::ld(g + (long long)i * D.pitch + c));
       if (!(rho > 0.0) || !isfinite(rho)) ++local;
     }
   }
@@ -986,6 +1301,38 @@ int dispatch(int precision, F&& f) {
   }
 }
 
+template <class S>
+size_t even_tma_smem() { return (size_t)kStages * kQ * kRun * sizeof(S) + 2 * kStages * sizeof(uint64_t); }
+template <class S>
+size_t odd_tma_smem() {
+  return (size_t)kStages * kQ * (kRun + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * kStages * sizeof(uint64_t);
+}
+
+template <class S>
+int tma_grid(int* grid) {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0, a = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaFuncSetAttribute(aa_even_tma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)even_tma_smem<S>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(aa_odd_tma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)odd_tma_smem<S>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, aa_even_tma_kernel<S>, kTmaThreads, even_tma_smem<S>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, aa_odd_tma_kernel<S>, kTmaThreads, odd_tma_smem<S>());
+    if (e != cudaSuccess) return (int)e;
+    const int per = a < b ? a : b;
+    if (per < 1) return (int)cudaErrorInvalidConfiguration;
+    cached = sms * per;
+  }
+  *grid = cached;
+  return 0;
+}
+
 }  // namespace
 
 // ======================================================================= launchers
@@ -996,10 +1343,20 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
     using S = std::remove_pointer_t<decltype(tag)>;
     if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
     else {
+      int tgrid = 0;
+      if (P.tma) {
+        int rc = tma_grid<S>(&tgrid);
+        if (rc) return rc;
+        if ((long long)tgrid > P.total_runs) tgrid = (int)P.total_runs;
+      }
       if (parity == 0) {
-        aa_even_kernel<S><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+        if (P.tma) aa_even_tma_kernel<S><<<tgrid, kTmaThreads, even_tma_smem<S>(), s>>>(P);
+        else if (P.regs85) aa_even_kernel<S, 3><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+        else aa_even_kernel<S, 4><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
       } else {
-        aa_odd_bulk_kernel<S><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+        if (P.tma) aa_odd_tma_kernel<S><<<tgrid, kTmaThreads, odd_tma_smem<S>(), s>>>(P);
+        else if (P.regs85) aa_odd_bulk_kernel<S, 3><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+        else aa_odd_bulk_kernel<S, 4><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
         const long long grid = (P.total_bitems + 255) / 256;
         aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
       }
@@ -1047,23 +1404,18 @@ int launch_plain_step(const StepParams& P, unsigned long long n, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int launch_set_counter(unsigned long long* p, unsigned long long v, void* stream) {
-  set_counter_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(p, v);
-  return (int)cudaGetLastError();
-}
-
 int launch_init_equilibrium(const StepParams& P, int precision, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (int d = 0; d < P.n_domains; ++d) {
     const DevDomain& D = P.dom[d];
-    const long long total = (long long)D.nodes * kQ * D.ncell;
+    const long long total = (long long)D.nodes * kQ * D.pitch;
     int rc = dispatch(precision, [&](auto tag) -> int {
       using S = std::remove_pointer_t<decltype(tag)>;
       if constexpr (std::is_same_v<S, double>) {
-        init_kernel<double, false><<<grid_for(total, 256), 256, 0, s>>>((double*)D.g, D.ncell, total);
-        init_kernel<double, false><<<grid_for(total, 256), 256, 0, s>>>((double*)D.g2, D.ncell, total);
+        init_kernel<double, false><<<grid_for(total, 256), 256, 0, s>>>((double*)D.g, D.pitch, total);
+        init_kernel<double, false><<<grid_for(total, 256), 256, 0, s>>>((double*)D.g2, D.pitch, total);
       } else {
-        init_kernel<S, true><<<grid_for(total, 256), 256, 0, s>>>((S*)D.g, D.ncell, total);
+        init_kernel<S, true><<<grid_for(total, 256), 256, 0, s>>>((S*)D.g, D.pitch, total);
       }
       return (int)cudaGetLastError();
     });

@@ -16,6 +16,7 @@ namespace sclbm {
 constexpr int kQ = 19;
 constexpr int kMaxDomains = SC_MAX_DOMAINS;
 constexpr int kMaxGpcP = 20;     // largest gPC basis the reduction kernel keeps in registers
+constexpr int kRun = 256;        // cells per run of the TMA-staged kernels; the row pitch is a multiple
 
 // Link word per cell: bit i (0..18) set when the pull source x - c_i of
 // direction i is not an in-domain fluid cell reached without periodic wrap
@@ -40,7 +41,8 @@ struct DevDomain {
   const uint32_t* link;     // [ncell]
   const float4* uin_f;      // [nodes][nz] (ux, uy, uz, 0)
   const double* uin_d;      // [nodes][nz][3]
-  void* g;                  // [nodes][19][ncell] storage (AA) or FP64 array A
+  long long pitch;          // population row stride (elements), multiple of kRun
+  void* g;                  // [nodes][19][pitch] storage (AA) or FP64 array A
   void* g2;                 // FP64 plain: array B, else null
   float* bout;              // [nodes][nz*ny][5] outflow plane (AA only)
   const int32_t* bcell;     // [nb] fluid cells with a boundary link or on the outlet
@@ -48,6 +50,8 @@ struct DevDomain {
   long long tiles_x, tiles_y, tiles_z, tiles_per_node;
   long long tile_begin;     // first global tile of this domain
   long long bitem_begin;    // first global boundary item (node-major) of this domain
+  long long runs_per_node;  // pitch / kRun
+  long long run_begin;      // first global run of this domain
 };
 
 struct StepParams {
@@ -60,11 +64,14 @@ struct StepParams {
   const float* ramp_f;        // [ramp_steps + 1]
   const double* ramp_d;
   int ramp_steps;
-  unsigned long long* step;   // device step counter (time level of the state)
-  unsigned int* done;         // blocks finished in the current launch
+  unsigned long long n_host;  // time level of the state (observables, persistent start)
+  float r_pull, r_push;       // odd-level launches: ramp r(n) and r(n + 1)
   unsigned int* err;          // latched error bits
   long long total_tiles;       // bulk tiles of all domains and nodes
   long long total_bitems;      // boundary (node, cell) items of all domains
+  long long total_runs;        // runs of kRun cells of all domains and nodes
+  int tma;                     // bulk kernels staged through shared memory by TMA
+  int regs85;                  // per-thread bulk kernels sized for 3 blocks (85 registers)
   int bx, by, bz, order;
   // persistent mode
   unsigned int* bar_count;
@@ -96,7 +103,6 @@ double hn_ramp(int ramp_steps, long long m);
 int launch_aa_step(const StepParams& P, int precision, void* stream, int parity);
 int launch_aa_persistent(const StepParams& P, int precision, void* stream, int grid);
 int launch_plain_step(const StepParams& P, unsigned long long n, void* stream);
-int launch_set_counter(unsigned long long* p, unsigned long long v, void* stream);
 int aa_persistent_max_grid(const StepParams& P, int precision, int* grid);
 int launch_init_equilibrium(const StepParams& P, int precision, void* stream);
 struct MomentArgs {

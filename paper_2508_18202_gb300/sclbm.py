@@ -53,7 +53,8 @@ class sc_lbm_config(C.Structure):
 
 class sc_lbm_tuning(C.Structure):
     _fields_ = [("block_x", C.c_int), ("block_y", C.c_int), ("slab_z", C.c_int),
-                ("tile_order", C.c_int), ("exec_mode", C.c_int), ("graph_steps", C.c_int)]
+                ("tile_order", C.c_int), ("exec_mode", C.c_int), ("graph_steps", C.c_int),
+                ("variant", C.c_int)]
 
 
 # Every exported symbol of include/sclbm.h with its ctypes signature.
@@ -246,8 +247,8 @@ def sc_lbm_autotune(h, cache_path=None):
 
 
 def sc_lbm_set_tuning(h, block_x, block_y, slab_z, tile_order=0, exec_mode=SC_EXEC_LAUNCH,
-                      graph_steps=50):
-    t = sc_lbm_tuning(block_x, block_y, slab_z, tile_order, exec_mode, graph_steps)
+                      graph_steps=50, variant=0):
+    t = sc_lbm_tuning(block_x, block_y, slab_z, tile_order, exec_mode, graph_steps, variant)
     _call("sc_lbm_set_tuning", h, C.byref(t), handle=h)
 
 
@@ -255,7 +256,7 @@ def sc_lbm_get_tuning(h):
     t = sc_lbm_tuning()
     _call("sc_lbm_get_tuning", h, C.byref(t), handle=h)
     return dict(block_x=t.block_x, block_y=t.block_y, slab_z=t.slab_z, tile_order=t.tile_order,
-                exec_mode=t.exec_mode, graph_steps=t.graph_steps)
+                exec_mode=t.exec_mode, graph_steps=t.graph_steps, variant=t.variant)
 
 
 def sc_lbm_counters(h):
