@@ -254,6 +254,39 @@ int sc_lbm_state_size(sc_lbm_t h, size_t* bytes);
 int sc_lbm_save(sc_lbm_t h, void* host_buf, size_t bytes);
 int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes);
 
+/* ------------------------------------------------------------ assimilation
+ * The paper assimilates measured inflow by prescribing it at the boundary
+ * (Sec. 2.4 step 5) and names data assimilation as the purpose (Sec. 1); it
+ * does not differentiate the solver.  These calls add gradient-based
+ * estimation of the inflow parameters from velocity probes.              */
+
+/* Replace the nominal inflow parameters (u_ref, alpha, theta in degrees) and
+ * rebuild every node's inflow table.  Synchronises the handle's stream.    */
+int sc_lbm_set_inflow(sc_lbm_t h, double u_ref, double alpha, double angle_deg);
+
+/* Device bytes the adjoint needs for this domain, step count, checkpoint
+ * count (0 = ceil(sqrt(n_steps))) and probe count (1..256).                */
+int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_snapshots,
+                                  int n_probes, size_t* bytes);
+
+/* Loss and gradient of the probe misfit for one collocation node:
+ *   J = sum_p |u(x_p, T) - u_target_p|^2 at time level T = n_steps of a run
+ *   from the equilibrium at rho = 1, u = 0 with that node's inflow, and
+ *   dJ/d(u_ref, alpha) by the discrete adjoint of the FP32 BGK step (the
+ *   transpose of the collision Jacobian and of the streaming / link rules),
+ *   with the forward states recomputed per segment from n_snapshots
+ *   checkpoints (0 = ceil(sqrt(n_steps))) and the gradient accumulated in
+ *   FP64.  alpha is the node's power-law exponent.
+ * probes: host int32 [n_probes][3] fluid cells; u_target: host double
+ * [n_probes][3]; d_ws: device workspace of sc_lbm_adjoint_workspace_size
+ * bytes (256-byte aligned), caller-owned, overwritten; loss_out: host double;
+ * grad_out: host double[2]; u_probe_out: host double [n_probes][3] or NULL.
+ * Leaves the handle's populations untouched; synchronises.
+ * SC_ERR_UNSUPPORTED when c_smag > 0 (the adjoint covers BGK).            */
+int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int n_probes,
+                   const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
+                   double* loss_out, double* grad_out, double* u_probe_out);
+
 const char* sc_lbm_last_error(sc_lbm_t h);
 int sc_lbm_destroy(sc_lbm_t h);
 

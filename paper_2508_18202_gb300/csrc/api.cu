@@ -248,6 +248,8 @@ struct sc_lbm_s {
   StepParams P;
   std::vector<double> wsum;
   std::vector<int> nq;
+  std::vector<std::vector<double>> Z;         // collocation nodes per domain
+  std::vector<std::vector<uint8_t>> flags;    // solid flags per domain (host copy)
   int gpcP = 0;
   sc_lbm_tuning tune;
   long long steps = 0, launches = 0;
@@ -604,6 +606,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     node_count(&c, d, &Z, &w);
     const int nq = (int)w.size();
     h->nq[d] = nq;
+    h->Z.push_back(Z);
     double ws = 0.0;
     for (double v : w) ws += v;
     h->wsum[d] = ws;
@@ -691,6 +694,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) rc = cuda_fail(h, e, "init sync");
   }
+  h->flags = std::move(flags);
   if (rc) {
     delete h;
     return rc;
@@ -1014,6 +1018,204 @@ int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes) {
   CK(cudaStreamSynchronize(h->stream));
   h->steps = (long long)hd.steps;
   return SC_OK;
+}
+
+// ------------------------------------------------------------ inflow update
+// Node inflow u_in(z) = u_ref (1 + xi) (h/H)^alpha (cos theta, sin theta, 0)
+// with the node's coordinates replacing xi, alpha or theta.
+static void node_inflow(const sc_lbm_config& c, const std::vector<double>& Z, int j, int nz, double* ud,
+                        double* alpha_out) {
+  double xi = 0.0, al = c.alpha, th = c.angle_deg;
+  for (int t = 0; t < c.n_inputs; ++t) {
+    const double zt = Z[(size_t)j * c.n_inputs + t];
+    if (c.inputs[t] == SC_IN_SPEED_REL) xi = zt;
+    else if (c.inputs[t] == SC_IN_ALPHA) al = zt;
+    else th = zt;
+  }
+  const double H = c.H_ref > 0 ? c.H_ref : (double)nz;
+  hn_inflow(nz, c.u_ref, xi, al, H, th, ud);
+  if (alpha_out) *alpha_out = al;
+}
+
+int sc_lbm_set_inflow(sc_lbm_t h, double u_ref, double alpha, double angle_deg) {
+  if (!h || !(u_ref == u_ref) || !(alpha == alpha) || !(angle_deg == angle_deg)) return SC_ERR_ARG;
+  h->cfg.u_ref = u_ref;
+  h->cfg.alpha = alpha;
+  h->cfg.angle_deg = angle_deg;
+  CK(cudaStreamSynchronize(h->stream));
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    const int nz = h->doms[d].nz, nq = h->nq[d];
+    std::vector<double> ud((size_t)nq * nz * 3);
+    std::vector<float> uf((size_t)nq * nz * 4, 0.0f);
+    for (int j = 0; j < nq; ++j) {
+      node_inflow(h->cfg, h->Z[d], j, nz, &ud[(size_t)j * nz * 3], nullptr);
+      for (int k = 0; k < nz; ++k)
+        for (int a = 0; a < 3; ++a) uf[((size_t)j * nz + k) * 4 + a] = (float)ud[((size_t)j * nz + k) * 3 + a];
+    }
+    CK(cudaMemcpy(h->ws + h->L.dom[d].uin_f, uf.data(), sizeof(float) * uf.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->ws + h->L.dom[d].uin_d, ud.data(), sizeof(double) * ud.size(), cudaMemcpyHostToDevice));
+  }
+  return SC_OK;
+}
+
+// ------------------------------------------------------------ adjoint
+namespace {
+struct AdjLayout {
+  size_t accum, probes, target, uprobe, uin, du, states, state_bytes, total;
+  int K, L;
+};
+
+int adj_plan(sc_lbm_t h, int domain, int n_steps, int n_snapshots, int n_probes, AdjLayout& A) {
+  if (domain < 0 || domain >= h->P.n_domains || n_steps < 1 || n_snapshots < 0 || n_probes < 1 ||
+      n_probes > 256)
+    return SC_ERR_ARG;
+  int K = n_snapshots > 0 ? n_snapshots : (int)ceil(sqrt((double)n_steps));
+  if (K > n_steps) K = n_steps;
+  const int L = (n_steps + K - 1) / K;
+  K = (n_steps + L - 1) / L;
+  const DevDomain& D = h->P.dom[domain];
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  A.accum = take(3 * sizeof(double));
+  A.probes = take(3 * sizeof(int32_t) * (size_t)n_probes);
+  A.target = take(3 * sizeof(double) * (size_t)n_probes);
+  A.uprobe = take(3 * sizeof(double) * (size_t)n_probes);
+  A.uin = take(16 * (size_t)D.nz);
+  A.du = take(32 * (size_t)D.nz);
+  A.state_bytes = align_up(sizeof(float) * kQ * (size_t)D.pitch);
+  A.states = off;
+  A.K = K;
+  A.L = L;
+  A.total = off + A.state_bytes * (size_t)(K + L + 4);
+  return SC_OK;
+}
+}  // namespace
+
+int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_snapshots, int n_probes,
+                                  size_t* bytes) {
+  if (!h || !bytes) return SC_ERR_ARG;
+  AdjLayout A;
+  int rc = adj_plan(h, domain, n_steps, n_snapshots, n_probes, A);
+  if (rc) return rc;
+  *bytes = A.total;
+  return SC_OK;
+}
+
+int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int n_probes,
+                   const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
+                   double* loss_out, double* grad_out, double* u_probe_out) {
+  if (!h || !probes || !u_target || !loss_out || !grad_out) return SC_ERR_ARG;
+  if (h->cfg.c_smag != 0.0)
+    return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers BGK (c_smag = 0)");
+  AdjLayout L;
+  int rc = adj_plan(h, domain, n_steps, n_snapshots, n_probes, L);
+  if (rc) return fail(h, rc, "bad adjoint arguments");
+  if (node < 0 || node >= h->nq[domain]) return fail(h, SC_ERR_ARG, "node out of range");
+  if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0 || bytes < L.total) return SC_ERR_WORKSPACE;
+  const DevDomain& D = h->P.dom[domain];
+  for (int p = 0; p < n_probes; ++p) {
+    const int x = probes[3 * p], y = probes[3 * p + 1], z = probes[3 * p + 2];
+    if (x < 0 || x >= D.nx || y < 0 || y >= D.ny || z < 0 || z >= D.nz)
+      return fail(h, SC_ERR_ARG, "probe outside the domain");
+    if (h->flags[domain][(size_t)x + (size_t)D.nx * ((size_t)y + (size_t)D.ny * z)])
+      return fail(h, SC_ERR_ARG, "probe in a solid cell");
+  }
+  char* ws = (char*)d_ws;
+  // host tables: the node's inflow and its derivatives
+  std::vector<double> ud((size_t)D.nz * 3);
+  double al = 0.0;
+  node_inflow(h->cfg, h->Z[domain], node, D.nz, ud.data(), &al);
+  const double H = h->cfg.H_ref > 0 ? h->cfg.H_ref : (double)D.nz;
+  std::vector<float> uin((size_t)D.nz * 4, 0.0f), du((size_t)D.nz * 8, 0.0f);
+  for (int k = 0; k < D.nz; ++k) {
+    const double lh = log(((double)k + 0.5) / H);
+    for (int a = 0; a < 3; ++a) {
+      const double u = ud[3 * k + a];
+      uin[4 * k + a] = (float)u;
+      du[4 * k + a] = (float)(h->cfg.u_ref != 0.0 ? u / h->cfg.u_ref : 0.0);  // d/du_ref
+      du[4 * (D.nz + k) + a] = (float)(u * lh);                               // d/dalpha
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemset(ws + L.accum, 0, 3 * sizeof(double)));
+  CK(cudaMemcpy(ws + L.probes, probes, 3 * sizeof(int32_t) * (size_t)n_probes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ws + L.target, u_target, 3 * sizeof(double) * (size_t)n_probes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ws + L.uin, uin.data(), sizeof(float) * uin.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ws + L.du, du.data(), sizeof(float) * du.size(), cudaMemcpyHostToDevice));
+  AdjArgs A;
+  A.domain = domain;
+  A.uin = (const float4*)(ws + L.uin);
+  A.du = (const float4*)(ws + L.du);
+  A.probes = (const int32_t*)(ws + L.probes);
+  A.target = (const double*)(ws + L.target);
+  A.u_probe = (double*)(ws + L.uprobe);
+  A.n_probes = n_probes;
+  A.accum = (double*)(ws + L.accum);
+  auto state = [&](int k) { return (float*)(ws + L.states + L.state_bytes * (size_t)k); };
+  float* snap0 = state(0);           // K checkpoints
+  float* seg0 = state(L.K);          // L segment states
+  float* lamA = state(L.K + L.L);
+  float* lamB = state(L.K + L.L + 1);
+  float* fa = state(L.K + L.L + 2);
+  float* fb = state(L.K + L.L + 3);
+  const long long nstate = (long long)kQ * D.pitch;
+  const StepParams& P = h->P;
+  auto ck = [&](int r, const char* what) { return r ? cuda_fail(h, (cudaError_t)r, what) : SC_OK; };
+  // forward sweep with checkpoints every L steps, equilibrium start
+  if ((rc = ck(launch_fill_zero(fa, nstate, h->stream), "adjoint fill"))) return rc;
+  if ((rc = ck(launch_fill_zero(fb, nstate, h->stream), "adjoint fill"))) return rc;
+  float* cur = fa;
+  float* nxt = fb;
+  for (int n = 0; n < n_steps; ++n) {
+    if (n % L.L == 0)
+      CK(cudaMemcpyAsync(snap0 + (size_t)(n / L.L) * (L.state_bytes / sizeof(float)), cur,
+                         sizeof(float) * nstate, cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = ck(launch_adj_forward(P, A, cur, nxt, (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
+                 "adjoint forward")))
+      return rc;
+    std::swap(cur, nxt);
+  }
+  // loss and seed at level T
+  if ((rc = ck(launch_fill_zero(lamA, nstate, h->stream), "adjoint fill"))) return rc;
+  if ((rc = ck(launch_fill_zero(lamB, nstate, h->stream), "adjoint fill"))) return rc;
+  if ((rc = ck(launch_adj_loss(P, A, cur, lamA, h->stream), "adjoint loss"))) return rc;
+  float* lnext = lamA;
+  float* lcur = lamB;
+  const size_t sf = L.state_bytes / sizeof(float);
+  for (int sgm = L.K - 1; sgm >= 0; --sgm) {
+    const int n0 = sgm * L.L, n1 = std::min(n0 + L.L, n_steps);
+    CK(cudaMemcpyAsync(seg0, snap0 + (size_t)sgm * sf, sizeof(float) * nstate, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    for (int n = n0; n < n1 - 1; ++n)
+      if ((rc = ck(launch_adj_forward(P, A, seg0 + (size_t)(n - n0) * sf, seg0 + (size_t)(n - n0 + 1) * sf,
+                                      (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
+                   "adjoint recompute")))
+        return rc;
+    for (int n = n1 - 1; n >= n0; --n) {
+      if ((rc = ck(launch_adj_step(P, A, seg0 + (size_t)(n - n0) * sf, lnext, lcur,
+                                   (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
+                   "adjoint step")))
+        return rc;
+      std::swap(lnext, lcur);
+    }
+  }
+  h->launches += 2LL * n_steps + (n_steps - L.K) + 5;
+  double acc[3];
+  CK(cudaMemcpyAsync(acc, ws + L.accum, sizeof acc, cudaMemcpyDeviceToHost, h->stream));
+  if (u_probe_out)
+    CK(cudaMemcpyAsync(u_probe_out, ws + L.uprobe, 3 * sizeof(double) * (size_t)n_probes,
+                       cudaMemcpyDeviceToHost, h->stream));
+  unsigned bits = 0;
+  rc = read_err(h, &bits);
+  if (rc) return rc;
+  *loss_out = acc[0];
+  grad_out[0] = acc[1];
+  grad_out[1] = acc[2];
+  return err_status(h, bits);
 }
 
 const char* sc_lbm_last_error(sc_lbm_t h) {

@@ -1,0 +1,432 @@
+// lbm_device.cuh -- device-side building blocks shared by the forward and the
+// adjoint kernels of libsclbm: D3Q19 tables, population storage types, the
+// BGK(+Smagorinsky) collision, and the per-link boundary rules (in pull form
+// for the odd AA level and in push form for the deliveries).  Included by
+// the CUDA translation units only.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sclbm_internal.h"
+
+namespace sclbm {
+namespace {
+
+// ------------------------------------------------------------ lattice
+__host__ __device__ constexpr int CX(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int CY(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int CZ(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr int C2(int i) { return CX(i) * CX(i) + CY(i) * CY(i) + CZ(i) * CZ(i); }
+template <class T>
+__host__ __device__ constexpr T W(int i) {
+  return C2(i) == 0 ? T(1.0 / 3.0) : (C2(i) == 1 ? T(1.0 / 18.0) : T(1.0 / 36.0));
+}
+__host__ __device__ constexpr int DIR(int x, int y, int z) {
+  for (int i = 0; i < kQ; ++i)
+    if (CX(i) == x && CY(i) == y && CZ(i) == z) return i;
+  return 0;
+}
+// direction i with its component along axis a negated (specular reflection)
+__host__ __device__ constexpr int REFL(int i, int a) {
+  return DIR(a == 0 ? -CX(i) : CX(i), a == 1 ? -CY(i) : CY(i), a == 2 ? -CZ(i) : CZ(i));
+}
+// slot in the outflow plane of the five directions with c_x = -1
+__host__ __device__ constexpr int KOUT(int i) {
+  return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1;
+}
+
+// The same tables for run-time directions (compact boundary code).
+struct LatticeTables {
+  int cx[kQ], cy[kQ], cz[kQ], opp[kQ], kout[kQ], refl[kQ][3];
+  float wf[kQ];
+  double wd[kQ];
+};
+__constant__ LatticeTables c_lat = {
+    {CX(0), CX(1), CX(2), CX(3), CX(4), CX(5), CX(6), CX(7), CX(8), CX(9), CX(10), CX(11), CX(12),
+     CX(13), CX(14), CX(15), CX(16), CX(17), CX(18)},
+    {CY(0), CY(1), CY(2), CY(3), CY(4), CY(5), CY(6), CY(7), CY(8), CY(9), CY(10), CY(11), CY(12),
+     CY(13), CY(14), CY(15), CY(16), CY(17), CY(18)},
+    {CZ(0), CZ(1), CZ(2), CZ(3), CZ(4), CZ(5), CZ(6), CZ(7), CZ(8), CZ(9), CZ(10), CZ(11), CZ(12),
+     CZ(13), CZ(14), CZ(15), CZ(16), CZ(17), CZ(18)},
+    {OPP(0), OPP(1), OPP(2), OPP(3), OPP(4), OPP(5), OPP(6), OPP(7), OPP(8), OPP(9), OPP(10),
+     OPP(11), OPP(12), OPP(13), OPP(14), OPP(15), OPP(16), OPP(17), OPP(18)},
+    {KOUT(0), KOUT(1), KOUT(2), KOUT(3), KOUT(4), KOUT(5), KOUT(6), KOUT(7), KOUT(8), KOUT(9),
+     KOUT(10), KOUT(11), KOUT(12), KOUT(13), KOUT(14), KOUT(15), KOUT(16), KOUT(17), KOUT(18)},
+    {{REFL(0, 0), REFL(0, 1), REFL(0, 2)},    {REFL(1, 0), REFL(1, 1), REFL(1, 2)},
+     {REFL(2, 0), REFL(2, 1), REFL(2, 2)},    {REFL(3, 0), REFL(3, 1), REFL(3, 2)},
+     {REFL(4, 0), REFL(4, 1), REFL(4, 2)},    {REFL(5, 0), REFL(5, 1), REFL(5, 2)},
+     {REFL(6, 0), REFL(6, 1), REFL(6, 2)},    {REFL(7, 0), REFL(7, 1), REFL(7, 2)},
+     {REFL(8, 0), REFL(8, 1), REFL(8, 2)},    {REFL(9, 0), REFL(9, 1), REFL(9, 2)},
+     {REFL(10, 0), REFL(10, 1), REFL(10, 2)}, {REFL(11, 0), REFL(11, 1), REFL(11, 2)},
+     {REFL(12, 0), REFL(12, 1), REFL(12, 2)}, {REFL(13, 0), REFL(13, 1), REFL(13, 2)},
+     {REFL(14, 0), REFL(14, 1), REFL(14, 2)}, {REFL(15, 0), REFL(15, 1), REFL(15, 2)},
+     {REFL(16, 0), REFL(16, 1), REFL(16, 2)}, {REFL(17, 0), REFL(17, 1), REFL(17, 2)},
+     {REFL(18, 0), REFL(18, 1), REFL(18, 2)}},
+    {W<float>(0), W<float>(1), W<float>(2), W<float>(3), W<float>(4), W<float>(5), W<float>(6),
+     W<float>(7), W<float>(8), W<float>(9), W<float>(10), W<float>(11), W<float>(12), W<float>(13),
+     W<float>(14), W<float>(15), W<float>(16), W<float>(17), W<float>(18)},
+    {W<double>(0), W<double>(1), W<double>(2), W<double>(3), W<double>(4), W<double>(5),
+     W<double>(6), W<double>(7), W<double>(8), W<double>(9), W<double>(10), W<double>(11),
+     W<double>(12), W<double>(13), W<double>(14), W<double>(15), W<double>(16), W<double>(17),
+     W<double>(18)},
+};
+
+// ------------------------------------------------------------ storage
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldcg(p));
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<__half> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<double> {
+  using C = double;
+  static __device__ __forceinline__ double ld(const double* p) { return *p; }
+  static __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+
+template <class S, bool CG>
+__device__ __forceinline__ typename Store<S>::C LD(const S* p) {
+  if constexpr (CG) return Store<S>::ldcg(p);
+  else return Store<S>::ld(p);
+}
+
+// ------------------------------------------------------------ collision
+// Correctly rounded reciprocal (the same value as 1 / x in IEEE arithmetic).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
+// BGK with the Smagorinsky effective relaxation time (Sec. 2.2).  SHIFT:
+// populations are g = f - w.  The non-equilibrium stress uses the exact
+// second moment of the D3Q19 second-order equilibrium, rho/3 I + rho u u.
+template <class T, bool SHIFT>
+__device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_on) {
+  T m0 = T(0), jx = T(0), jy = T(0), jz = T(0);
+  T pxx = T(0), pyy = T(0), pzz = T(0), pxy = T(0), pxz = T(0), pyz = T(0);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    m0 += g[i];
+    if (CX(i)) jx += CX(i) > 0 ? g[i] : -g[i];
+    if (CY(i)) jy += CY(i) > 0 ? g[i] : -g[i];
+    if (CZ(i)) jz += CZ(i) > 0 ? g[i] : -g[i];
+    if (CX(i)) pxx += g[i];
+    if (CY(i)) pyy += g[i];
+    if (CZ(i)) pzz += g[i];
+    if (CX(i) * CY(i)) pxy += CX(i) * CY(i) > 0 ? g[i] : -g[i];
+    if (CX(i) * CZ(i)) pxz += CX(i) * CZ(i) > 0 ? g[i] : -g[i];
+    if (CY(i) * CZ(i)) pyz += CY(i) * CZ(i) > 0 ? g[i] : -g[i];
+  }
+  const T rho = SHIFT ? T(1) + m0 : m0;
+  const T inv = recip(rho);
+  const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const T usq = ux * ux + uy * uy + uz * uz;
+  T tau = tau0;
+  if (smag_on) {
+    // Pi^neq = sum c c g - (m0/3 I + rho u u); m0 = rho - 1 (shifted) or rho
+    const T third = m0 * T(1.0 / 3.0);
+    const T nxx = pxx - third - rho * ux * ux;
+    const T nyy = pyy - third - rho * uy * uy;
+    const T nzz = pzz - third - rho * uz * uz;
+    const T nxy = pxy - rho * ux * uy;
+    const T nxz = pxz - rho * ux * uz;
+    const T nyz = pyz - rho * uy * uz;
+    const T pipi = nxx * nxx + nyy * nyy + nzz * nzz + T(2) * (nxy * nxy + nxz * nxz + nyz * nyz);
+    const T pin = sqrt(T(2) * pipi + T(1e-30));
+    tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + smag18c2 * pin * inv));
+  }
+  const T omega = recip(tau);
+  const T base = m0;  // shifted: w (rho - 1) part; plain: w rho part
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const T cu = T(CX(i)) * ux + T(CY(i)) * uy + T(CZ(i)) * uz;
+    const T geq = W<T>(i) * (base + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+    g[i] = g[i] - omega * (g[i] - geq);
+  }
+}
+
+template <class T, bool SHIFT>
+__device__ __forceinline__ void collide_p(const StepParams& P, T g[kQ]) {
+  if constexpr (sizeof(T) == 8)
+    collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
+  else
+    collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+}
+
+// ------------------------------------------------------------ boundary helpers
+struct Cross {
+  int n;        // faces crossed (0, 1, 2)
+  int f[2];     // face ids
+  int p[3];     // position with periodic axes wrapped
+};
+
+__device__ __forceinline__ Cross classify(const DevDomain& D, int px, int py, int pz) {
+  Cross c;
+  c.n = 0;
+  c.f[0] = c.f[1] = -1;
+  int p[3] = {px, py, pz};
+  const int n[3] = {D.nx, D.ny, D.nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (D.bc[2 * a] == SC_BC_PERIODIC) {
+      if (p[a] < 0) p[a] += n[a];
+      else if (p[a] >= n[a]) p[a] -= n[a];
+    } else if (p[a] < 0) {
+      c.f[c.n < 2 ? c.n : 1] = 2 * a;
+      ++c.n;
+    } else if (p[a] >= n[a]) {
+      c.f[c.n < 2 ? c.n : 1] = 2 * a + 1;
+      ++c.n;
+    }
+  }
+  c.p[0] = p[0];
+  c.p[1] = p[1];
+  c.p[2] = p[2];
+  return c;
+}
+
+__device__ __forceinline__ long long cidx(const DevDomain& D, int x, int y, int z) {
+  return (long long)x + (long long)D.nx * ((long long)y + (long long)D.ny * z);
+}
+
+// Per-node pointers.
+template <class S>
+struct Node {
+  S* g;                // [19][pitch]
+  float* bout;         // [nz*ny][5]
+  const float4* uinf;  // [nz]
+  const double* uind;  // [nz][3]
+};
+
+// Inflow correction 6 w_i rho_w (c_i . u_w(z)) r of direction i (rho_w = 1).
+template <class S, class T>
+__device__ __forceinline__ T vel_term(const Node<S>& N, int i, int z, T r) {
+  if constexpr (sizeof(T) == 8) {
+    const double* u = N.uind + 3 * z;
+    const T cu = T(c_lat.cx[i]) * T(u[0]) + T(c_lat.cy[i]) * T(u[1]) + T(c_lat.cz[i]) * T(u[2]);
+    return T(6) * T(c_lat.wd[i]) * cu * r;
+  } else {
+    const float4 u = N.uinf[z];
+    const T cu = T(c_lat.cx[i]) * T(u.x) + T(c_lat.cy[i]) * T(u.y) + T(c_lat.cz[i]) * T(u.z);
+    return T(6) * T(c_lat.wf[i]) * cu * r;
+  }
+}
+
+// f_i of time level n (odd, AA swapped layout) for a boundary link.
+template <class S, bool CG>
+__device__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
+                                             int y, int z, long long idx,
+                                             typename Store<S>::C r) {
+  using T = typename Store<S>::C;
+  const long long pc = D.pitch;
+  const int cx = c_lat.cx[i], cy = c_lat.cy[i], cz = c_lat.cz[i];
+  const Cross c = classify(D, x - cx, y - cy, z - cz);
+  const T own = LD<S, CG>(N.g + (long long)i * pc + idx);  // f*_opp(i)(x)
+  if (c.n == 0) {
+    const long long p = cidx(D, c.p[0], c.p[1], c.p[2]);
+    if (D.flags[p] == 0) return LD<S, CG>(N.g + (long long)c_lat.opp[i] * pc + p);
+    return own;
+  }
+  if (c.n == 1) {
+    const int kind = D.bc[c.f[0]];
+    if (kind == SC_BC_BOUNCE_BACK) return own;
+    if (kind == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
+    const int a = c.f[0] >> 1;
+    int s[3] = {x - cx, y - cy, z - cz};
+    s[a] = a == 0 ? x : (a == 1 ? y : z);
+    const Cross cs = classify(D, s[0], s[1], s[2]);
+    const long long sp = cidx(D, cs.p[0], cs.p[1], cs.p[2]);
+    if (kind == SC_BC_FREE_SLIP) {
+      if (D.flags[sp] == 0) return LD<S, CG>(N.g + (long long)c_lat.opp[c_lat.refl[i][a]] * pc + sp);
+      return own;
+    }
+    // OUTFLOW on +x: transverse source on the outlet plane
+    if (D.flags[sp] == 0)
+      return T(__ldcg(N.bout + ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + c_lat.kout[i]));
+    return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + c_lat.kout[i]));
+  }
+  const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
+  if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) return own;
+  if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
+  if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) return own;
+  // outflow + free slip: own population reflected across the free-slip face
+  const int fs = (k0 == SC_BC_FREE_SLIP) ? c.f[0] : c.f[1];
+  return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + c_lat.kout[c_lat.refl[i][fs >> 1]]));
+}
+
+// Deliver f*_j of cell x for a boundary link into dst (AA: dst == src array).
+template <class S>
+__device__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
+                             typename Store<S>::C v, int x, int y, int z, long long idx,
+                             typename Store<S>::C r1) {
+  using T = typename Store<S>::C;
+  const long long pc = D.pitch;
+  const int cx = c_lat.cx[j], cy = c_lat.cy[j], cz = c_lat.cz[j], oj = c_lat.opp[j];
+  const Cross c = classify(D, x + cx, y + cy, z + cz);
+  S* own = dst + (long long)oj * pc + idx;
+  if (c.n == 0) {
+    const long long q = cidx(D, c.p[0], c.p[1], c.p[2]);
+    if (D.flags[q] == 0) Store<S>::st(dst + (long long)j * pc + q, v);
+    else Store<S>::st(own, v);
+    return;
+  }
+  if (c.n == 1) {
+    const int kind = D.bc[c.f[0]];
+    if (kind == SC_BC_BOUNCE_BACK) {
+      Store<S>::st(own, v);
+    } else if (kind == SC_BC_VELOCITY) {
+      Store<S>::st(own, v + vel_term<S, T>(N, oj, z, r1));
+    } else if (kind == SC_BC_FREE_SLIP) {
+      const int a = c.f[0] >> 1;
+      int t[3] = {x + cx, y + cy, z + cz};
+      t[a] = a == 0 ? x : (a == 1 ? y : z);
+      const Cross ct = classify(D, t[0], t[1], t[2]);
+      const long long tp = cidx(D, ct.p[0], ct.p[1], ct.p[2]);
+      if (D.flags[tp] == 0) Store<S>::st(dst + (long long)c_lat.refl[j][a] * pc + tp, v);
+      else Store<S>::st(own, v);
+    }
+    // OUTFLOW: the population leaves the domain
+    return;
+  }
+  const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
+  if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) {
+    Store<S>::st(own, v);
+  } else if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) {
+    Store<S>::st(own, v + vel_term<S, T>(N, oj, z, r1));
+  } else if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) {
+    Store<S>::st(own, v);
+  }
+  // outflow + free slip: delivered by the outlet pushes of the reflected direction
+}
+
+// Outlet cell (x = nx-1, +x OUTFLOW): deliver f*_j (c_jx = -1) to the outlet
+// links that read it.
+template <class S>
+__device__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x, int y,
+                            int z, long long idx) {
+  const long long pc = D.pitch;
+  const int cy = c_lat.cy[j], cz = c_lat.cz[j];
+  // (1) transverse neighbour on the outlet plane copies it
+  {
+    const Cross c = classify(D, x, y + cy, z + cz);
+    if (c.n == 0) {
+      const long long t = cidx(D, c.p[0], c.p[1], c.p[2]);
+      if (D.flags[t] == 0) Store<S>::st(dst + (long long)j * pc + t, v);
+    }
+  }
+  // (2) own link j whose transverse source is solid falls back to own value
+  {
+    const Cross c = classify(D, x, y - cy, z - cz);
+    if (c.n == 0 && D.flags[cidx(D, c.p[0], c.p[1], c.p[2])] != 0)
+      Store<S>::st(dst + (long long)j * pc + idx, v);
+  }
+  // (3) outflow + free-slip edge: reflected copy into the own cell
+  for (int a = 1; a < 3; ++a) {
+    const int cj = a == 1 ? cy : cz;
+    if (cj == 0) continue;
+    const int face = 2 * a + (cj > 0 ? 1 : 0);
+    const int pos = (a == 1 ? y : z) + cj;
+    const int lim = a == 1 ? D.ny : D.nz;
+    if (D.bc[face] == SC_BC_FREE_SLIP && (pos < 0 || pos >= lim))
+      Store<S>::st(dst + (long long)c_lat.refl[j][a] * pc + idx, v);
+  }
+}
+
+__device__ __forceinline__ long long link_offset(const DevDomain& D, int i) {
+  return (long long)c_lat.cx[i] + (long long)c_lat.cy[i] * D.nx + (long long)c_lat.cz[i] * D.nx * D.ny;
+}
+
+// f_i of the odd time level at a cell, any link kind (run-time loop, compact).
+template <class S, bool CG>
+__device__ void load_odd_general(const DevDomain& D, const Node<S>& N, uint32_t lw, int x, int y,
+                                 int z, long long idx, typename Store<S>::C g[kQ],
+                                 typename Store<S>::C r) {
+#pragma unroll 1
+  for (int i = 0; i < kQ; ++i) {
+    if (!((lw >> i) & 1u))
+      g[i] = LD<S, CG>(N.g + (long long)c_lat.opp[i] * D.pitch + idx - link_offset(D, i));
+    else
+      g[i] = pull_special<S, CG>(D, N, i, x, y, z, idx, r);
+  }
+}
+
+// Push of the odd level (or of the FP64 two-array path) for a cell with
+// boundary links, any link kind.
+template <class S>
+__device__ void push_general(const DevDomain& D, const Node<S>& N, S* dst, uint32_t lw, int x, int y,
+                             int z, long long idx, const typename Store<S>::C g[kQ],
+                             typename Store<S>::C r1) {
+#pragma unroll 1
+  for (int j = 0; j < kQ; ++j) {
+    if (!((lw >> c_lat.opp[j]) & 1u))
+      Store<S>::st(dst + (long long)j * D.pitch + idx + link_offset(D, j), g[j]);
+    else
+      push_special<S>(D, N, dst, j, g[j], x, y, z, idx, r1);
+  }
+  if (lw & kLinkOutlet) {
+    push_outlet<S>(D, dst, 2, g[2], x, y, z, idx);
+    push_outlet<S>(D, dst, 8, g[8], x, y, z, idx);
+    push_outlet<S>(D, dst, 10, g[10], x, y, z, idx);
+    push_outlet<S>(D, dst, 12, g[12], x, y, z, idx);
+    push_outlet<S>(D, dst, 14, g[14], x, y, z, idx);
+  }
+}
+
+// ------------------------------------------------------------ per-node views
+template <class S>
+__device__ __forceinline__ Node<S> node_view(const DevDomain& D, int node) {
+  Node<S> N;
+  N.g = reinterpret_cast<S*>(D.g) + (long long)node * kQ * D.pitch;
+  N.bout = D.bout ? D.bout + (long long)node * D.nz * D.ny * 5 : nullptr;
+  N.uinf = D.uin_f + (long long)node * D.nz;
+  N.uind = D.uin_d + (long long)node * D.nz * 3;
+  return N;
+}
+
+// Outlet cells save their five post-collision populations with c_x = -1
+// into the outflow plane at even levels.
+template <class S>
+__device__ __forceinline__ void save_outlet(const DevDomain& D, const Node<S>& N, int y, int z,
+                                            const typename Store<S>::C g[kQ]) {
+  float* b = N.bout + ((long long)z * D.ny + y) * 5;
+  b[0] = float(g[2]);
+  b[1] = float(g[8]);
+  b[2] = float(g[10]);
+  b[3] = float(g[12]);
+  b[4] = float(g[14]);
+}
+
+}  // namespace
+}  // namespace sclbm

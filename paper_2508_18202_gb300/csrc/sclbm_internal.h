@@ -124,4 +124,22 @@ int launch_export(const StepParams& P, int precision, int domain, int node, doub
                   float* d_u, void* stream);
 int launch_check(const StepParams& P, int precision, unsigned long long* d_count, void* stream);
 
+// Adjoint of one node's time step (adjoint.cu).
+struct AdjArgs {
+  int domain;
+  const float4* uin;      // [nz] inflow of the node
+  const float4* du;       // [2][nz] d u_in / d u_ref, d u_in / d alpha
+  const int32_t* probes;  // [n_probes][3]
+  const double* target;   // [n_probes][3]
+  double* u_probe;        // [n_probes][3]
+  int n_probes;
+  double* accum;          // [0] loss, [1] dJ/du_ref, [2] dJ/dalpha
+};
+int launch_adj_forward(const StepParams& P, const AdjArgs& A, const float* src, float* dst, float r1,
+                       void* stream);
+int launch_adj_loss(const StepParams& P, const AdjArgs& A, const float* f, float* lam, void* stream);
+int launch_adj_step(const StepParams& P, const AdjArgs& A, const float* f, const float* lam_next, float* lam,
+                    float r1, void* stream);
+int launch_fill_zero(float* p, long long n, void* stream);
+
 }  // namespace sclbm

@@ -83,6 +83,11 @@ SIGNATURES = {
     "sc_lbm_state_size": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
     "sc_lbm_save": (C.c_int, [_H, _P, C.c_size_t]),
     "sc_lbm_load": (C.c_int, [_H, _P, C.c_size_t]),
+    "sc_lbm_set_inflow": (C.c_int, [_H, C.c_double, C.c_double, C.c_double]),
+    "sc_lbm_adjoint_workspace_size": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                C.POINTER(C.c_size_t)]),
+    "sc_lbm_adjoint": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, _P, C.c_size_t,
+                                 C.POINTER(C.c_double), _P, _P]),
     "sc_lbm_last_error": (C.c_char_p, [_H]),
     "sc_lbm_destroy": (C.c_int, [_H]),
 }
@@ -293,6 +298,29 @@ def sc_lbm_load(h, buf):
     _call("sc_lbm_load", h, _ptr(buf), buf.nbytes, handle=h)
 
 
+def sc_lbm_set_inflow(h, u_ref, alpha, angle_deg=0.0):
+    _call("sc_lbm_set_inflow", h, float(u_ref), float(alpha), float(angle_deg), handle=h)
+
+
+def sc_lbm_adjoint_workspace_size(h, domain, n_steps, n_snapshots, n_probes):
+    n = C.c_size_t(0)
+    _call("sc_lbm_adjoint_workspace_size", h, domain, n_steps, n_snapshots, n_probes, C.byref(n), handle=h)
+    return n.value
+
+
+def sc_lbm_adjoint(h, domain, node, probes, u_target, n_steps, n_snapshots, ws_ptr, ws_bytes):
+    """Returns (loss, grad[2], u_probe[n][3])."""
+    probes = np.ascontiguousarray(np.asarray(probes, np.int32).reshape(-1, 3))
+    ut = np.ascontiguousarray(np.asarray(u_target, np.float64).reshape(-1, 3))
+    loss = C.c_double(0.0)
+    grad = np.zeros(2)
+    up = np.zeros((probes.shape[0], 3))
+    _call("sc_lbm_adjoint", h, domain, node, probes.ctypes.data, probes.shape[0], ut.ctypes.data,
+          int(n_steps), int(n_snapshots), C.c_void_p(ws_ptr), ws_bytes, C.byref(loss), grad.ctypes.data,
+          up.ctypes.data, handle=h)
+    return loss.value, grad, up
+
+
 def sc_lbm_last_error(h):
     m = lib().sc_lbm_last_error(h)
     return m.decode() if m else ""
@@ -391,3 +419,83 @@ def make_config(workload, **over):
                   w["hi"], w["quad_rule"], w["precision"], ramp_steps=w["ramp_steps"],
                   angle_deg=w.get("angle_deg", 0.0), H_ref=w.get("H_ref", 0.0),
                   gpc_degree=w.get("gpc_degree", -1))
+
+
+# ------------------------------------------------------------------ assimilation
+class Assimilation:
+    """Probe-misfit loss of one collocation node and its adjoint gradient with
+    respect to the inflow parameters (u_ref, alpha)."""
+
+    def __init__(self, ens, probes, u_target, n_steps, n_snapshots=0, domain=0, node=0):
+        import torch
+        self.ens, self.domain, self.node = ens, domain, node
+        self.probes = np.asarray(probes, np.int32).reshape(-1, 3)
+        self.u_target = np.asarray(u_target, np.float64).reshape(-1, 3)
+        self.n_steps, self.n_snapshots = int(n_steps), int(n_snapshots)
+        self.nbytes = sc_lbm_adjoint_workspace_size(ens.h, domain, self.n_steps, self.n_snapshots,
+                                                    self.probes.shape[0])
+        with torch.cuda.stream(ens.stream):
+            self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=ens.device)
+
+    def loss_and_grad(self, u_ref, alpha):
+        c = self.ens.cfg.c
+        sc_lbm_set_inflow(self.ens.h, u_ref, alpha, c.angle_deg)
+        return sc_lbm_adjoint(self.ens.h, self.domain, self.node, self.probes, self.u_target, self.n_steps,
+                              self.n_snapshots, self.ws.data_ptr(), self.nbytes)
+
+
+def _inflow_loss_function():
+    import torch
+
+    class InflowLoss(torch.autograd.Function):
+        """J(theta) for theta = (u_ref, alpha); the backward pass returns the
+        adjoint gradient computed alongside the forward run."""
+
+        @staticmethod
+        def forward(ctx, theta, assim):
+            t = theta.detach().cpu().double().numpy()
+            loss, grad, _ = assim.loss_and_grad(float(t[0]), float(t[1]))
+            ctx.save_for_backward(torch.as_tensor(grad, dtype=theta.dtype, device=theta.device))
+            return torch.as_tensor(loss, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad, None
+
+    return InflowLoss
+
+
+def InflowLoss():
+    """torch.autograd.Function class computing the assimilation loss."""
+    return _inflow_loss_function()
+
+
+def assimilate(assim, theta0, iters=20, scale=(0.05, 0.25), c1=1e-4, step0=0.1):
+    """Gradient descent on the inflow parameters scaled to O(1): the trial step
+    length is the Barzilai-Borwein one (s.s / s.y), accepted under a
+    backtracking Armijo condition, so the loss decreases monotonically.
+    Returns the history of (theta, J)."""
+    scale = np.asarray(scale, np.float64)
+    x = np.asarray(theta0, np.float64) / scale
+    J, g, _ = assim.loss_and_grad(*(x * scale))
+    gx = g * scale
+    hist = [(x * scale, J)]
+    t0 = step0 / max(np.linalg.norm(gx), 1e-300)
+    for _ in range(iters):
+        if not np.any(gx):
+            break
+        t = t0
+        while True:
+            xn = x - t * gx
+            Jn, gn, _ = assim.loss_and_grad(*(xn * scale))
+            if Jn <= J - c1 * t * float(gx @ gx) or t < 1e-14:
+                break
+            t *= 0.5
+        gnx = gn * scale
+        s, y = xn - x, gnx - gx
+        sy = float(s @ y)
+        t0 = float(s @ s) / sy if sy > 0 else 2.0 * t
+        x, J, gx = xn, Jn, gnx
+        hist.append((x * scale, J))
+    return hist
