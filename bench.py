@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--nodes", type=int, default=0,
                     help="profiling case: keep only this many Smolyak levels' worth of nodes (0 = all)")
-    ap.add_argument("--skip", default="", help="comma list of extra legs to skip: plain,storage,cpu,e2e,tune")
+    ap.add_argument("--skip", default="",
+                    help="comma list of extra legs to skip: plain,storage,cpu,e2e,tune,adjoint")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shape block_x,block_y,slab_z,tile_order,exec_mode,graph_steps,variant "
                          "instead of the autotuner")
@@ -388,6 +389,44 @@ def main():
                "note": "per step: sc_lbm_init from pinned host geometry, %d time steps, moments to pinned host" % L}
         del ws
 
+    # ---- adjoint seconds per gradient (128x64x48 urban domain, 2000 steps, 16 probes)
+    adjoint = None
+    if "adjoint" not in skip and rank == 0:
+        aw = W.URBAN_ADJOINT
+        acfg = S.make_config(aw)
+        probes = S.sc_lbm_probe_points(acfg, 0, aw["n_probes"])
+        ae = S.Ensemble(acfg)
+        S.sc_lbm_set_inflow(ae.h, *aw["truth"], 0.0)
+        ae.step(aw["steps"])
+        ua = ae.velocity(0, 0).double().cpu().numpy()
+        AD = aw["domains"][0]
+        target = np.array([ua[:, x + AD["nx"] * (y + AD["ny"] * z)] for x, y, z in probes])
+        assim = S.Assimilation(ae, probes, target, aw["steps"])
+        assim.loss_and_grad(*aw["guess"])  # warm-up
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            Jg, gg, _ = assim.loss_and_grad(*aw["guess"])
+        s_grad = (time.perf_counter() - t0) / reps
+        S.sc_lbm_reset(ae.h)
+        S.sc_lbm_set_inflow(ae.h, *aw["guess"], 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ae.step(aw["steps"])
+        ae.sync()
+        s_fwd = time.perf_counter() - t0
+        acells = AD["nx"] * AD["ny"] * AD["nz"]
+        adjoint = {"value": round(s_grad, 4), "unit": "s/gradient",
+                   "workload": aw["name"], "time_steps": aw["steps"],
+                   "checkpoints": int(np.ceil(np.sqrt(aw["steps"]))),
+                   "forward_s": round(s_fwd, 4), "ratio_to_forward": round(s_grad / s_fwd, 2),
+                   "sweeps_glups": round(3 * acells * aw["steps"] / s_grad / 1e9, 3),
+                   "loss": Jg, "grad": [float(gg[0]), float(gg[1])]}
+        ae.close()
+        del ae, assim
+        torch.cuda.empty_cache()
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if "cpu" not in skip and rank == 0 and world == 1:
@@ -408,11 +447,13 @@ def main():
                        "tuning": tuning},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "peak_kind": peak_kind, "kernel": "aa_step_kernel<float>",
+                         "peak_kind": peak_kind,
+                         "kernel": "one time step: aa_even + (aa_odd_bulk + aa_odd_boundary), averaged per level",
                          "bytes_per_fluid_lup": BYTES_PER_LUP[wl["precision"]],
                          "avg_launch_ms": round(launch_ms, 5), "kernel_hash": khash},
             "fluid_glups": round(glups * fluid / cells, 4),
             "plain_fp64": plain, "storage": storage or None,
+            "adjoint": adjoint,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(k1 - k0),
             "clocks": clk.summary(), "extra": extra,
         }

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
   const DevDomain& D = P.dom[A.domain];
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
-  const uint32_t lw = __ldg(D.link + c);
+  const LinkWord lw = __ldg(D.link + c);
   if (lw & kLinkSolid) return;
   const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
   const long long pc = D.pitch;
@@ -43,20 +43,17 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
 #pragma unroll
   for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + c];
   collide_p<float, true>(P, g);
-  if (!(lw & kLinkSlow)) {
-    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
-#pragma unroll
-    for (int j = 0; j < kQ; ++j) {
-      const long long stream = (long long)j * pc + c + (CX(j) + CY(j) * sy + CZ(j) * sz);
-      dst[((lw >> OPP(j)) & 1u) ? (long long)OPP(j) * pc + c : stream] = g[j];
-    }
-    return;
-  }
   Node<float> N;
   N.g = dst;
   N.bout = nullptr;
   N.uinf = A.uin;
   N.uind = nullptr;
+  if (!(lw & kLinkSlow)) {
+    float ux, uy, uz;
+    wall_velocity<float>(N, lw, z, ux, uy, uz);
+    fast_push<float>(dst + c, lw, (int)pc, D.nx, D.nx * D.ny, ux, uy, uz, r1, g);
+    return;
+  }
   push_general<float>(D, N, dst, lw, x, y, z, c, g, r1);
 }
 
@@ -95,11 +92,11 @@ __global__ void adj_loss_kernel(const __grid_constant__ StepParams P, AdjArgs A,
 // lambda*_k(x): the sum of lambda^{n+1} over every slot that the forward
 // step delivers f*_k(x) to (the transpose of the push rules).
 __device__ float gather_deliveries(const DevDomain& D, const float* lam, int k, int x, int y, int z,
-                                   long long c, uint32_t lw) {
+                                   long long c, LinkWord lw) {
   const long long pc = D.pitch;
   const int cx = c_lat.cx[k], cy = c_lat.cy[k], cz = c_lat.cz[k], ok = c_lat.opp[k];
   float s = 0.0f;
-  if (!((lw >> ok) & 1u)) {
+  if (link_kind(lw, ok) == kStream) {
     s = lam[(long long)k * pc + c + link_offset(D, k)];
   } else {
     const Cross q = classify(D, x + cx, y + cy, z + cz);
@@ -176,7 +173,7 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double gr0 = 0.0, gr1 = 0.0;
   if (c < D.ncell) {
-    const uint32_t lw = __ldg(D.link + c);
+    const LinkWord lw = __ldg(D.link + c);
     if (!(lw & kLinkSolid)) {
       const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
       const long long pc = D.pitch;
@@ -213,11 +210,11 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
       for (int m = 0; m < kQ; ++m)
         lam[(long long)m * pc + c] = (1.0f - om) * ls[m] + om * (al + CX(m) * bx + CY(m) * by + CZ(m) * bz);
       // inflow links of this cell at level n + 1
-      if (lw & kLinkComplex) {
+      if (lw & kLinkVel) {
         const float4 du0 = A.du[z], du1 = A.du[D.nz + z];
 #pragma unroll 1
         for (int i = 1; i < kQ; ++i) {
-          if (!((lw >> i) & 1u) || !velocity_link(D, i, x, y, z)) continue;
+          if (link_kind(lw, i) == kStream || !velocity_link(D, i, x, y, z)) continue;
           const double li = (double)lam_next[(long long)i * pc + c];
           const double pre = 6.0 * c_lat.wd[i] * (double)r1;
           const double d0 = c_lat.cx[i] * (double)du0.x + c_lat.cy[i] * (double)du0.y + c_lat.cz[i] * (double)du0.z;

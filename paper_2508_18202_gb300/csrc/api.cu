@@ -134,7 +134,7 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     M.P = P;
     M.ncell = (long long)D.nx * D.ny * D.nz;
     M.flags = take((size_t)M.ncell);
-    M.link = take(sizeof(uint32_t) * (size_t)M.ncell);
+    M.link = take(sizeof(LinkWord) * (size_t)M.ncell);
     M.bcell = take(sizeof(int32_t) * (size_t)M.ncell);  // boundary list, at most every cell
     M.uin_f = take(16 * (size_t)M.nq * D.nz);
     M.uin_d = take(24 * (size_t)M.nq * D.nz);
@@ -578,7 +578,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
 
   // host tables (kept alive until the stream is synchronised below)
   std::vector<std::vector<uint8_t>> flags(c.n_domains);
-  std::vector<std::vector<uint32_t>> links(c.n_domains);
+  std::vector<std::vector<LinkWord>> links(c.n_domains);
   std::vector<std::vector<int32_t>> bcells(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
@@ -643,7 +643,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     V.ncell = M.ncell;
     for (int f = 0; f < 6; ++f) V.bc[f] = D.bc[f];
     V.flags = (const uint8_t*)(h->ws + M.flags);
-    V.link = (const uint32_t*)(h->ws + M.link);
+    V.link = (const LinkWord*)(h->ws + M.link);
     V.bcell = (const int32_t*)(h->ws + M.bcell);
     V.nb = (long long)bcells[d].size();
     V.uin_f = (const float4*)(h->ws + M.uin_f);
@@ -675,7 +675,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   for (int d = 0; d < c.n_domains && e == cudaSuccess; ++d) {
     const DomLayout& M = L.dom[d];
     e = up(M.flags, flags[d].data(), flags[d].size());
-    if (e == cudaSuccess) e = up(M.link, links[d].data(), sizeof(uint32_t) * links[d].size());
+    if (e == cudaSuccess) e = up(M.link, links[d].data(), sizeof(LinkWord) * links[d].size());
     if (e == cudaSuccess && !bcells[d].empty())
       e = up(M.bcell, bcells[d].data(), sizeof(int32_t) * bcells[d].size());
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());

@@ -313,15 +313,15 @@ int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_
   return SC_OK;
 }
 
-// Per-cell link word: bit i when the pull source x - c_i of direction i is not
-// an in-domain fluid cell reached without a periodic wrap; kLinkComplex when
-// one of those links resolves to anything but plain bounce-back (a solid
-// source, a BOUNCE_BACK face, two faces one of which is BOUNCE_BACK, or two
-// FREE_SLIP faces, whose double reflection is bounce-back).
-void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<uint32_t>& link) {
+// Per-cell link word (see sclbm_internal.h): the kind of each link from the
+// pull rules of the face kinds and the geometry.
+void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<LinkWord>& link) {
   const long long n = (long long)D.nx * D.ny * D.nz;
-  link.assign((size_t)n, 0u);
+  link.assign((size_t)n, 0ull);
   const int dims[3] = {D.nx, D.ny, D.nz};
+  auto fluid_at = [&](const int* q) {
+    return flags[(size_t)q[0] + (size_t)D.nx * ((size_t)q[1] + (size_t)D.ny * q[2])] == 0;
+  };
   for (int z = 0; z < D.nz; ++z)
     for (int y = 0; y < D.ny; ++y)
       for (int x = 0; x < D.nx; ++x) {
@@ -330,10 +330,12 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<ui
           link[c] = kLinkSolid;
           continue;
         }
-        uint32_t word = 0;
-        bool complex_link = false;
+        const int xc[3] = {x, y, z};
+        LinkWord word = 0;
+        bool complex_cell = false, vel = false;
         for (int i = 0; i < kQ; ++i) {
-          int p[3] = {x - kCx[i], y - kCy[i], z - kCz[i]};
+          const int ci[3] = {kCx[i], kCy[i], kCz[i]};
+          int p[3] = {x - ci[0], y - ci[1], z - ci[2]};
           int faces[3], nf = 0;
           bool wrapped = false;
           for (int a = 0; a < 3; ++a) {
@@ -345,34 +347,50 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<ui
               faces[nf++] = 2 * a + (p[a] >= dims[a] ? 1 : 0);
             }
           }
+          int kind = kStream;
           if (nf == 0) {
-            const bool solid = flags[(size_t)p[0] + (size_t)D.nx * ((size_t)p[1] + (size_t)D.ny * p[2])] != 0;
-            if (!solid && !wrapped) continue;          // plain streaming link
-            word |= 1u << i;
-            if (!solid) complex_link = true;             // streaming across a periodic face
-            continue;
+            if (!fluid_at(p)) kind = kBounce;
+            else if (wrapped) {
+              kind = kBounce;  // placeholder: streaming across a periodic face
+              complex_cell = true;
+            }
+          } else {
+            bool bb = false, vl = false, all_fs = true, out = false;
+            for (int k = 0; k < nf; ++k) {
+              const int kd = D.bc[faces[k]];
+              if (kd == SC_BC_BOUNCE_BACK) bb = true;
+              if (kd == SC_BC_VELOCITY) vl = true;
+              if (kd == SC_BC_OUTFLOW) out = true;
+              if (kd != SC_BC_FREE_SLIP) all_fs = false;
+            }
+            if (bb) {
+              kind = kBounce;
+            } else if (vl) {
+              kind = kMoving;
+              vel = true;
+            } else if (nf == 2 && all_fs) {
+              kind = kBounce;
+            } else if (nf == 1 && !out && faces[0] / 2 == 2 && !wrapped) {
+              // free slip at a z face: in-plane source x - (c_x, c_y, 0)
+              int s[3] = {xc[0] - ci[0], xc[1] - ci[1], xc[2]};
+              kind = fluid_at(s) ? kSpecZ : kBounce;
+            } else {
+              kind = kBounce;  // placeholder: outflow or free slip on an x/y face
+              complex_cell = true;
+            }
           }
-          word |= 1u << i;
-          bool bb = false, other = false, all_fs = true;
-          for (int k = 0; k < nf; ++k) {
-            const int kind = D.bc[faces[k]];
-            if (kind == SC_BC_BOUNCE_BACK) bb = true;
-            else other = true;
-            if (kind != SC_BC_FREE_SLIP) all_fs = false;
-          }
-          const bool plain_bb = bb || (nf == 2 && all_fs);
-          (void)other;
-          if (!plain_bb) complex_link = true;
+          word |= (LinkWord)kind << (2 * i);
         }
-        if (complex_link) word |= kLinkComplex;
+        if (complex_cell) word |= kLinkComplex;
+        if (vel) word |= kLinkVel;
         if (x == D.nx - 1 && D.bc[1] == SC_BC_OUTFLOW) word |= kLinkOutlet;
         link[c] = word;
       }
 }
 
 // Fluid cells that need the general boundary path of the odd AA level: a
-// link that is not plain streaming or bounce-back, or a cell on the outlet.
-void hn_boundary_cells(const std::vector<uint32_t>& link, std::vector<int32_t>& cells) {
+// link of a kind the fast path does not cover, or a cell on the outlet.
+void hn_boundary_cells(const std::vector<LinkWord>& link, std::vector<int32_t>& cells) {
   cells.clear();
   for (size_t c = 0; c < link.size(); ++c)
     if (!(link[c] & kLinkSolid) && (link[c] & (kLinkOutlet | kLinkComplex))) cells.push_back((int32_t)c);

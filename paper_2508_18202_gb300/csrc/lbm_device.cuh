@@ -370,12 +370,12 @@ __device__ __forceinline__ long long link_offset(const DevDomain& D, int i) {
 
 // f_i of the odd time level at a cell, any link kind (run-time loop, compact).
 template <class S, bool CG>
-__device__ void load_odd_general(const DevDomain& D, const Node<S>& N, uint32_t lw, int x, int y,
+__device__ void load_odd_general(const DevDomain& D, const Node<S>& N, LinkWord lw, int x, int y,
                                  int z, long long idx, typename Store<S>::C g[kQ],
                                  typename Store<S>::C r) {
 #pragma unroll 1
   for (int i = 0; i < kQ; ++i) {
-    if (!((lw >> i) & 1u))
+    if (link_kind(lw, i) == kStream)
       g[i] = LD<S, CG>(N.g + (long long)c_lat.opp[i] * D.pitch + idx - link_offset(D, i));
     else
       g[i] = pull_special<S, CG>(D, N, i, x, y, z, idx, r);
@@ -385,12 +385,12 @@ __device__ void load_odd_general(const DevDomain& D, const Node<S>& N, uint32_t 
 // Push of the odd level (or of the FP64 two-array path) for a cell with
 // boundary links, any link kind.
 template <class S>
-__device__ void push_general(const DevDomain& D, const Node<S>& N, S* dst, uint32_t lw, int x, int y,
+__device__ void push_general(const DevDomain& D, const Node<S>& N, S* dst, LinkWord lw, int x, int y,
                              int z, long long idx, const typename Store<S>::C g[kQ],
                              typename Store<S>::C r1) {
 #pragma unroll 1
   for (int j = 0; j < kQ; ++j) {
-    if (!((lw >> c_lat.opp[j]) & 1u))
+    if (link_kind(lw, c_lat.opp[j]) == kStream)
       Store<S>::st(dst + (long long)j * D.pitch + idx + link_offset(D, j), g[j]);
     else
       push_special<S>(D, N, dst, j, g[j], x, y, z, idx, r1);
@@ -401,6 +401,78 @@ __device__ void push_general(const DevDomain& D, const Node<S>& N, S* dst, uint3
     push_outlet<S>(D, dst, 10, g[10], x, y, z, idx);
     push_outlet<S>(D, dst, 12, g[12], x, y, z, idx);
     push_outlet<S>(D, dst, 14, g[14], x, y, z, idx);
+  }
+}
+
+// ------------------------------------------------------------ fast link rules
+// Links of kind kStream, kBounce, kMoving and kSpecZ resolve to an address
+// (and, for kMoving, an added moving-wall term), so cells whose links are all
+// of these kinds update without branches.  Offsets are 32-bit element
+// offsets from the cell's own slot 0 (a node holds fewer than 2^31
+// populations).
+
+// 6 w_i (c_i . u) r, direction i known at compile time.
+template <class T>
+__device__ __forceinline__ T wall_term(int i, T ux, T uy, T uz, T r) {
+  return T(6) * W<T>(i) * (T(CX(i)) * ux + T(CY(i)) * uy + T(CZ(i)) * uz) * r;
+}
+
+// Pull of the odd AA level (swapped layout in place).
+template <class S, bool CG>
+__device__ __forceinline__ void fast_pull(const S* base, LinkWord lw, int pc, int sy, int sz,
+                                          typename Store<S>::C ux, typename Store<S>::C uy,
+                                          typename Store<S>::C uz, typename Store<S>::C r,
+                                          typename Store<S>::C g[kQ]) {
+  using T = typename Store<S>::C;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int kind = link_kind(lw, i);
+    const int stream = OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz);
+    const int spec = OPP(REFL(i, 2)) * pc - (CX(i) + CY(i) * sy);
+    const int off = kind == kStream ? stream : (kind == kSpecZ ? spec : i * pc);
+    T v = LD<S, CG>(base + off);
+    if (kind == kMoving) v += wall_term<T>(i, ux, uy, uz, r);
+    g[i] = v;
+  }
+}
+
+// Delivery of the post-collision populations (odd AA level in place, or the
+// two-array push form with base in the destination array).
+template <class S>
+__device__ __forceinline__ void fast_push(S* base, LinkWord lw, int pc, int sy, int sz,
+                                          typename Store<S>::C ux, typename Store<S>::C uy,
+                                          typename Store<S>::C uz, typename Store<S>::C r1,
+                                          const typename Store<S>::C g[kQ]) {
+  using T = typename Store<S>::C;
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    const int kind = link_kind(lw, OPP(j));
+    const int stream = j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz);
+    const int spec = REFL(j, 2) * pc + (CX(j) + CY(j) * sy);
+    const int off = kind == kStream ? stream : (kind == kSpecZ ? spec : OPP(j) * pc);
+    T v = g[j];
+    if (kind == kMoving) v += wall_term<T>(OPP(j), ux, uy, uz, r1);
+    Store<S>::st(base + off, v);
+  }
+}
+
+// Inflow velocity of layer z for the moving-wall term (zero when the cell has
+// no inflow link, so the table is not read).
+template <class S>
+__device__ __forceinline__ void wall_velocity(const Node<S>& N, LinkWord lw, int z, typename Store<S>::C& ux,
+                                              typename Store<S>::C& uy, typename Store<S>::C& uz) {
+  using T = typename Store<S>::C;
+  ux = uy = uz = T(0);
+  if (!(lw & kLinkVel)) return;
+  if constexpr (sizeof(T) == 8) {
+    ux = T(N.uind[3 * z]);
+    uy = T(N.uind[3 * z + 1]);
+    uz = T(N.uind[3 * z + 2]);
+  } else {
+    const float4 u = N.uinf[z];
+    ux = T(u.x);
+    uy = T(u.y);
+    uz = T(u.z);
   }
 }
 

@@ -64,7 +64,7 @@ namespace {
 // their five populations with c_x = -1 into the outflow plane.
 template <class S, bool CG>
 __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& D,
-                                          const Node<S>& N, uint32_t lw, int y, int z,
+                                          const Node<S>& N, LinkWord lw, int y, int z,
                                           long long idx) {
   using T = typename Store<S>::C;
   const int pc = (int)D.pitch;
@@ -78,38 +78,30 @@ __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& 
   if (lw & kLinkOutlet) save_outlet<S>(D, N, y, z, g);
 }
 
-// Odd time level, cell whose boundary links (if any) are all plain
-// bounce-back: pull each f_i from slot opp(i) of the upstream neighbour, or
-// from the cell's own slot i where the link bounces back; push each f*_j to
-// slot j of the downstream neighbour, or to the own slot opp(j).  The choice
-// is an address select, so a warp stays converged.
+// Odd time level, cell whose links are all of the fast kinds (stream,
+// bounce-back, moving wall, specular at a z face): each f_i is pulled from
+// the address its kind selects and each f*_j delivered likewise, so a warp
+// stays converged.
 template <class S, bool CG>
 __device__ __forceinline__ void cell_odd_bulk(const StepParams& P, const DevDomain& D,
-                                              const Node<S>& N, uint32_t lw, long long idx) {
+                                              const Node<S>& N, LinkWord lw, long long idx, int z,
+                                              float r, float r1) {
   using T = typename Store<S>::C;
-  // 32-bit element offsets from the cell's own slot 0 (one node holds fewer
-  // than 2^31 populations, checked at init)
   const int pc = (int)D.pitch;
   const int sy = D.nx, sz = D.nx * D.ny;
   S* base = N.g + idx;
+  T ux, uy, uz;
+  wall_velocity<S>(N, lw, z, ux, uy, uz);
   T g[kQ];
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const int stream = OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz);
-    g[i] = LD<S, CG>(base + ((lw >> i) & 1u ? i * pc : stream));
-  }
+  fast_pull<S, CG>(base, lw, pc, sy, sz, ux, uy, uz, T(r), g);
   collide_p<T, true>(P, g);
-#pragma unroll
-  for (int j = 0; j < kQ; ++j) {
-    const int stream = j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz);
-    Store<S>::st(base + ((lw >> OPP(j)) & 1u ? OPP(j) * pc : stream), g[j]);
-  }
+  fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, T(r1), g);
 }
 
 // Odd time level, listed boundary cell: the general per-link rules.
 template <class S, bool CG>
 __device__ void cell_odd_general(const StepParams& P, const DevDomain& D, const Node<S>& N,
-                                 uint32_t lw, int x, int y, int z, long long idx,
+                                 LinkWord lw, int x, int y, int z, long long idx,
                                  typename Store<S>::C r, typename Store<S>::C r1) {
   using T = typename Store<S>::C;
   T g[kQ];
@@ -183,23 +175,23 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
   const int plane = D.nx * D.ny;
   int idx = R.x + D.nx * (R.y + D.ny * R.z0);
   for (int z = R.z0; z < R.z1; ++z, idx += plane) {
-    const uint32_t lw = __ldg(D.link + idx);
+    const LinkWord lw = __ldg(D.link + idx);
     if (lw & kLinkSolid) continue;
     cell_even<S, CG>(P, D, N, lw, R.y, z, idx);
   }
 }
 
 template <class S, bool CG>
-__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R) {
+__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R, float r, float r1) {
   if (!R.valid) return;
   const DevDomain& D = P.dom[R.d];
   const Node<S> N = node_view<S>(D, R.node);
   const int plane = D.nx * D.ny;
   int idx = R.x + D.nx * (R.y + D.ny * R.z0);
   for (int z = R.z0; z < R.z1; ++z, idx += plane) {
-    const uint32_t lw = __ldg(D.link + idx);
+    const LinkWord lw = __ldg(D.link + idx);
     if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
-    cell_odd_bulk<S, CG>(P, D, N, lw, idx);
+    cell_odd_bulk<S, CG>(P, D, N, lw, idx, z, r, r1);
   }
 }
 
@@ -219,7 +211,7 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   const int x = (int)(idx % D.nx);
   const int y = (int)((idx / D.nx) % D.ny);
   const int z = (int)(idx / ((long long)D.nx * D.ny));
-  const uint32_t lw = __ldg(D.link + idx);
+  const LinkWord lw = __ldg(D.link + idx);
   cell_odd_general<S, CG>(P, D, node_view<S>(D, node), lw, x, y, z, idx, T(r), T(r1));
 }
 
@@ -241,7 +233,7 @@ __global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constan
 // links carry no boundary term.
 template <class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
-  odd_bulk_tile<S, false>(P, block_tile(P, blockIdx.x));
+  odd_bulk_tile<S, false>(P, block_tile(P, blockIdx.x), P.r_pull, P.r_push);
 }
 
 // Odd time level, listed boundary cells (launched after the bulk kernel of the
@@ -425,7 +417,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) aa_even_tma_kernel(const __gri
     T g[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(sb + i * kRun + tid);
-    const uint32_t lw = c < D.ncell ? __ldg(D.link + c) : kLinkSolid;
+    const LinkWord lw = c < D.ncell ? __ldg(D.link + c) : kLinkSolid;
     if (!(lw & kLinkSolid)) {
       collide_p<T, true>(P, g);
       if (lw & kLinkOutlet) {
@@ -503,7 +495,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) aa_odd_tma_kernel(const __grid
     const DevDomain& D = P.dom[R.d];
     const S* sb = buf + s * kQ * RW;
     const long long c = R.c0 + tid;
-    const uint32_t lw = c < D.ncell ? __ldg(D.link + c) : kLinkSlow;
+    const LinkWord lw = c < D.ncell ? __ldg(D.link + c) : kLinkSlow;
     T g[kQ];
     const bool bulk = !(lw & kLinkSlow);
     if (bulk) {
@@ -513,17 +505,25 @@ __global__ void __launch_bounds__(kTmaThreads, 2) aa_odd_tma_kernel(const __grid
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);  // stage s is no longer read
     if (bulk) {
-      S* base = reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + c;
+      const Node<S> N = node_view<S>(D, R.node);
+      S* base = N.g + c;
       const int pc = (int)D.pitch, sy = D.nx, sz = D.nx * D.ny;
+      const int z = (int)(c / ((long long)sz));
+      T ux, uy, uz;
+      wall_velocity<S>(N, lw, z, ux, uy, uz);
+      // links that do not stream take their value from the own or the
+      // in-plane slot in global memory
 #pragma unroll
-      for (int i = 0; i < kQ; ++i)
-        if ((lw >> i) & 1u) g[i] = Store<S>::ld(base + i * pc);
-      collide_p<T, true>(P, g);
-#pragma unroll
-      for (int j = 0; j < kQ; ++j) {
-        const int stream = j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz);
-        Store<S>::st(base + ((lw >> OPP(j)) & 1u ? OPP(j) * pc : stream), g[j]);
+      for (int i = 0; i < kQ; ++i) {
+        const int kind = link_kind(lw, i);
+        if (kind == kStream) continue;
+        const int off = kind == kSpecZ ? OPP(REFL(i, 2)) * pc - (CX(i) + CY(i) * sy) : i * pc;
+        T v = Store<S>::ld(base + off);
+        if (kind == kMoving) v += wall_term<T>(i, ux, uy, uz, T(P.r_pull));
+        g[i] = v;
       }
+      collide_p<T, true>(P, g);
+      fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, T(P.r_push), g);
     }
   }
 }
@@ -585,12 +585,12 @@ __global__ void __launch_bounds__(256) aa_persistent_kernel(const __grid_constan
         __syncthreads();  // the shared tile head is rewritten next iteration
       }
     } else {
+      const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
       for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) {
-        odd_bulk_tile<S, true>(P, block_tile(P, (unsigned)t));
+        odd_bulk_tile<S, true>(P, block_tile(P, (unsigned)t), r, r1);
         __syncthreads();
       }
       // bulk and boundary cells touch disjoint slots: no barrier between them
-      const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
       for (long long b = blockIdx.x; b < bblocks; b += gridDim.x)
         odd_boundary_item<S, true>(P, b * threads + threadIdx.y * P.bx + threadIdx.x, r, r1);
     }
@@ -621,19 +621,24 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
     const int y = ty * P.by + threadIdx.y;
     if (x >= D.nx || y >= D.ny) return;
     const int z0 = tz * P.bz, z1 = min(z0 + P.bz, D.nz);
+    Node<double> N;
+    N.g = dst;
+    N.bout = nullptr;
+    N.uinf = nullptr;
+    N.uind = D.uin_d + (long long)node * D.nz * 3;
+    const unsigned long long m1 = n + 1;
+    const double r1 = P.ramp_d[m1 < (unsigned long long)P.ramp_steps ? m1 : P.ramp_steps];
     for (int z = z0; z < z1; ++z) {
       const long long idx = cidx(D, x, y, z);
-      const uint32_t lw = __ldg(D.link + idx);
+      const LinkWord lw = __ldg(D.link + idx);
       if (lw & kLinkSlow) continue;
       double g[kQ];
 #pragma unroll
       for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
       collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
-#pragma unroll
-      for (int j = 0; j < kQ; ++j) {
-        const long long stream = (long long)j * pc + idx + (CX(j) * sx + CY(j) * sy + CZ(j) * sz);
-        dst[((lw >> OPP(j)) & 1u) ? (long long)OPP(j) * pc + idx : stream] = g[j];
-      }
+      double ux, uy, uz;
+      wall_velocity<double>(N, lw, z, ux, uy, uz);
+      fast_push<double>(dst + idx, lw, (int)pc, (int)sy, (int)sz, ux, uy, uz, r1, g);
     }
     return;
   }
@@ -643,7 +648,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   const int x = (int)(idx % D.nx);
   const int y = (int)((idx / D.nx) % D.ny);
   const int z = (int)(idx / ((long long)D.nx * D.ny));
-  const uint32_t lw = __ldg(D.link + idx);
+  const LinkWord lw = __ldg(D.link + idx);
   Node<double> N;
   N.g = dst;
   N.bout = nullptr;
@@ -680,7 +685,7 @@ __global__ void init_kernel(S* g, long long pitch, long long total) {
 template <class S, bool SHIFT>
 __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain& D, int node,
                                             unsigned long long n, int x, int y, int z,
-                                            long long idx, uint32_t lw,
+                                            long long idx, LinkWord lw,
                                             typename Store<S>::C g[kQ]) {
   using T = typename Store<S>::C;
   if constexpr (!SHIFT) {
@@ -731,7 +736,7 @@ __global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs 
     const int x = (int)(c % D.nx);
     const int y = (int)((c / D.nx) % D.ny);
     const int z = (int)(c / ((long long)D.nx * D.ny));
-    const uint32_t lw = __ldg(D.link + c);
+    const LinkWord lw = __ldg(D.link + c);
     double s1 = 0.0, s2 = 0.0;
     double coef[kMaxGpcP];
 #pragma unroll
@@ -778,7 +783,7 @@ __global__ void profiles_kernel(const __grid_constant__ StepParams P, MomentArgs
   const int z = warp % D.nz;
   const int x = A.probes[2 * p], y = A.probes[2 * p + 1];
   const long long c = cidx(D, x, y, z);
-  const uint32_t lw = __ldg(D.link + c);
+  const LinkWord lw = __ldg(D.link + c);
   const unsigned long long n = P.n_host;
   double s1 = 0.0, s2 = 0.0;
   for (int j = lane; j < A.nq; j += 32) {
@@ -824,7 +829,7 @@ __global__ void export_kernel(const __grid_constant__ StepParams P, int domain, 
   const int x = (int)(c % D.nx);
   const int y = (int)((c / D.nx) % D.ny);
   const int z = (int)(c / ((long long)D.nx * D.ny));
-  const uint32_t lw = __ldg(D.link + c);
+  const LinkWord lw = __ldg(D.link + c);
   if (lw & kLinkSolid) {
     if (f)
       for (int i = 0; i < kQ; ++i) f[(long long)i * D.ncell + c] = 0.0;

@@ -18,15 +18,29 @@ constexpr int kMaxDomains = SC_MAX_DOMAINS;
 constexpr int kMaxGpcP = 20;     // largest gPC basis the reduction kernel keeps in registers
 constexpr int kRun = 256;        // cells per run of the TMA-staged kernels; the row pitch is a multiple
 
-// Link word per cell: bit i (0..18) set when the pull source x - c_i of
-// direction i is not an in-domain fluid cell reached without periodic wrap
-// (solid, across a face, or wrapped).  Such links take the boundary path.
-constexpr uint32_t kLinkSolid = 1u << 19;    // the cell itself is solid
-constexpr uint32_t kLinkOutlet = 1u << 20;   // fluid cell on an OUTFLOW +x face
-constexpr uint32_t kLinkComplex = 1u << 21;  // some boundary link is not plain bounce-back
-constexpr uint32_t kLinkMask = (1u << 19) - 1u;
-// Cells without these bits take the fast path (boundary links = bounce-back).
-constexpr uint32_t kLinkSlow = kLinkSolid | kLinkOutlet | kLinkComplex;
+// Link word per cell (64 bits).  Bits 2i, 2i+1 give the kind of link i, the
+// rule that supplies f_i from the source x - c_i:
+//   kStream  in-domain fluid source, no periodic wrap
+//   kBounce  bounce-back (solid source, wall face, two walls, two free-slip faces)
+//   kMoving  bounce-back plus the moving-wall term of an inflow face
+//   kSpecZ   specular reflection at a free-slip z face from a fluid in-plane source
+// Links of any other kind (outflow, free slip on an x/y face, periodic wraps
+// of fluid sources, outflow + free-slip edges) carry a nonzero placeholder
+// kind and mark the cell kLinkComplex: such cells take the general path.
+using LinkWord = unsigned long long;
+constexpr int kStream = 0, kBounce = 1, kMoving = 2, kSpecZ = 3;
+constexpr LinkWord kLinkSolid = 1ull << 40;    // the cell itself is solid
+constexpr LinkWord kLinkOutlet = 1ull << 41;   // fluid cell on an OUTFLOW +x face
+constexpr LinkWord kLinkComplex = 1ull << 42;  // some link needs the general rules
+constexpr LinkWord kLinkVel = 1ull << 43;      // some link carries the moving-wall term
+constexpr LinkWord kLinkKinds = (1ull << 38) - 1ull;
+// Cells without these bits take the fast path.
+constexpr LinkWord kLinkSlow = kLinkSolid | kLinkOutlet | kLinkComplex;
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int link_kind(LinkWord w, int i) { return (int)((w >> (2 * i)) & 3ull); }
 
 // Device error word bits.
 constexpr unsigned kErrDiverged = 1u;
@@ -38,7 +52,7 @@ struct DevDomain {
   long long ncell;
   int bc[6];
   const uint8_t* flags;     // [ncell]
-  const uint32_t* link;     // [ncell]
+  const LinkWord* link;     // [ncell]
   const float4* uin_f;      // [nodes][nz] (ux, uy, uz, 0)
   const double* uin_d;      // [nodes][nz][3]
   long long pitch;          // population row stride (elements), multiple of kRun
@@ -90,8 +104,8 @@ int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi
 int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags);
 int hn_probe_columns(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xy);
 int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xyz);
-void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<uint32_t>& link);
-void hn_boundary_cells(const std::vector<uint32_t>& link, std::vector<int32_t>& cells);
+void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<LinkWord>& link);
+void hn_boundary_cells(const std::vector<LinkWord>& link, std::vector<int32_t>& cells);
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin /*[nz][3]*/);
 int hn_gpc_size(int d, int degree);
