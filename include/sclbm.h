@@ -24,7 +24,8 @@
  *   - "device" pointers are CUDA device memory owned by the caller; "host"
  *     pointers are ordinary (optionally pinned) host memory owned by the
  *     caller.  The library never frees caller memory.  The only memory the
- *     library owns is the small host-side state behind an sc_lbm_t.
+ *     library owns is the small host-side state behind an sc_lbm_t and the
+ *     fixed scratch array of sc_lbm_quad_moments_noalloc (below).
  *   - All device work of a handle is issued on the CUDA stream given to
  *     sc_lbm_init and is asynchronous unless a function says it synchronises.
  *     Device-side failures (non-finite populations, an expired wait) are
@@ -49,6 +50,7 @@ extern "C" {
 #define SC_ERR_TIMEOUT (-5)      /* a bounded device-side wait expired         */
 #define SC_ERR_UNSUPPORTED (-6)  /* valid request this build does not support  */
 #define SC_ERR_STATE (-7)        /* call not valid in the handle's state       */
+#define SC_ERR_SCRATCH (-8)      /* request exceeds the fixed no-alloc scratch */
 
 /* ------------------------------------------------------------ enumerations */
 /* boundary kind per face (Sec. 2.2 boundary list; OUTFLOW added for channels) */
@@ -289,6 +291,46 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
 
 const char* sc_lbm_last_error(sc_lbm_t h);
 int sc_lbm_destroy(sc_lbm_t h);
+
+/* ------------------------------------------------------------ no-alloc form
+ * The paper has no counterpart to this call: it is a library facility.
+ *
+ * The per-cell quadrature mean and standard deviation of sc_lbm_moments
+ * (same FP64 arithmetic, nodes in order) for a per-node field the caller
+ * already holds, with no handle, no workspace and no device allocation.
+ * For callers that cannot allocate device memory where they need the
+ * statistics: a process whose free HBM is already reserved by another
+ * allocator (a caching allocator or a serving pool that takes the device's
+ * memory up front, where cudaMalloc fails or forces a cache flush), or code
+ * on a latency-critical stream, where cudaMalloc / cudaFree would
+ * synchronise the device.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * Its scratch (the weight table on the device and a counter of non-finite
+ * inputs) is a fixed file-scope device array of about 8 KB, held by every
+ * GPU that loads the library until the process exits.  The first call on
+ * each device (with that device current) looks up the array's address; make
+ * that first call before any stream capture begins.  Every call shares the
+ * array and it keeps the last call's contents (the counter is cleared at the
+ * start of each call): calls whose device work overlaps (unordered streams,
+ * several host threads) race on it.
+ *
+ * d_field: device double [n_nodes][n_cells], Q_j(c) of node j at cell c;
+ * weights: host double [n_nodes], the quadrature weights a_j (their sum must
+ * be positive); d_mean, d_stdev: device double [n_cells] outputs,
+ *   mean = sum_j a_j Q_j / sum_j a_j,
+ *   std  = sqrt(max(sum_j a_j Q_j^2 / sum_j a_j - mean^2, 0));
+ * d_nonfinite: device unsigned long long or NULL, receives the count of
+ * non-finite Q_j(c); stream: CUDA stream (NULL = legacy default stream); the
+ * call is asynchronous on it.  err: host buffer of err_len bytes or NULL,
+ * receives a message on failure.
+ * Returns SC_ERR_SCRATCH when n_nodes > SC_NOALLOC_MAX_NODES, SC_ERR_ARG for
+ * other invalid arguments, SC_ERR_CUDA when a CUDA call fails.             */
+#define SC_NOALLOC_MAX_NODES 1024
+int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, long long n_cells,
+                                const double* weights, double* d_mean, double* d_stdev,
+                                unsigned long long* d_nonfinite, void* stream, char* err,
+                                size_t err_len);
 
 #ifdef __cplusplus
 }

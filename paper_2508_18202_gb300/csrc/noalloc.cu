@@ -1,0 +1,158 @@
+// noalloc.cu -- sc_lbm_quad_moments_noalloc: the quadrature mean / standard
+// deviation reduction of sc_lbm_moments for a per-node field the caller
+// already holds, run without any device allocation and without a handle or
+// workspace.
+//
+// Who needs it: callers that cannot allocate device memory at the point where
+// they want the statistics -- a process whose free HBM is already reserved by
+// another allocator (a PyTorch caching allocator or a serving pool that takes
+// the device's memory up front, where cudaMalloc fails or forces a cache
+// flush), and code on a latency-critical stream, where cudaMalloc / cudaFree
+// would synchronise the whole device.  Such a caller cannot size and hand
+// over a workspace either, so the two pieces of scratch the reduction needs
+// (the quadrature weight table on the device and a counter of non-finite
+// inputs) live in a fixed file-scope device array instead.
+//
+// The scratch array is a static __device__ symbol: every GPU on which the
+// library's module is loaded holds it (kNoallocScratchBytes, about 8 KB)
+// until the process exits.  Its device address is looked up once per device,
+// by the first call made with that device current; that first call should be
+// made before any stream capture begins.  All calls share the array and it
+// keeps the last call's contents: the counter is cleared at the start of each
+// call, the weight table is overwritten.  Calls whose device work overlaps
+// (different streams without ordering, or several host threads) race on it.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "sclbm.h"
+
+namespace {
+
+constexpr int kNoallocMaxNodes = SC_NOALLOC_MAX_NODES;
+constexpr size_t kWeightBytes = sizeof(double) * kNoallocMaxNodes;
+constexpr size_t kCounterOffset = kWeightBytes;               // 256-byte aligned
+constexpr size_t kNoallocScratchBytes = kWeightBytes + 256;  // weights + counter
+constexpr int kMaxDevices = 64;
+
+// [0, kWeightBytes): the weights a_j (FP64); at kCounterOffset: the count of
+// non-finite field values (unsigned long long, cleared per call).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+void put_err(char* err, size_t err_len, const char* fmt, long long a, long long b) {
+  if (err && err_len) snprintf(err, err_len, fmt, a, b);
+}
+
+// Device address of the scratch array on the current device (looked up once
+// per device, with that device current).
+int scratch_for_current_device(void** out, char* err, size_t err_len) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    put_err(err, err_len, "cudaGetDevice failed (%lld)%lld", (long long)e, 0);
+    return SC_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    put_err(err, err_len, "device ordinal %lld beyond the %lld devices the scratch table covers", dev,
+            kMaxDevices);
+    return SC_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      put_err(err, err_len, "cudaGetSymbolAddress of the no-alloc scratch failed (%lld) on device %lld",
+              (long long)e, dev);
+      return SC_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return SC_OK;
+}
+
+// Per cell c: s1 = sum_j a_j Q_j(c), s2 = sum_j a_j Q_j(c)^2 (FP64, nodes in
+// order), mean = s1 / sum_j a_j, std = sqrt(max(s2 / sum_j a_j - mean^2, 0))
+// -- the same arithmetic as the handle path's moment reduction.  Non-finite
+// Q_j(c) are counted in the scratch counter.
+__global__ void __launch_bounds__(256) quad_moments_noalloc_kernel(
+    const double* __restrict__ field, long long n_cells, int n_nodes, const double* __restrict__ w,
+    double wsum, double* __restrict__ mean, double* __restrict__ stdev, unsigned long long* nonfinite) {
+  unsigned bad = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int j = 0; j < n_nodes; ++j) {
+      const double q = field[(long long)j * n_cells + c];
+      if (!isfinite(q)) ++bad;
+      const double aq = w[j] * q;
+      s1 += aq;
+      s2 += aq * q;
+    }
+    const double m = s1 / wsum;
+    double var = s2 / wsum - m * m;
+    if (var < 0.0) var = 0.0;
+    mean[c] = m;
+    stdev[c] = sqrt(var);
+  }
+  const unsigned total = __reduce_add_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && total) atomicAdd(nonfinite, (unsigned long long)total);
+}
+
+}  // namespace
+
+extern "C" int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, long long n_cells,
+                                           const double* weights, double* d_mean, double* d_stdev,
+                                           unsigned long long* d_nonfinite, void* stream, char* err,
+                                           size_t err_len) {
+  if (err && err_len) err[0] = '\0';
+  if (n_nodes < 1 || n_cells < 0) {
+    put_err(err, err_len, "n_nodes = %lld and n_cells = %lld must be >= 1 and >= 0", n_nodes, n_cells);
+    return SC_ERR_ARG;
+  }
+  if (n_nodes > kNoallocMaxNodes) {
+    put_err(err, err_len, "n_nodes = %lld exceeds the no-alloc scratch maximum of %lld nodes", n_nodes,
+            kNoallocMaxNodes);
+    return SC_ERR_SCRATCH;
+  }
+  if (!weights || (n_cells > 0 && (!d_field || !d_mean || !d_stdev))) {
+    put_err(err, err_len, "null weights, field or output pointer%lld%lld", 0, 0);
+    return SC_ERR_ARG;
+  }
+  double wsum = 0.0;
+  for (int j = 0; j < n_nodes; ++j) wsum += weights[j];
+  if (!(wsum > 0.0) || !isfinite(wsum)) {
+    put_err(err, err_len, "the weights must have a positive finite sum%lld%lld", 0, 0);
+    return SC_ERR_ARG;
+  }
+  void* base = nullptr;
+  int rc = scratch_for_current_device(&base, err, err_len);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d_w = (double*)base;
+  unsigned long long* d_count = (unsigned long long*)((unsigned char*)base + kCounterOffset);
+  cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_w, weights, sizeof(double) * (size_t)n_nodes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_cells > 0) {
+    long long blocks = (n_cells + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    quad_moments_noalloc_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_field, n_cells, n_nodes, d_w, wsum,
+                                                                 d_mean, d_stdev, d_count);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && d_nonfinite)
+    e = cudaMemcpyAsync(d_nonfinite, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    put_err(err, err_len, "CUDA error %lld in the no-alloc moment reduction%lld", (long long)e, 0);
+    return SC_ERR_CUDA;
+  }
+  return SC_OK;
+}

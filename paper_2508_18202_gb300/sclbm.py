@@ -17,6 +17,8 @@ from . import build as _build
 SC_OK = 0
 SC_ERR_ARG, SC_ERR_WORKSPACE, SC_ERR_CUDA = -1, -2, -3
 SC_ERR_DIVERGED, SC_ERR_TIMEOUT, SC_ERR_UNSUPPORTED, SC_ERR_STATE = -4, -5, -6, -7
+SC_ERR_SCRATCH = -8
+SC_NOALLOC_MAX_NODES = 1024
 SC_BC_VELOCITY, SC_BC_OUTFLOW, SC_BC_BOUNCE_BACK, SC_BC_FREE_SLIP, SC_BC_PERIODIC = 0, 1, 2, 3, 4
 SC_IN_SPEED_REL, SC_IN_ALPHA, SC_IN_ANGLE_DEG = 0, 1, 2
 SC_Q_GL, SC_Q_CC_SMOLYAK = 0, 1
@@ -25,7 +27,8 @@ SC_EXEC_LAUNCH, SC_EXEC_GRAPH, SC_EXEC_PERSISTENT = 0, 1, 2
 
 _NAMES = {SC_ERR_ARG: "SC_ERR_ARG", SC_ERR_WORKSPACE: "SC_ERR_WORKSPACE", SC_ERR_CUDA: "SC_ERR_CUDA",
           SC_ERR_DIVERGED: "SC_ERR_DIVERGED", SC_ERR_TIMEOUT: "SC_ERR_TIMEOUT",
-          SC_ERR_UNSUPPORTED: "SC_ERR_UNSUPPORTED", SC_ERR_STATE: "SC_ERR_STATE"}
+          SC_ERR_UNSUPPORTED: "SC_ERR_UNSUPPORTED", SC_ERR_STATE: "SC_ERR_STATE",
+          SC_ERR_SCRATCH: "SC_ERR_SCRATCH"}
 
 
 class ScError(RuntimeError):
@@ -90,6 +93,8 @@ SIGNATURES = {
                                  C.POINTER(C.c_double), _P, _P]),
     "sc_lbm_last_error": (C.c_char_p, [_H]),
     "sc_lbm_destroy": (C.c_int, [_H]),
+    "sc_lbm_quad_moments_noalloc": (C.c_int, [_P, C.c_int, C.c_longlong, _P, _P, _P, _P, _P, C.c_char_p,
+                                              C.c_size_t]),
 }
 
 _lib = None
@@ -328,6 +333,22 @@ def sc_lbm_last_error(h):
 
 def sc_lbm_destroy(h):
     _call("sc_lbm_destroy", h)
+
+
+def sc_lbm_quad_moments_noalloc(field, weights, mean, std, nonfinite=None, stream=0):
+    """Quadrature mean / std of a caller-held per-node field without device
+    allocation (no handle, no workspace; scratch is the library's fixed
+    device array).  field: device double [n_nodes][n_cells]; weights: host
+    doubles; mean, std: device double [n_cells]; nonfinite: device uint64[1]
+    or None; stream: raw CUDA stream handle (0 = legacy default stream)."""
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    n_nodes = int(w.shape[0])
+    n_cells = int(field.shape[-1]) if n_nodes else 0
+    err = C.create_string_buffer(256)
+    rc = lib().sc_lbm_quad_moments_noalloc(_ptr(field), n_nodes, n_cells, w.ctypes.data, _ptr(mean),
+                                          _ptr(std), _ptr(nonfinite), stream, err, len(err))
+    if rc != SC_OK:
+        raise ScError(rc, "sc_lbm_quad_moments_noalloc", err.value.decode())
 
 
 # ------------------------------------------------------------------ convenience
