@@ -375,8 +375,16 @@ class Ensemble:
         with self.torch.cuda.stream(self.stream):
             return self.torch.empty(*shape, dtype=dtype or self.torch.float64, device=self.device)
 
-    def _hand_over(self):
-        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+    def _hand_over(self, *tensors):
+        """Make the caller's current stream wait for the handle's stream and
+        mark the outputs as used there, so that the caching allocator does
+        not hand their memory to a later output of the handle's stream while
+        the caller's stream still reads them."""
+        cur = self.torch.cuda.current_stream(self.device)
+        cur.wait_stream(self.stream)
+        for t in tensors:
+            if t is not None:
+                t.record_stream(cur)
 
     def ncell(self, d):
         D = self.cfg.domains[d]
@@ -401,19 +409,19 @@ class Ensemble:
             P = comb(self.cfg.c.gpc_degree + self.cfg.c.n_inputs, self.cfg.c.n_inputs)
             coef = self._out(P, n)
         sc_lbm_moments(self.h, domain, mean, std, probes, prof, pn, coef)
-        self._hand_over()
+        self._hand_over(mean, std, prof, pn, coef)
         return dict(mean=mean, std=std, prof=prof, prof_nodes=pn, coef=coef)
 
     def velocity(self, domain, node):
         u = self._out(3, self.ncell(domain), dtype=self.torch.float32)
         sc_lbm_velocity(self.h, domain, node, u)
-        self._hand_over()
+        self._hand_over(u)
         return u
 
     def populations(self, domain, node):
         f = self._out(19, self.ncell(domain))
         sc_lbm_populations(self.h, domain, node, f)
-        self._hand_over()
+        self._hand_over(f)
         return f
 
     def sync(self):
