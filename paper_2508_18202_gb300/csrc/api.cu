@@ -347,7 +347,7 @@ int run_launches(sc_lbm_t h, long long start, int n) {
     P.r_push = ramp_f(h, lvl + 1);
     int rc = launch_aa_step(P, h->cfg.precision, h->stream, parity);
     if (rc) return cuda_fail(h, (cudaError_t)rc, "aa_step launch");
-    h->launches += parity ? 2 : 1;  // odd levels: bulk + boundary kernels
+    h->launches += parity && h->P.tma ? 2 : 1;  // TMA odd levels: bulk + boundary kernels
   }
   return SC_OK;
 }
@@ -394,7 +394,7 @@ int run_graph(sc_lbm_t h, int n) {
   const int reps = n / G;
   for (int r = 0; r < reps; ++r) {
     CK(cudaGraphLaunch(h->graph, h->stream));
-    h->launches += G + G / 2;  // G/2 odd levels of two kernels each
+    h->launches += G + (h->P.tma ? G / 2 : 0);  // TMA odd levels launch two kernels
   }
   return run_launches(h, t + (long long)reps * G, n - reps * G);
 }

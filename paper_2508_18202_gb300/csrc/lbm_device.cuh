@@ -169,11 +169,20 @@ __device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_o
   }
   const T omega = recip(tau);
   const T base = m0;  // shifted: w (rho - 1) part; plain: w rho part
+  // Opposite pairs (i, i + 1), i odd, share c_i . u up to the sign: the
+  // bracket of the equilibrium splits into an even part
+  // base + rho (4.5 cu^2 - 1.5 u^2) and an odd part 3 rho cu; the weight
+  // multiplies last (a rounded 3 w would bias the momentum of every
+  // collision).
+  const T r15 = T(1.5) * usq;
+  g[0] = g[0] - omega * (g[0] - W<T>(0) * (base - rho * r15));
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
+  for (int i = 1; i < kQ; i += 2) {
     const T cu = T(CX(i)) * ux + T(CY(i)) * uy + T(CZ(i)) * uz;
-    const T geq = W<T>(i) * (base + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
-    g[i] = g[i] - omega * (g[i] - geq);
+    const T even = base + rho * (T(4.5) * cu * cu - r15);
+    const T odd = T(3) * rho * cu;
+    g[i] = g[i] - omega * (g[i] - W<T>(i) * (even + odd));
+    g[i + 1] = g[i + 1] - omega * (g[i + 1] - W<T>(i) * (even - odd));
   }
 }
 

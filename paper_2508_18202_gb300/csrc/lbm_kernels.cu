@@ -181,6 +181,26 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
   }
 }
 
+// Odd time level, cell whose 19 links all stream (the interior).
+template <class S, bool CG>
+__device__ __forceinline__ void cell_odd_stream(const StepParams& P, const DevDomain& D, const Node<S>& N,
+                                                long long idx) {
+  using T = typename Store<S>::C;
+  const int pc = (int)D.pitch;
+  const int sy = D.nx, sz = D.nx * D.ny;
+  S* base = N.g + idx;
+  T g[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    g[i] = LD<S, CG>(base + (OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz)));
+  collide_p<T, true>(P, g);
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz)), g[j]);
+}
+
+// A warp whose cells are all interior (or skipped) takes the plain streaming
+// form; a warp with any wall, inflow or lid link takes the link-kind form for
+// all its cells, so neither diverges.
 template <class S, bool CG>
 __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R, float r, float r1) {
   if (!R.valid) return;
@@ -190,8 +210,10 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef
   int idx = R.x + D.nx * (R.y + D.ny * R.z0);
   for (int z = R.z0; z < R.z1; ++z, idx += plane) {
     const LinkWord lw = __ldg(D.link + idx);
+    const bool interior = __all_sync(__activemask(), lw == 0 || (lw & kLinkSlow));
     if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
-    cell_odd_bulk<S, CG>(P, D, N, lw, idx, z, r, r1);
+    if (interior) cell_odd_stream<S, CG>(P, D, N, idx);
+    else cell_odd_bulk<S, CG>(P, D, N, lw, idx, z, r, r1);
   }
 }
 
@@ -229,16 +251,31 @@ __global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constan
   even_tile<S, false>(P, block_tile(P, blockIdx.x));
 }
 
-// Odd time level, bulk cells of every tile.  Needs no time level: the bulk
-// links carry no boundary term.
-template <class S, int MINB>
-__global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
-  odd_bulk_tile<S, false>(P, block_tile(P, blockIdx.x), P.r_pull, P.r_push);
+// Blocks at the head of the odd launch that carry listed boundary items.
+__device__ __forceinline__ unsigned odd_lead_blocks(const StepParams& P) {
+  const long long threads = (long long)blockDim.x * blockDim.y;
+  return (unsigned)((P.total_bitems + threads - 1) / threads);
 }
 
-// Odd time level, listed boundary cells (launched after the bulk kernel of the
-// same level; the two touch disjoint slots).  The inflow ramp factors of the
-// odd level n (pulls, r(n)) and of level n + 1 (pushes) come with the launch.
+// Odd time level in one launch: the leading blocks take the listed boundary
+// cells (one thread per (node, cell)), the rest the tiles of bulk cells.  The
+// two sets touch disjoint slots, so the long-latency boundary work overlaps
+// with the bulk stream.  The inflow ramp factors of the odd level n (pulls,
+// r(n)) and of level n + 1 (pushes) come with the launch.
+template <class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
+  const unsigned lead = odd_lead_blocks(P);
+  if (blockIdx.x < lead) {
+    const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x +
+                           threadIdx.x;
+    odd_boundary_item<S, false>(P, item, P.r_pull, P.r_push);
+    return;
+  }
+  odd_bulk_tile<S, false>(P, block_tile(P, blockIdx.x - lead), P.r_pull, P.r_push);
+}
+
+// Odd time level, listed boundary cells alone (after the TMA odd kernel of the
+// same level; the two touch disjoint slots).
 template <class S>
 __global__ void __launch_bounds__(256) aa_odd_boundary_kernel(const __grid_constant__ StepParams P) {
   const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
@@ -302,7 +339,6 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigne
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -611,7 +647,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   double* B = reinterpret_cast<double*>(D.g2) + (long long)node * kQ * pc;
   const double* src = (n & 1ull) ? B : A;
   double* dst = (n & 1ull) ? A : B;
-  const long long sx = 1, sy = D.nx, sz = (long long)D.nx * D.ny;
+  const long long sy = D.nx, sz = (long long)D.nx * D.ny;
   const long long b = blockIdx.x;
   if (b < D.tiles_per_node) {
     const int tx = (int)(b % D.tiles_x);
@@ -950,11 +986,17 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
         else if (P.regs85) aa_even_kernel<S, 3><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
         else aa_even_kernel<S, 4><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
       } else {
-        if (P.tma) aa_odd_tma_kernel<S><<<tgrid, kTmaThreads, odd_tma_smem<S>(), s>>>(P);
-        else if (P.regs85) aa_odd_bulk_kernel<S, 3><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
-        else aa_odd_bulk_kernel<S, 4><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
-        const long long grid = (P.total_bitems + 255) / 256;
-        aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
+        const long long threads = (long long)P.bx * P.by;
+        const unsigned ogrid = (unsigned)(P.total_tiles + (P.total_bitems + threads - 1) / threads);
+        if (P.tma) {
+          aa_odd_tma_kernel<S><<<tgrid, kTmaThreads, odd_tma_smem<S>(), s>>>(P);
+          const long long grid = (P.total_bitems + 255) / 256;
+          aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
+        } else if (P.regs85) {
+          aa_odd_bulk_kernel<S, 3><<<ogrid, block, 0, s>>>(P);
+        } else {
+          aa_odd_bulk_kernel<S, 4><<<ogrid, block, 0, s>>>(P);
+        }
       }
       return (int)cudaGetLastError();
     }
