@@ -78,26 +78,6 @@ __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& 
   if (lw & kLinkOutlet) save_outlet<S>(D, N, y, z, g);
 }
 
-// Odd time level, cell whose links are all of the fast kinds (stream,
-// bounce-back, moving wall, specular at a z face): each f_i is pulled from
-// the address its kind selects and each f*_j delivered likewise, so a warp
-// stays converged.
-template <class S, bool CG>
-__device__ __forceinline__ void cell_odd_bulk(const StepParams& P, const DevDomain& D,
-                                              const Node<S>& N, LinkWord lw, long long idx, int z,
-                                              float r, float r1) {
-  using T = typename Store<S>::C;
-  const int pc = (int)D.pitch;
-  const int sy = D.nx, sz = D.nx * D.ny;
-  S* base = N.g + idx;
-  T ux, uy, uz;
-  wall_velocity<S>(N, lw, z, ux, uy, uz);
-  T g[kQ];
-  fast_pull<S, CG>(base, lw, pc, sy, sz, ux, uy, uz, T(r), g);
-  collide_p<T, true>(P, g);
-  fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, T(r1), g);
-}
-
 // Odd time level, listed boundary cell: the general per-link rules.
 template <class S, bool CG>
 __device__ void cell_odd_general(const StepParams& P, const DevDomain& D, const Node<S>& N,
@@ -167,13 +147,46 @@ __device__ __forceinline__ TileRef block_tile(const StepParams& P, unsigned t) {
   return R;
 }
 
+// Even level over the z-slab of a tile.  The link word of the next cell is
+// loaded one cell ahead so the population loads do not wait on it.
+// LISTED_APART: listed cells (outlet, general boundary) are left to the
+// leading blocks of the launch, so the bulk path carries no outlet save.
+// Even level, bulk cells of a z-run: n cells, plane apart, from base (slot 0
+// of the first cell) and its link words lp.  Only these scalars stay live in
+// the loop.
 template <class S, bool CG>
+__device__ __forceinline__ void even_run(const StepParams& P, S* base, const LinkWord* lp, int pc, int plane,
+                                         int n) {
+  using T = typename Store<S>::C;
+  LinkWord next = __ldg(lp);
+  for (int k = 0; k < n; ++k, base += plane, lp += plane) {
+    const LinkWord lw = next;
+    if (k + 1 < n) next = __ldg(lp + plane);
+    if (lw & kLinkSlow) continue;
+    T g[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(base + i * pc);
+    collide_p<T, true>(P, g);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) Store<S>::st(base + OPP(i) * pc, g[i]);
+  }
+}
+
+// LISTED_APART: listed cells (outlet, general boundary) are left to the
+// leading blocks of the launch, so the bulk path carries no outlet save.
+template <class S, bool CG, bool LISTED_APART>
 __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R) {
   if (!R.valid) return;
   const DevDomain& D = P.dom[R.d];
-  const Node<S> N = node_view<S>(D, R.node);
   const int plane = D.nx * D.ny;
-  int idx = R.x + D.nx * (R.y + D.ny * R.z0);
+  const int idx0 = R.x + D.nx * (R.y + D.ny * R.z0);
+  if (LISTED_APART) {
+    even_run<S, CG>(P, reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0, D.link + idx0,
+                    (int)D.pitch, plane, R.z1 - R.z0);
+    return;
+  }
+  const Node<S> N = node_view<S>(D, R.node);
+  int idx = idx0;
   for (int z = R.z0; z < R.z1; ++z, idx += plane) {
     const LinkWord lw = __ldg(D.link + idx);
     if (lw & kLinkSolid) continue;
@@ -181,40 +194,60 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
   }
 }
 
-// Odd time level, cell whose 19 links all stream (the interior).
-template <class S, bool CG>
-__device__ __forceinline__ void cell_odd_stream(const StepParams& P, const DevDomain& D, const Node<S>& N,
-                                                long long idx) {
-  using T = typename Store<S>::C;
-  const int pc = (int)D.pitch;
-  const int sy = D.nx, sz = D.nx * D.ny;
-  S* base = N.g + idx;
-  T g[kQ];
-#pragma unroll
-  for (int i = 0; i < kQ; ++i)
-    g[i] = LD<S, CG>(base + (OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz)));
-  collide_p<T, true>(P, g);
-#pragma unroll
-  for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz)), g[j]);
-}
-
 // A warp whose cells are all interior (or skipped) takes the plain streaming
 // form; a warp with any wall, inflow or lid link takes the link-kind form for
 // all its cells, so neither diverges.
 template <class S, bool CG>
 __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R, float r, float r1) {
+  using T = typename Store<S>::C;
   if (!R.valid) return;
   const DevDomain& D = P.dom[R.d];
-  const Node<S> N = node_view<S>(D, R.node);
-  const int plane = D.nx * D.ny;
-  int idx = R.x + D.nx * (R.y + D.ny * R.z0);
-  for (int z = R.z0; z < R.z1; ++z, idx += plane) {
-    const LinkWord lw = __ldg(D.link + idx);
+  const int sy = D.nx, sz = D.nx * D.ny;
+  const int idx0 = R.x + D.nx * (R.y + D.ny * R.z0);
+  const int pc = (int)D.pitch;
+  S* base = reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0;
+  const LinkWord* lp = D.link + idx0;
+  const float4* uinf = D.uin_f + (long long)R.node * D.nz;
+  const double* uind = D.uin_d + (long long)R.node * D.nz * 3;
+  LinkWord next = __ldg(lp);
+  for (int z = R.z0; z < R.z1; ++z, base += sz, lp += sz) {
+    const LinkWord lw = next;
+    if (z + 1 < R.z1) next = __ldg(lp + sz);
     const bool interior = __all_sync(__activemask(), lw == 0 || (lw & kLinkSlow));
     if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
-    if (interior) cell_odd_stream<S, CG>(P, D, N, idx);
-    else cell_odd_bulk<S, CG>(P, D, N, lw, idx, z, r, r1);
+    T g[kQ];
+    if (interior) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i)
+        g[i] = LD<S, CG>(base + (OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz)));
+      collide_p<T, true>(P, g);
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz)), g[j]);
+    } else {
+      Node<S> N;
+      N.g = nullptr;
+      N.bout = nullptr;
+      N.uinf = uinf;
+      N.uind = uind;
+      T ux, uy, uz;
+      wall_velocity<S>(N, lw, z, ux, uy, uz);
+      fast_pull<S, CG>(base, lw, pc, sy, sz, ux, uy, uz, T(r), g);
+      collide_p<T, true>(P, g);
+      fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, T(r1), g);
+    }
   }
+}
+
+// Listed (node, cell) items: item -> domain, node and cell index.
+__device__ __forceinline__ int decode_bitem(const StepParams& P, long long item, int* node, long long* idx) {
+  int d = 0;
+  for (int k = 1; k < P.n_domains; ++k)
+    if (item >= P.dom[k].bitem_begin) d = k;
+  const DevDomain& D = P.dom[d];
+  const long long k = item - D.bitem_begin;
+  *node = (int)(k / D.nb);
+  *idx = __ldg(D.bcell + (k % D.nb));
+  return d;
 }
 
 // Boundary cells of the odd level: one thread per (node, listed cell).
@@ -223,13 +256,9 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
                                                   float r1) {
   using T = typename Store<S>::C;
   if (item >= P.total_bitems) return;
-  int d = 0;
-  for (int k = 1; k < P.n_domains; ++k)
-    if (item >= P.dom[k].bitem_begin) d = k;
-  const DevDomain& D = P.dom[d];
-  const long long k = item - D.bitem_begin;
-  const int node = (int)(k / D.nb);
-  const long long idx = __ldg(D.bcell + (k % D.nb));
+  int node;
+  long long idx;
+  const DevDomain& D = P.dom[decode_bitem(P, item, &node, &idx)];
   const int x = (int)(idx % D.nx);
   const int y = (int)((idx / D.nx) % D.ny);
   const int z = (int)(idx / ((long long)D.nx * D.ny));
@@ -237,9 +266,45 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   cell_odd_general<S, CG>(P, D, node_view<S>(D, node), lw, x, y, z, idx, T(r), T(r1));
 }
 
+// Listed cells of the even level (local update; outlet cells save their
+// outflow plane values).
+template <class S, bool CG>
+__device__ __forceinline__ void even_boundary_item(const StepParams& P, long long item) {
+  if (item >= P.total_bitems) return;
+  int node;
+  long long idx;
+  const DevDomain& D = P.dom[decode_bitem(P, item, &node, &idx)];
+  const int y = (int)((idx / D.nx) % D.ny);
+  const int z = (int)(idx / ((long long)D.nx * D.ny));
+  const LinkWord lw = __ldg(D.link + idx);
+  cell_even<S, CG>(P, D, node_view<S>(D, node), lw, y, z, idx);
+}
+
 __device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long m) {
   const unsigned long long k = m < (unsigned long long)P.ramp_steps ? m : (unsigned long long)P.ramp_steps;
   return P.ramp_f[k];
+}
+
+// Blocks of an even or odd launch that carry the listed (node, cell) items:
+// ceil(items / threads) of them, spread evenly over the grid (every q-th
+// block) so their long-latency work overlaps the bulk tiles throughout the
+// launch.  Returns true for a listed block, with its rank among the listed
+// blocks in *index, else the rank among the bulk blocks (the tile index).
+__device__ __forceinline__ bool block_role(const StepParams& P, unsigned* index) {
+  const long long threads = (long long)blockDim.x * blockDim.y;
+  const unsigned listed = (unsigned)((P.total_bitems + threads - 1) / threads);
+  const unsigned b = blockIdx.x;
+  if (listed == 0) {
+    *index = b;
+    return false;
+  }
+  const unsigned q = gridDim.x / listed;  // >= 1: the grid is tiles + listed blocks
+  if (b % q == 0 && b / q < listed) {
+    *index = b / q;
+    return true;
+  }
+  *index = b - min((b + q - 1) / q, listed);
+  return false;
 }
 
 // Even time level for every (domain, node, tile).  The even level carries no
@@ -248,30 +313,29 @@ __device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long
 // (4: at most 64 registers; 3: at most 85), chosen by the autotuner.
 template <class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constant__ StepParams P) {
-  even_tile<S, false>(P, block_tile(P, blockIdx.x));
+  unsigned k;
+  if (block_role(P, &k)) {
+    const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
+    even_boundary_item<S, false>(P, item);
+    return;
+  }
+  even_tile<S, false, true>(P, block_tile(P, k));
 }
 
-// Blocks at the head of the odd launch that carry listed boundary items.
-__device__ __forceinline__ unsigned odd_lead_blocks(const StepParams& P) {
-  const long long threads = (long long)blockDim.x * blockDim.y;
-  return (unsigned)((P.total_bitems + threads - 1) / threads);
-}
-
-// Odd time level in one launch: the leading blocks take the listed boundary
+// Odd time level in one launch: the listed blocks take the listed boundary
 // cells (one thread per (node, cell)), the rest the tiles of bulk cells.  The
 // two sets touch disjoint slots, so the long-latency boundary work overlaps
 // with the bulk stream.  The inflow ramp factors of the odd level n (pulls,
 // r(n)) and of level n + 1 (pushes) come with the launch.
 template <class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
-  const unsigned lead = odd_lead_blocks(P);
-  if (blockIdx.x < lead) {
-    const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x +
-                           threadIdx.x;
+  unsigned k;
+  if (block_role(P, &k)) {
+    const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
     odd_boundary_item<S, false>(P, item, P.r_pull, P.r_push);
     return;
   }
-  odd_bulk_tile<S, false>(P, block_tile(P, blockIdx.x - lead), P.r_pull, P.r_push);
+  odd_bulk_tile<S, false>(P, block_tile(P, k), P.r_pull, P.r_push);
 }
 
 // Odd time level, listed boundary cells alone (after the TMA odd kernel of the
@@ -602,7 +666,7 @@ __device__ bool grid_barrier(const StepParams& P, unsigned int& gen) {
 // One cooperative launch advances n_steps; blocks stride over the work of
 // each level and meet at a grid barrier between time steps.
 template <class S>
-__global__ void __launch_bounds__(256) aa_persistent_kernel(const __grid_constant__ StepParams P) {
+__global__ void __launch_bounds__(256, 3) aa_persistent_kernel(const __grid_constant__ StepParams P) {
   __shared__ unsigned long long s_n;
   __shared__ unsigned int s_gen;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -617,7 +681,7 @@ __global__ void __launch_bounds__(256) aa_persistent_kernel(const __grid_constan
   for (int s = 0; s < P.n_steps; ++s) {
     if ((n & 1ull) == 0) {
       for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) {
-        even_tile<S, true>(P, block_tile(P, (unsigned)t));
+        even_tile<S, true, false>(P, block_tile(P, (unsigned)t));
         __syncthreads();  // the shared tile head is rewritten next iteration
       }
     } else {
@@ -981,21 +1045,22 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
         if (rc) return rc;
         if ((long long)tgrid > P.total_runs) tgrid = (int)P.total_runs;
       }
+      // listed items ride in blocks spread over the per-thread launches
+      const long long threads = (long long)P.bx * P.by;
+      const unsigned lgrid = (unsigned)(P.total_tiles + (P.total_bitems + threads - 1) / threads);
       if (parity == 0) {
         if (P.tma) aa_even_tma_kernel<S><<<tgrid, kTmaThreads, even_tma_smem<S>(), s>>>(P);
-        else if (P.regs85) aa_even_kernel<S, 3><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
-        else aa_even_kernel<S, 4><<<(unsigned)P.total_tiles, block, 0, s>>>(P);
+        else if (P.regs85) aa_even_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
+        else aa_even_kernel<S, 4><<<lgrid, block, 0, s>>>(P);
       } else {
-        const long long threads = (long long)P.bx * P.by;
-        const unsigned ogrid = (unsigned)(P.total_tiles + (P.total_bitems + threads - 1) / threads);
         if (P.tma) {
           aa_odd_tma_kernel<S><<<tgrid, kTmaThreads, odd_tma_smem<S>(), s>>>(P);
           const long long grid = (P.total_bitems + 255) / 256;
           aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
         } else if (P.regs85) {
-          aa_odd_bulk_kernel<S, 3><<<ogrid, block, 0, s>>>(P);
+          aa_odd_bulk_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
         } else {
-          aa_odd_bulk_kernel<S, 4><<<ogrid, block, 0, s>>>(P);
+          aa_odd_bulk_kernel<S, 4><<<lgrid, block, 0, s>>>(P);
         }
       }
       return (int)cudaGetLastError();
