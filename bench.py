@@ -69,7 +69,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cu", "sclbm_internal.h"):
+    for f in ("lbm_kernels.cu", "lbm_device.cuh", "sclbm_internal.h"):
         with open(os.path.join(ROOT, "paper_2508_18202_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
