@@ -127,9 +127,11 @@ typedef struct {
  * stays in L2), 1 runs all patches of one node first.  graph_steps: time
  * steps per captured graph (SC_EXEC_GRAPH).  variant 0 loads per thread
  * with a register budget for 4 resident blocks of 256 threads, 2 the same
- * for 3 blocks, 1 streams runs of 256 consecutive cells through shared
- * memory with TMA bulk copies (needs nx a multiple of 16 bytes of
- * populations; launch and graph modes only).                                */
+ * for 3 blocks, 3 uses 4 blocks for the even and 3 for the odd level, 1
+ * streams runs of 256 consecutive cells through shared memory with TMA bulk
+ * copies (needs nx a multiple of 16 bytes of populations; launch and graph
+ * modes only).  Default: 64 x 2, slab 8, tile order 1, variant 0, launch
+ * mode.                                                                     */
 typedef struct {
   int block_x, block_y, slab_z, tile_order, exec_mode, graph_steps, variant;
 } sc_lbm_tuning;

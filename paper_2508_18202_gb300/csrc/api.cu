@@ -36,7 +36,7 @@ struct DomLayout {
   int nq = 0, P = 0;
   long long ncell = 0, pitch = 0;
   size_t guard = 0;
-  size_t flags = 0, link = 0, bcell = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
+  size_t flags = 0, link = 0, cls = 0, bcell = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
 };
 struct Layout {
   size_t hdr = 0, ramp_f = 0, ramp_d = 0, probes = 0;
@@ -135,6 +135,7 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     M.ncell = (long long)D.nx * D.ny * D.nz;
     M.flags = take((size_t)M.ncell);
     M.link = take(sizeof(LinkWord) * (size_t)M.ncell);
+    M.cls = take((size_t)M.ncell);
     M.bcell = take(sizeof(int32_t) * (size_t)M.ncell);  // boundary list, at most every cell
     M.uin_f = take(16 * (size_t)M.nq * D.nz);
     M.uin_d = take(24 * (size_t)M.nq * D.nz);
@@ -306,7 +307,8 @@ void apply_tiling(sc_lbm_t h) {
   P.total_bitems = bbegin;
   P.total_runs = rbegin;
   P.tma = (h->tune.variant == 1 && h->tma_ok && h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
-  P.regs85 = h->tune.variant == 2 ? 1 : 0;
+  P.even85 = h->tune.variant == 2 ? 1 : 0;
+  P.odd85 = (h->tune.variant == 2 || h->tune.variant == 3) ? 1 : 0;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -322,7 +324,7 @@ int check_tuning(const sc_lbm_tuning& t) {
   if (t.tile_order < 0 || t.tile_order > 1) return SC_ERR_ARG;
   if (t.exec_mode < SC_EXEC_LAUNCH || t.exec_mode > SC_EXEC_PERSISTENT) return SC_ERR_ARG;
   if (t.graph_steps < 1 || t.graph_steps > 100000) return SC_ERR_ARG;
-  if (t.variant < 0 || t.variant > 2) return SC_ERR_ARG;
+  if (t.variant < 0 || t.variant > 3) return SC_ERR_ARG;
   return SC_OK;
 }
 
@@ -580,6 +582,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   std::vector<std::vector<uint8_t>> flags(c.n_domains);
   std::vector<std::vector<LinkWord>> links(c.n_domains);
   std::vector<std::vector<int32_t>> bcells(c.n_domains);
+  std::vector<std::vector<uint8_t>> classes(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
   std::vector<float> rampf(c.ramp_steps + 1);
@@ -602,6 +605,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     }
     hn_link_words(D, flags[d].data(), links[d]);
     hn_boundary_cells(links[d], bcells[d]);
+    hn_cell_classes(links[d], classes[d]);
     std::vector<double> Z, w;
     node_count(&c, d, &Z, &w);
     const int nq = (int)w.size();
@@ -644,6 +648,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     for (int f = 0; f < 6; ++f) V.bc[f] = D.bc[f];
     V.flags = (const uint8_t*)(h->ws + M.flags);
     V.link = (const LinkWord*)(h->ws + M.link);
+    V.cls = (const uint8_t*)(h->ws + M.cls);
     V.bcell = (const int32_t*)(h->ws + M.bcell);
     V.nb = (long long)bcells[d].size();
     V.uin_f = (const float4*)(h->ws + M.uin_f);
@@ -657,11 +662,11 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   for (int d = 0; d < c.n_domains; ++d)
     if (c.domains[d].nx % (int)(16 / storage_bytes(c.precision)) != 0) h->tma_ok = 0;
   // default launch shape
-  h->tune.variant = h->tma_ok ? 1 : 0;
-  h->tune.block_x = 128;
+  h->tune.variant = 0;
+  h->tune.block_x = 64;
   h->tune.block_y = 2;
-  h->tune.slab_z = 1;
-  h->tune.tile_order = 0;
+  h->tune.slab_z = 8;
+  h->tune.tile_order = 1;
   h->tune.exec_mode = SC_EXEC_LAUNCH;
   h->tune.graph_steps = 50;
   apply_tiling(h);
@@ -676,6 +681,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     const DomLayout& M = L.dom[d];
     e = up(M.flags, flags[d].data(), flags[d].size());
     if (e == cudaSuccess) e = up(M.link, links[d].data(), sizeof(LinkWord) * links[d].size());
+    if (e == cudaSuccess) e = up(M.cls, classes[d].data(), classes[d].size());
     if (e == cudaSuccess && !bcells[d].empty())
       e = up(M.bcell, bcells[d].data(), sizeof(int32_t) * bcells[d].size());
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
@@ -822,7 +828,7 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
       for (int bz : bzs) {
         if (bx * by > 256 || bx * by < 64) continue;
         for (int order = 0; order < 2; ++order)
-          for (int v : {0, 2}) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50, v});
+          for (int v : {0, 2, 3}) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50, v});
       }
   }
   if (h->tma_ok)

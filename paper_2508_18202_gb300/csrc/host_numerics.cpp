@@ -396,6 +396,21 @@ void hn_boundary_cells(const std::vector<LinkWord>& link, std::vector<int32_t>& 
     if (!(link[c] & kLinkSolid) && (link[c] & (kLinkOutlet | kLinkComplex))) cells.push_back((int32_t)c);
 }
 
+void hn_cell_classes(const std::vector<LinkWord>& link, std::vector<uint8_t>& cls) {
+  cls.assign(link.size(), 0);
+  for (size_t c = 0; c < link.size(); ++c) {
+    const LinkWord w = link[c];
+    uint8_t k = 0;
+    if (w & kLinkSlow) k |= kClsSkip;
+    for (int i = 0; i < kQ; ++i) {
+      const int kind = link_kind(w, i);
+      if (kind != kStream) k |= kClsWall;
+      if (kind == kMoving || kind == kSpecZ) k |= kClsMoveSpec;
+    }
+    cls[c] = k;
+  }
+}
+
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin) {
   const double theta = theta_deg * M_PI / 180.0;

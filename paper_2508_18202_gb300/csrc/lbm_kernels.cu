@@ -152,17 +152,17 @@ __device__ __forceinline__ TileRef block_tile(const StepParams& P, unsigned t) {
 // LISTED_APART: listed cells (outlet, general boundary) are left to the
 // leading blocks of the launch, so the bulk path carries no outlet save.
 // Even level, bulk cells of a z-run: n cells, plane apart, from base (slot 0
-// of the first cell) and its link words lp.  Only these scalars stay live in
-// the loop.
+// of the first cell) and their class bytes cp.  Only these scalars stay live
+// in the loop; the next cell's class byte is loaded one cell ahead.
 template <class S, bool CG>
-__device__ __forceinline__ void even_run(const StepParams& P, S* base, const LinkWord* lp, int pc, int plane,
+__device__ __forceinline__ void even_run(const StepParams& P, S* base, const uint8_t* cp, int pc, int plane,
                                          int n) {
   using T = typename Store<S>::C;
-  LinkWord next = __ldg(lp);
-  for (int k = 0; k < n; ++k, base += plane, lp += plane) {
-    const LinkWord lw = next;
-    if (k + 1 < n) next = __ldg(lp + plane);
-    if (lw & kLinkSlow) continue;
+  uint8_t next = __ldg(cp);
+  for (int k = 0; k < n; ++k, base += plane, cp += plane) {
+    const uint8_t cls = next;
+    if (k + 1 < n) next = __ldg(cp + plane);
+    if (cls & kClsSkip) continue;
     T g[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(base + i * pc);
@@ -181,7 +181,7 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
   const int plane = D.nx * D.ny;
   const int idx0 = R.x + D.nx * (R.y + D.ny * R.z0);
   if (LISTED_APART) {
-    even_run<S, CG>(P, reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0, D.link + idx0,
+    even_run<S, CG>(P, reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0, D.cls + idx0,
                     (int)D.pitch, plane, R.z1 - R.z0);
     return;
   }
@@ -194,9 +194,10 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
   }
 }
 
-// A warp whose cells are all interior (or skipped) takes the plain streaming
-// form; a warp with any wall, inflow or lid link takes the link-kind form for
-// all its cells, so neither diverges.
+// Odd level over the z-slab of a tile.  A warp whose cells are all interior
+// (or skipped) takes the plain streaming form; a warp with any wall, inflow
+// or lid link takes the link-kind form for all its cells, so neither
+// diverges.  The next cell's link word is loaded one cell ahead.
 template <class S, bool CG>
 __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R, float r, float r1) {
   using T = typename Store<S>::C;
@@ -1050,14 +1051,14 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
       const unsigned lgrid = (unsigned)(P.total_tiles + (P.total_bitems + threads - 1) / threads);
       if (parity == 0) {
         if (P.tma) aa_even_tma_kernel<S><<<tgrid, kTmaThreads, even_tma_smem<S>(), s>>>(P);
-        else if (P.regs85) aa_even_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
+        else if (P.even85) aa_even_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
         else aa_even_kernel<S, 4><<<lgrid, block, 0, s>>>(P);
       } else {
         if (P.tma) {
           aa_odd_tma_kernel<S><<<tgrid, kTmaThreads, odd_tma_smem<S>(), s>>>(P);
           const long long grid = (P.total_bitems + 255) / 256;
           aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
-        } else if (P.regs85) {
+        } else if (P.odd85) {
           aa_odd_bulk_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
         } else {
           aa_odd_bulk_kernel<S, 4><<<lgrid, block, 0, s>>>(P);

@@ -42,6 +42,13 @@ __host__ __device__
 #endif
 inline int link_kind(LinkWord w, int i) { return (int)((w >> (2 * i)) & 3ull); }
 
+// Per-cell class byte read by the bulk loops (one byte, so the decision for
+// the next cell costs little L2 traffic); the link word is read only where
+// kClsWall is set.
+constexpr uint8_t kClsSkip = 1;      // solid, or listed for the general boundary path
+constexpr uint8_t kClsWall = 2;      // some link does not stream
+constexpr uint8_t kClsMoveSpec = 4;  // some link is a moving wall or specular
+
 // Device error word bits.
 constexpr unsigned kErrDiverged = 1u;
 constexpr unsigned kErrTimeout = 2u;
@@ -53,6 +60,7 @@ struct DevDomain {
   int bc[6];
   const uint8_t* flags;     // [ncell]
   const LinkWord* link;     // [ncell]
+  const uint8_t* cls;       // [ncell] kCls* bits: what the bulk loops need to know
   const float4* uin_f;      // [nodes][nz] (ux, uy, uz, 0)
   const double* uin_d;      // [nodes][nz][3]
   long long pitch;          // population row stride (elements), multiple of kRun
@@ -85,7 +93,7 @@ struct StepParams {
   long long total_bitems;      // boundary (node, cell) items of all domains
   long long total_runs;        // runs of kRun cells of all domains and nodes
   int tma;                     // bulk kernels staged through shared memory by TMA
-  int regs85;                  // per-thread bulk kernels sized for 3 blocks (85 registers)
+  int odd85, even85;           // per-thread odd / even kernels sized for 3 blocks (85 registers)
   int bx, by, bz, order;
   // persistent mode
   unsigned int* bar_count;
@@ -106,6 +114,7 @@ int hn_probe_columns(const sc_domain_desc& D, const uint8_t* flags, int n, int32
 int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xyz);
 void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<LinkWord>& link);
 void hn_boundary_cells(const std::vector<LinkWord>& link, std::vector<int32_t>& cells);
+void hn_cell_classes(const std::vector<LinkWord>& link, std::vector<uint8_t>& cls);
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin /*[nz][3]*/);
 int hn_gpc_size(int d, int degree);

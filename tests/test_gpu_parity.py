@@ -181,10 +181,11 @@ def _states(ens):
 @pytest.mark.parametrize("shape", [(32, 1, 1, 0), (64, 4, 2, 1), (128, 2, 4, 0), (256, 1, 3, 1)])
 def test_launch_shapes_and_modes_are_bitwise_identical(cuda, shape):
     """Every launch shape, tile order, execution mode (launch, graph,
-    persistent) and kernel form (per-thread, TMA-staged) gives the same bits."""
+    persistent) and kernel form (per-thread with either register budget,
+    TMA-staged) gives the same bits."""
     wl = ragged(BC_SETS["urban"], nx=40)
     want = {}
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         ref = S.Ensemble(S.make_config(wl))
         S.sc_lbm_set_tuning(ref.h, 64, 1, 1, variant=variant)
         ref.step(17)
@@ -192,11 +193,11 @@ def test_launch_shapes_and_modes_are_bitwise_identical(cuda, shape):
         ref.close()
     # the two kernel forms are compiled separately (rounding may differ in the
     # last bit); within a form every shape and mode is bitwise identical
-    for v in (1, 2):
+    for v in (1, 2, 3):
         for a, b in zip(want[0], want[v]):
             assert np.max(np.abs(a - b)) < 1e-6
     for mode in (S.SC_EXEC_LAUNCH, S.SC_EXEC_GRAPH, S.SC_EXEC_PERSISTENT):
-        for variant in (0, 1, 2):
+        for variant in (0, 1, 2, 3):
             ens = S.Ensemble(S.make_config(wl))
             S.sc_lbm_set_tuning(ens.h, *shape, exec_mode=mode, graph_steps=4, variant=variant)
             ens.step(17)
