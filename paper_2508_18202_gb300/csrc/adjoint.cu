@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
   if (c >= D.ncell) return;
   const LinkWord lw = __ldg(D.link + c);
   if (lw & kLinkSolid) return;
-  const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
+  const int z = (int)(c / ((long long)D.nx * D.ny));
   const long long pc = D.pitch;
   float g[kQ];
 #pragma unroll
@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
     fast_push<float>(dst + c, lw, (int)pc, D.nx, D.nx * D.ny, ux, uy, uz, r1, g);
     return;
   }
-  push_general<float>(D, N, dst, lw, x, y, z, c, g, r1);
+  const ListedLinks* L = D.ltab + listed_index(D, c);
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+  if (L->push_move) inflow_velocity<float>(N, z, ux, uy, uz);
+  listed_push<float>(L, dst, ux, uy, uz, r1, g);
 }
 
 // Loss at the probes and the adjoint seed lambda^T = dJ/df^T

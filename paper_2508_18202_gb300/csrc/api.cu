@@ -36,7 +36,8 @@ struct DomLayout {
   int nq = 0, P = 0;
   long long ncell = 0, pitch = 0;
   size_t guard = 0;
-  size_t flags = 0, link = 0, cls = 0, bcell = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
+  long long nb_max = 0;
+  size_t flags = 0, link = 0, cls = 0, bcell = 0, ltab = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
 };
 struct Layout {
   size_t hdr = 0, ramp_f = 0, ramp_d = 0, probes = 0;
@@ -136,7 +137,15 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     M.flags = take((size_t)M.ncell);
     M.link = take(sizeof(LinkWord) * (size_t)M.ncell);
     M.cls = take((size_t)M.ncell);
-    M.bcell = take(sizeof(int32_t) * (size_t)M.ncell);  // boundary list, at most every cell
+    // listed cells lie on faces of kind OUTFLOW, PERIODIC or FREE_SLIP
+    const long long area[3] = {(long long)D.ny * D.nz, (long long)D.nx * D.nz, (long long)D.nx * D.ny};
+    M.nb_max = 0;
+    for (int f = 0; f < 6; ++f)
+      if (D.bc[f] == SC_BC_OUTFLOW || D.bc[f] == SC_BC_PERIODIC || D.bc[f] == SC_BC_FREE_SLIP)
+        M.nb_max += area[f >> 1];
+    M.nb_max = std::min(M.nb_max, M.ncell);
+    M.bcell = take(sizeof(int32_t) * (size_t)M.nb_max);
+    M.ltab = take(sizeof(ListedLinks) * (size_t)M.nb_max);
     M.uin_f = take(16 * (size_t)M.nq * D.nz);
     M.uin_d = take(24 * (size_t)M.nq * D.nz);
     M.pitch = (M.ncell + kRun - 1) / kRun * kRun;
@@ -583,6 +592,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   std::vector<std::vector<LinkWord>> links(c.n_domains);
   std::vector<std::vector<int32_t>> bcells(c.n_domains);
   std::vector<std::vector<uint8_t>> classes(c.n_domains);
+  std::vector<std::vector<ListedLinks>> ltabs(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
   std::vector<float> rampf(c.ramp_steps + 1);
@@ -606,6 +616,11 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     hn_link_words(D, flags[d].data(), links[d]);
     hn_boundary_cells(links[d], bcells[d]);
     hn_cell_classes(links[d], classes[d]);
+    if ((long long)bcells[d].size() > L.dom[d].nb_max) {
+      delete h;
+      return SC_ERR_ARG;  // cannot happen: listed cells lie on the counted faces
+    }
+    hn_listed_links(D, flags[d].data(), links[d], bcells[d], L.dom[d].pitch, ltabs[d]);
     std::vector<double> Z, w;
     node_count(&c, d, &Z, &w);
     const int nq = (int)w.size();
@@ -650,6 +665,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     V.link = (const LinkWord*)(h->ws + M.link);
     V.cls = (const uint8_t*)(h->ws + M.cls);
     V.bcell = (const int32_t*)(h->ws + M.bcell);
+    V.ltab = (const ListedLinks*)(h->ws + M.ltab);
     V.nb = (long long)bcells[d].size();
     V.uin_f = (const float4*)(h->ws + M.uin_f);
     V.uin_d = (const double*)(h->ws + M.uin_d);
@@ -684,6 +700,8 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     if (e == cudaSuccess) e = up(M.cls, classes[d].data(), classes[d].size());
     if (e == cudaSuccess && !bcells[d].empty())
       e = up(M.bcell, bcells[d].data(), sizeof(int32_t) * bcells[d].size());
+    if (e == cudaSuccess && !ltabs[d].empty())
+      e = up(M.ltab, ltabs[d].data(), sizeof(ListedLinks) * ltabs[d].size());
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
     if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
     if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());

@@ -411,6 +411,193 @@ void hn_cell_classes(const std::vector<LinkWord>& link, std::vector<uint8_t>& cl
   }
 }
 
+namespace {
+
+int h_opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+int h_dir(int x, int y, int z) {
+  for (int i = 0; i < kQ; ++i)
+    if (kCx[i] == x && kCy[i] == y && kCz[i] == z) return i;
+  return 0;
+}
+int h_refl(int i, int a) {
+  return h_dir(a == 0 ? -kCx[i] : kCx[i], a == 1 ? -kCy[i] : kCy[i], a == 2 ? -kCz[i] : kCz[i]);
+}
+int h_kout(int i) { return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1; }
+
+struct HCross {
+  int n;     // faces crossed
+  int f[2];  // face ids
+  int p[3];  // position with periodic axes wrapped
+};
+
+HCross h_classify(const sc_domain_desc& D, int px, int py, int pz) {
+  HCross c;
+  c.n = 0;
+  c.f[0] = c.f[1] = -1;
+  int p[3] = {px, py, pz};
+  const int n[3] = {D.nx, D.ny, D.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (D.bc[2 * a] == SC_BC_PERIODIC) {
+      if (p[a] < 0) p[a] += n[a];
+      else if (p[a] >= n[a]) p[a] -= n[a];
+    } else if (p[a] < 0) {
+      c.f[c.n < 2 ? c.n : 1] = 2 * a;
+      ++c.n;
+    } else if (p[a] >= n[a]) {
+      c.f[c.n < 2 ? c.n : 1] = 2 * a + 1;
+      ++c.n;
+    }
+  }
+  for (int a = 0; a < 3; ++a) c.p[a] = p[a];
+  return c;
+}
+
+}  // namespace
+
+// Compiles the per-link rules of the listed cells (pull form of the odd AA
+// level, and the matching deliveries) into offsets:
+//   source inside and solid            -> bounce-back (own slot)
+//   one face crossed: BOUNCE_BACK      -> bounce-back
+//                     VELOCITY         -> bounce-back + 6 w_i (c_i . u_in(z)) r
+//                     FREE_SLIP        -> specular reflection from the in-plane
+//                                         neighbour (bounce-back if it is solid)
+//                     OUTFLOW (+x)     -> f*_i of the transverse neighbour on the
+//                                         outlet plane, saved at the even level
+//                                         (own saved value if that cell is solid)
+//   two faces crossed: any wall        -> bounce-back; else any inflow ->
+//                                         moving wall; else (outflow + free
+//                                         slip) the cell's own saved f* reflected
+//                                         across the free-slip face.
+// Deliveries are the transpose: f*_j goes where the pull of the receiving
+// link reads it; outlet cells also copy their f*_j with c_jx = -1 to the
+// outlet links that read them (after the primary deliveries, which they may
+// replace).
+void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::vector<LinkWord>& link,
+                     const std::vector<int32_t>& cells, long long pitch, std::vector<ListedLinks>& tab) {
+  const long long plane = (long long)D.nx * D.ny;
+  auto cidx = [&](const int* p) { return (long long)p[0] + (long long)D.nx * p[1] + plane * p[2]; };
+  auto loff = [&](int i) { return (long long)kCx[i] + (long long)kCy[i] * D.nx + (long long)kCz[i] * plane; };
+  tab.assign(cells.size(), ListedLinks{});
+  for (size_t k = 0; k < cells.size(); ++k) {
+    const long long idx = cells[k];
+    const int x = (int)(idx % D.nx), y = (int)((idx / D.nx) % D.ny), z = (int)(idx / plane);
+    const int xyz[3] = {x, y, z};
+    const LinkWord lw = link[(size_t)idx];
+    ListedLinks& L = tab[k];
+    memset(&L, 0, sizeof(L));
+    for (int i = 0; i < kQ; ++i) {
+      const long long own = (long long)i * pitch + idx;
+      long long src = own;
+      if (link_kind(lw, i) == kStream) {
+        src = (long long)h_opp(i) * pitch + idx - loff(i);
+      } else {
+        const int cx = kCx[i], cy = kCy[i], cz = kCz[i];
+        const HCross c = h_classify(D, x - cx, y - cy, z - cz);
+        if (c.n == 0) {
+          const long long p = cidx(c.p);
+          if (flags[p] == 0) src = (long long)h_opp(i) * pitch + p;
+        } else if (c.n == 1) {
+          const int kind = D.bc[c.f[0]];
+          if (kind == SC_BC_VELOCITY) {
+            L.pull_move |= 1u << i;
+          } else if (kind != SC_BC_BOUNCE_BACK) {
+            const int a = c.f[0] >> 1;
+            int sv[3] = {x - cx, y - cy, z - cz};
+            sv[a] = xyz[a];
+            const HCross cs = h_classify(D, sv[0], sv[1], sv[2]);
+            const long long sp = cidx(cs.p);
+            if (kind == SC_BC_FREE_SLIP) {
+              if (flags[sp] == 0) src = (long long)h_opp(h_refl(i, a)) * pitch + sp;
+            } else {  // OUTFLOW on +x
+              L.bout_mask |= 1u << i;
+              src = flags[sp] == 0 ? ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + h_kout(i)
+                                   : ((long long)z * D.ny + y) * 5 + h_kout(i);
+            }
+          }
+        } else {
+          const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
+          if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) {
+          } else if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) {
+            L.pull_move |= 1u << i;
+          } else if (!(k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP)) {
+            const int fs = (k0 == SC_BC_FREE_SLIP) ? c.f[0] : c.f[1];
+            L.bout_mask |= 1u << i;
+            src = ((long long)z * D.ny + y) * 5 + h_kout(h_refl(i, fs >> 1));
+          }
+        }
+      }
+      L.src[i] = (int32_t)src;
+    }
+    for (int j = 0; j < kQ; ++j) {
+      const int oj = h_opp(j);
+      const long long own = (long long)oj * pitch + idx;
+      long long dst = own;
+      if (link_kind(lw, oj) == kStream) {
+        dst = (long long)j * pitch + idx + loff(j);
+      } else {
+        const int cx = kCx[j], cy = kCy[j], cz = kCz[j];
+        const HCross c = h_classify(D, x + cx, y + cy, z + cz);
+        if (c.n == 0) {
+          const long long q = cidx(c.p);
+          if (flags[q] == 0) dst = (long long)j * pitch + q;
+        } else if (c.n == 1) {
+          const int kind = D.bc[c.f[0]];
+          if (kind == SC_BC_VELOCITY) {
+            L.push_move |= 1u << j;
+          } else if (kind == SC_BC_FREE_SLIP) {
+            const int a = c.f[0] >> 1;
+            int t[3] = {x + cx, y + cy, z + cz};
+            t[a] = xyz[a];
+            const HCross ct = h_classify(D, t[0], t[1], t[2]);
+            const long long tp = cidx(ct.p);
+            if (flags[tp] == 0) dst = (long long)h_refl(j, a) * pitch + tp;
+          } else if (kind != SC_BC_BOUNCE_BACK) {
+            dst = -1;  // OUTFLOW: leaves the domain
+          }
+        } else {
+          const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
+          if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) {
+          } else if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) {
+            L.push_move |= 1u << j;
+          } else if (!(k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP)) {
+            dst = -1;  // outflow + free slip: delivered by the outlet copies
+          }
+        }
+      }
+      L.dst[j] = (int32_t)dst;
+    }
+    for (int m = 0; m < kOutletPops * kOutletCopies; ++m) L.extra[m] = -1;
+    if (lw & kLinkOutlet) {
+      const int pops[kOutletPops] = {2, 8, 10, 12, 14};
+      for (int e = 0; e < kOutletPops; ++e) {
+        const int j = pops[e], cy = kCy[j], cz = kCz[j];
+        int m = 0;
+        // (1) the transverse neighbour on the outlet plane copies it
+        {
+          const HCross c = h_classify(D, x, y + cy, z + cz);
+          if (c.n == 0 && flags[cidx(c.p)] == 0)
+            L.extra[e * kOutletCopies + m++] = (int32_t)((long long)j * pitch + cidx(c.p));
+        }
+        // (2) own link j whose transverse source is solid takes its own value
+        {
+          const HCross c = h_classify(D, x, y - cy, z - cz);
+          if (c.n == 0 && flags[cidx(c.p)] != 0) L.extra[e * kOutletCopies + m++] = (int32_t)((long long)j * pitch + idx);
+        }
+        // (3) outflow + free-slip edge: reflected copy into the own cell
+        for (int a = 1; a < 3; ++a) {
+          const int cj = a == 1 ? cy : cz;
+          if (cj == 0) continue;
+          const int face = 2 * a + (cj > 0 ? 1 : 0);
+          const int pos = (a == 1 ? y : z) + cj;
+          const int lim = a == 1 ? D.ny : D.nz;
+          if (D.bc[face] == SC_BC_FREE_SLIP && (pos < 0 || pos >= lim))
+            L.extra[e * kOutletCopies + m++] = (int32_t)((long long)h_refl(j, a) * pitch + idx);
+        }
+      }
+    }
+  }
+}
+
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin) {
   const double theta = theta_deg * M_PI / 180.0;

@@ -239,178 +239,8 @@ struct Node {
   const double* uind;  // [nz][3]
 };
 
-// Inflow correction 6 w_i rho_w (c_i . u_w(z)) r of direction i (rho_w = 1).
-template <class S, class T>
-__device__ __forceinline__ T vel_term(const Node<S>& N, int i, int z, T r) {
-  if constexpr (sizeof(T) == 8) {
-    const double* u = N.uind + 3 * z;
-    const T cu = T(c_lat.cx[i]) * T(u[0]) + T(c_lat.cy[i]) * T(u[1]) + T(c_lat.cz[i]) * T(u[2]);
-    return T(6) * T(c_lat.wd[i]) * cu * r;
-  } else {
-    const float4 u = N.uinf[z];
-    const T cu = T(c_lat.cx[i]) * T(u.x) + T(c_lat.cy[i]) * T(u.y) + T(c_lat.cz[i]) * T(u.z);
-    return T(6) * T(c_lat.wf[i]) * cu * r;
-  }
-}
-
-// f_i of time level n (odd, AA swapped layout) for a boundary link.
-template <class S, bool CG>
-__device__ typename Store<S>::C pull_special(const DevDomain& D, const Node<S>& N, int i, int x,
-                                             int y, int z, long long idx,
-                                             typename Store<S>::C r) {
-  using T = typename Store<S>::C;
-  const long long pc = D.pitch;
-  const int cx = c_lat.cx[i], cy = c_lat.cy[i], cz = c_lat.cz[i];
-  const Cross c = classify(D, x - cx, y - cy, z - cz);
-  const T own = LD<S, CG>(N.g + (long long)i * pc + idx);  // f*_opp(i)(x)
-  if (c.n == 0) {
-    const long long p = cidx(D, c.p[0], c.p[1], c.p[2]);
-    if (D.flags[p] == 0) return LD<S, CG>(N.g + (long long)c_lat.opp[i] * pc + p);
-    return own;
-  }
-  if (c.n == 1) {
-    const int kind = D.bc[c.f[0]];
-    if (kind == SC_BC_BOUNCE_BACK) return own;
-    if (kind == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
-    const int a = c.f[0] >> 1;
-    int s[3] = {x - cx, y - cy, z - cz};
-    s[a] = a == 0 ? x : (a == 1 ? y : z);
-    const Cross cs = classify(D, s[0], s[1], s[2]);
-    const long long sp = cidx(D, cs.p[0], cs.p[1], cs.p[2]);
-    if (kind == SC_BC_FREE_SLIP) {
-      if (D.flags[sp] == 0) return LD<S, CG>(N.g + (long long)c_lat.opp[c_lat.refl[i][a]] * pc + sp);
-      return own;
-    }
-    // OUTFLOW on +x: transverse source on the outlet plane
-    if (D.flags[sp] == 0)
-      return T(__ldcg(N.bout + ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + c_lat.kout[i]));
-    return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + c_lat.kout[i]));
-  }
-  const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
-  if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) return own;
-  if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) return own + vel_term<S, T>(N, i, z, r);
-  if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) return own;
-  // outflow + free slip: own population reflected across the free-slip face
-  const int fs = (k0 == SC_BC_FREE_SLIP) ? c.f[0] : c.f[1];
-  return T(__ldcg(N.bout + ((long long)z * D.ny + y) * 5 + c_lat.kout[c_lat.refl[i][fs >> 1]]));
-}
-
-// Deliver f*_j of cell x for a boundary link into dst (AA: dst == src array).
-template <class S>
-__device__ void push_special(const DevDomain& D, const Node<S>& N, S* dst, int j,
-                             typename Store<S>::C v, int x, int y, int z, long long idx,
-                             typename Store<S>::C r1) {
-  using T = typename Store<S>::C;
-  const long long pc = D.pitch;
-  const int cx = c_lat.cx[j], cy = c_lat.cy[j], cz = c_lat.cz[j], oj = c_lat.opp[j];
-  const Cross c = classify(D, x + cx, y + cy, z + cz);
-  S* own = dst + (long long)oj * pc + idx;
-  if (c.n == 0) {
-    const long long q = cidx(D, c.p[0], c.p[1], c.p[2]);
-    if (D.flags[q] == 0) Store<S>::st(dst + (long long)j * pc + q, v);
-    else Store<S>::st(own, v);
-    return;
-  }
-  if (c.n == 1) {
-    const int kind = D.bc[c.f[0]];
-    if (kind == SC_BC_BOUNCE_BACK) {
-      Store<S>::st(own, v);
-    } else if (kind == SC_BC_VELOCITY) {
-      Store<S>::st(own, v + vel_term<S, T>(N, oj, z, r1));
-    } else if (kind == SC_BC_FREE_SLIP) {
-      const int a = c.f[0] >> 1;
-      int t[3] = {x + cx, y + cy, z + cz};
-      t[a] = a == 0 ? x : (a == 1 ? y : z);
-      const Cross ct = classify(D, t[0], t[1], t[2]);
-      const long long tp = cidx(D, ct.p[0], ct.p[1], ct.p[2]);
-      if (D.flags[tp] == 0) Store<S>::st(dst + (long long)c_lat.refl[j][a] * pc + tp, v);
-      else Store<S>::st(own, v);
-    }
-    // OUTFLOW: the population leaves the domain
-    return;
-  }
-  const int k0 = D.bc[c.f[0]], k1 = D.bc[c.f[1]];
-  if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK) {
-    Store<S>::st(own, v);
-  } else if (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY) {
-    Store<S>::st(own, v + vel_term<S, T>(N, oj, z, r1));
-  } else if (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP) {
-    Store<S>::st(own, v);
-  }
-  // outflow + free slip: delivered by the outlet pushes of the reflected direction
-}
-
-// Outlet cell (x = nx-1, +x OUTFLOW): deliver f*_j (c_jx = -1) to the outlet
-// links that read it.
-template <class S>
-__device__ void push_outlet(const DevDomain& D, S* dst, int j, typename Store<S>::C v, int x, int y,
-                            int z, long long idx) {
-  const long long pc = D.pitch;
-  const int cy = c_lat.cy[j], cz = c_lat.cz[j];
-  // (1) transverse neighbour on the outlet plane copies it
-  {
-    const Cross c = classify(D, x, y + cy, z + cz);
-    if (c.n == 0) {
-      const long long t = cidx(D, c.p[0], c.p[1], c.p[2]);
-      if (D.flags[t] == 0) Store<S>::st(dst + (long long)j * pc + t, v);
-    }
-  }
-  // (2) own link j whose transverse source is solid falls back to own value
-  {
-    const Cross c = classify(D, x, y - cy, z - cz);
-    if (c.n == 0 && D.flags[cidx(D, c.p[0], c.p[1], c.p[2])] != 0)
-      Store<S>::st(dst + (long long)j * pc + idx, v);
-  }
-  // (3) outflow + free-slip edge: reflected copy into the own cell
-  for (int a = 1; a < 3; ++a) {
-    const int cj = a == 1 ? cy : cz;
-    if (cj == 0) continue;
-    const int face = 2 * a + (cj > 0 ? 1 : 0);
-    const int pos = (a == 1 ? y : z) + cj;
-    const int lim = a == 1 ? D.ny : D.nz;
-    if (D.bc[face] == SC_BC_FREE_SLIP && (pos < 0 || pos >= lim))
-      Store<S>::st(dst + (long long)c_lat.refl[j][a] * pc + idx, v);
-  }
-}
-
 __device__ __forceinline__ long long link_offset(const DevDomain& D, int i) {
   return (long long)c_lat.cx[i] + (long long)c_lat.cy[i] * D.nx + (long long)c_lat.cz[i] * D.nx * D.ny;
-}
-
-// f_i of the odd time level at a cell, any link kind (run-time loop, compact).
-template <class S, bool CG>
-__device__ void load_odd_general(const DevDomain& D, const Node<S>& N, LinkWord lw, int x, int y,
-                                 int z, long long idx, typename Store<S>::C g[kQ],
-                                 typename Store<S>::C r) {
-#pragma unroll 1
-  for (int i = 0; i < kQ; ++i) {
-    if (link_kind(lw, i) == kStream)
-      g[i] = LD<S, CG>(N.g + (long long)c_lat.opp[i] * D.pitch + idx - link_offset(D, i));
-    else
-      g[i] = pull_special<S, CG>(D, N, i, x, y, z, idx, r);
-  }
-}
-
-// Push of the odd level (or of the FP64 two-array path) for a cell with
-// boundary links, any link kind.
-template <class S>
-__device__ void push_general(const DevDomain& D, const Node<S>& N, S* dst, LinkWord lw, int x, int y,
-                             int z, long long idx, const typename Store<S>::C g[kQ],
-                             typename Store<S>::C r1) {
-#pragma unroll 1
-  for (int j = 0; j < kQ; ++j) {
-    if (link_kind(lw, c_lat.opp[j]) == kStream)
-      Store<S>::st(dst + (long long)j * D.pitch + idx + link_offset(D, j), g[j]);
-    else
-      push_special<S>(D, N, dst, j, g[j], x, y, z, idx, r1);
-  }
-  if (lw & kLinkOutlet) {
-    push_outlet<S>(D, dst, 2, g[2], x, y, z, idx);
-    push_outlet<S>(D, dst, 8, g[8], x, y, z, idx);
-    push_outlet<S>(D, dst, 10, g[10], x, y, z, idx);
-    push_outlet<S>(D, dst, 12, g[12], x, y, z, idx);
-    push_outlet<S>(D, dst, 14, g[14], x, y, z, idx);
-  }
 }
 
 // ------------------------------------------------------------ fast link rules
@@ -465,6 +295,62 @@ __device__ __forceinline__ void fast_push(S* base, LinkWord lw, int pc, int sy, 
   }
 }
 
+// ------------------------------------------------------------ listed cells
+// Pull of the odd AA level for a listed cell from its compiled rules: g0 is
+// the node's population base, bo its outflow plane (float).
+template <class S, bool CG>
+__device__ __forceinline__ void listed_pull(const ListedLinks* L, const S* g0, const float* bo,
+                                            typename Store<S>::C ux, typename Store<S>::C uy,
+                                            typename Store<S>::C uz, typename Store<S>::C r,
+                                            typename Store<S>::C g[kQ]) {
+  using T = typename Store<S>::C;
+  const uint32_t bm = L->bout_mask, pm = L->pull_move;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int s = L->src[i];
+    T v = ((bm >> i) & 1u) ? T(__ldcg(bo + s)) : LD<S, CG>(g0 + s);
+    if ((pm >> i) & 1u) v += wall_term<T>(i, ux, uy, uz, r);
+    g[i] = v;
+  }
+}
+
+// Deliveries of a listed cell's post-collision populations into the node's
+// array g0 (AA in place, or the destination array of a two-array step).
+template <class S>
+__device__ __forceinline__ void listed_push(const ListedLinks* L, S* g0, typename Store<S>::C ux,
+                                            typename Store<S>::C uy, typename Store<S>::C uz,
+                                            typename Store<S>::C r1, const typename Store<S>::C g[kQ]) {
+  using T = typename Store<S>::C;
+  const uint32_t mm = L->push_move;
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    const int d = L->dst[j];
+    T v = g[j];
+    if ((mm >> j) & 1u) v += wall_term<T>(OPP(j), ux, uy, uz, r1);
+    if (d >= 0) Store<S>::st(g0 + d, v);
+  }
+  // outlet copies after the primary deliveries (they may replace one)
+  constexpr int kPops[kOutletPops] = {2, 8, 10, 12, 14};
+#pragma unroll
+  for (int e = 0; e < kOutletPops; ++e)
+#pragma unroll
+    for (int m = 0; m < kOutletCopies; ++m) {
+      const int d = L->extra[e * kOutletCopies + m];
+      if (d >= 0) Store<S>::st(g0 + d, g[kPops[e]]);
+    }
+}
+
+// Index of cell idx in the ascending listed-cell array of the domain.
+__device__ __forceinline__ long long listed_index(const DevDomain& D, long long idx) {
+  long long lo = 0, hi = D.nb - 1;
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (__ldg(D.bcell + mid) < idx) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Inflow velocity of layer z for the moving-wall term (zero when the cell has
 // no inflow link, so the table is not read).
 template <class S>
@@ -473,6 +359,23 @@ __device__ __forceinline__ void wall_velocity(const Node<S>& N, LinkWord lw, int
   using T = typename Store<S>::C;
   ux = uy = uz = T(0);
   if (!(lw & kLinkVel)) return;
+  if constexpr (sizeof(T) == 8) {
+    ux = T(N.uind[3 * z]);
+    uy = T(N.uind[3 * z + 1]);
+    uz = T(N.uind[3 * z + 2]);
+  } else {
+    const float4 u = N.uinf[z];
+    ux = T(u.x);
+    uy = T(u.y);
+    uz = T(u.z);
+  }
+}
+
+// Inflow velocity of layer z of a node, unconditionally.
+template <class S>
+__device__ __forceinline__ void inflow_velocity(const Node<S>& N, int z, typename Store<S>::C& ux,
+                                                typename Store<S>::C& uy, typename Store<S>::C& uz) {
+  using T = typename Store<S>::C;
   if constexpr (sizeof(T) == 8) {
     ux = T(N.uind[3 * z]);
     uy = T(N.uind[3 * z + 1]);

@@ -78,18 +78,6 @@ __device__ __forceinline__ void cell_even(const StepParams& P, const DevDomain& 
   if (lw & kLinkOutlet) save_outlet<S>(D, N, y, z, g);
 }
 
-// Odd time level, listed boundary cell: the general per-link rules.
-template <class S, bool CG>
-__device__ void cell_odd_general(const StepParams& P, const DevDomain& D, const Node<S>& N,
-                                 LinkWord lw, int x, int y, int z, long long idx,
-                                 typename Store<S>::C r, typename Store<S>::C r1) {
-  using T = typename Store<S>::C;
-  T g[kQ];
-  load_odd_general<S, CG>(D, N, lw, x, y, z, idx, g, r);
-  collide_p<T, true>(P, g);
-  push_general<S>(D, N, N.g, lw, x, y, z, idx, g, r1);
-}
-
 // ------------------------------------------------------------ step driver
 // A tile is a block_x * block_y patch of one x-y plane range, slab_z deep,
 // of one node of one domain.  Decoded once per block (32-bit arithmetic; tile
@@ -251,20 +239,30 @@ __device__ __forceinline__ int decode_bitem(const StepParams& P, long long item,
   return d;
 }
 
-// Boundary cells of the odd level: one thread per (node, listed cell).
+// Listed cells of the odd level: one thread per (node, listed cell), from
+// the compiled link rules (one round of table loads, one of population
+// loads).
 template <class S, bool CG>
 __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long item, float r,
                                                   float r1) {
   using T = typename Store<S>::C;
   if (item >= P.total_bitems) return;
-  int node;
-  long long idx;
-  const DevDomain& D = P.dom[decode_bitem(P, item, &node, &idx)];
-  const int x = (int)(idx % D.nx);
-  const int y = (int)((idx / D.nx) % D.ny);
-  const int z = (int)(idx / ((long long)D.nx * D.ny));
-  const LinkWord lw = __ldg(D.link + idx);
-  cell_odd_general<S, CG>(P, D, node_view<S>(D, node), lw, x, y, z, idx, T(r), T(r1));
+  int d = 0;
+  for (int k = 1; k < P.n_domains; ++k)
+    if (item >= P.dom[k].bitem_begin) d = k;
+  const DevDomain& D = P.dom[d];
+  const long long k = item - D.bitem_begin;
+  const int node = (int)(k / D.nb);
+  const long long li = k % D.nb;
+  const ListedLinks* L = D.ltab + li;
+  const int z = (int)(__ldg(D.bcell + li) / ((long long)D.nx * D.ny));
+  const Node<S> N = node_view<S>(D, node);
+  T ux = T(0), uy = T(0), uz = T(0);
+  if (L->pull_move | L->push_move) inflow_velocity<S>(N, z, ux, uy, uz);
+  T g[kQ];
+  listed_pull<S, CG>(L, N.g, N.bout, ux, uy, uz, T(r), g);
+  collide_p<T, true>(P, g);
+  listed_push<S>(L, N.g, ux, uy, uz, T(r1), g);
 }
 
 // Listed cells of the even level (local update; outlet cells save their
@@ -746,10 +744,8 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   const long long item = (b - D.tiles_per_node) * (long long)(P.bx * P.by) + threadIdx.y * P.bx + threadIdx.x;
   if (item >= D.nb) return;
   const long long idx = __ldg(D.bcell + item);
-  const int x = (int)(idx % D.nx);
-  const int y = (int)((idx / D.nx) % D.ny);
   const int z = (int)(idx / ((long long)D.nx * D.ny));
-  const LinkWord lw = __ldg(D.link + idx);
+  const ListedLinks* L = D.ltab + item;
   Node<double> N;
   N.g = dst;
   N.bout = nullptr;
@@ -761,7 +757,9 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
 #pragma unroll
   for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
   collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
-  push_general<double>(D, N, dst, lw, x, y, z, idx, g, r1);
+  double ux = 0.0, uy = 0.0, uz = 0.0;
+  if (L->push_move) inflow_velocity<double>(N, z, ux, uy, uz);
+  listed_push<double>(L, dst, ux, uy, uz, r1, g);
 }
 
 // ------------------------------------------------------------ initialisation
@@ -801,7 +799,16 @@ __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain
 #pragma unroll
       for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(N.g + (long long)i * D.pitch + idx);
     } else {
-      load_odd_general<S, false>(D, N, lw, x, y, z, idx, g, T(ramp_at(P, n)));
+      const T r = T(ramp_at(P, n));
+      T ux, uy, uz;
+      if (lw & kLinkSlow) {
+        const ListedLinks* L = D.ltab + listed_index(D, idx);
+        inflow_velocity<S>(N, z, ux, uy, uz);
+        listed_pull<S, false>(L, N.g, N.bout, ux, uy, uz, r, g);
+      } else {
+        wall_velocity<S>(N, lw, z, ux, uy, uz);
+        fast_pull<S, false>(N.g + idx, lw, (int)D.pitch, D.nx, D.nx * D.ny, ux, uy, uz, r, g);
+      }
     }
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] += W<T>(i);

@@ -53,6 +53,24 @@ constexpr uint8_t kClsMoveSpec = 4;  // some link is a moving wall or specular
 constexpr unsigned kErrDiverged = 1u;
 constexpr unsigned kErrTimeout = 2u;
 
+// Listed cells (outlet plane, free-slip x/y faces, periodic wraps) carry their
+// link rules compiled into offsets on the host, so the odd AA level updates
+// them with two rounds of independent loads.  Offsets are element offsets
+// from the node's population base (slot * pitch + cell) or, for outflow
+// pulls, from the node's outflow plane ((z * ny + y) * 5 + k).
+constexpr int kOutletPops = 5;                         // f*_j with c_jx = -1
+constexpr int kOutletCopies = 4;                       // extra deliveries each
+struct alignas(16) ListedLinks {
+  int32_t src[kQ];                                     // pull source of link i
+  int32_t dst[kQ];                                     // delivery of f*_j, -1: leaves
+  int32_t extra[kOutletPops * kOutletCopies];          // outlet copies of f*_{2,8,10,12,14}, -1: none
+  uint32_t bout_mask;                                  // bit i: src[i] is in the outflow plane
+  uint32_t pull_move;                                  // bit i: pull of link i adds 6 w_i (c_i.u) r
+  uint32_t push_move;                                  // bit j: delivery of f*_j adds the term of opp(j)
+  uint32_t pad[3];
+};
+static_assert(sizeof(ListedLinks) == 256, "ListedLinks is 256 bytes");
+
 // Per-domain view handed to the kernels (plain pointers into the workspace).
 struct DevDomain {
   int nx, ny, nz, nodes;
@@ -67,7 +85,8 @@ struct DevDomain {
   void* g;                  // [nodes][19][pitch] storage (AA) or FP64 array A
   void* g2;                 // FP64 plain: array B, else null
   float* bout;              // [nodes][nz*ny][5] outflow plane (AA only)
-  const int32_t* bcell;     // [nb] fluid cells with a boundary link or on the outlet
+  const int32_t* bcell;     // [nb] fluid cells with a boundary link or on the outlet (ascending)
+  const ListedLinks* ltab;  // [nb] their compiled link rules
   long long nb;
   long long tiles_x, tiles_y, tiles_z, tiles_per_node;
   long long tile_begin;     // first global tile of this domain
@@ -115,6 +134,8 @@ int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_
 void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<LinkWord>& link);
 void hn_boundary_cells(const std::vector<LinkWord>& link, std::vector<int32_t>& cells);
 void hn_cell_classes(const std::vector<LinkWord>& link, std::vector<uint8_t>& cls);
+void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::vector<LinkWord>& link,
+                     const std::vector<int32_t>& cells, long long pitch, std::vector<ListedLinks>& tab);
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
                double* uin /*[nz][3]*/);
 int hn_gpc_size(int d, int degree);
