@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
     fast_push<float>(dst + c, lw, (int)pc, D.nx, D.nx * D.ny, ux, uy, uz, r1, g);
     return;
   }
-  const ListedLinks* L = D.ltab + listed_index(D, c);
+  const ListedRef L = listed_ref(D, listed_index(D, c));
   float ux = 0.f, uy = 0.f, uz = 0.f;
-  if (L->push_move) inflow_velocity<float>(N, z, ux, uy, uz);
+  if (L.word(kWordPushMove)) inflow_velocity<float>(N, z, ux, uy, uz);
   listed_push<float>(L, dst, ux, uy, uz, r1, g);
 }
 

@@ -593,6 +593,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   std::vector<std::vector<int32_t>> bcells(c.n_domains);
   std::vector<std::vector<uint8_t>> classes(c.n_domains);
   std::vector<std::vector<ListedLinks>> ltabs(c.n_domains);
+  std::vector<std::vector<int32_t>> ltab_words(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
   std::vector<float> rampf(c.ramp_steps + 1);
@@ -665,7 +666,8 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     V.link = (const LinkWord*)(h->ws + M.link);
     V.cls = (const uint8_t*)(h->ws + M.cls);
     V.bcell = (const int32_t*)(h->ws + M.bcell);
-    V.ltab = (const ListedLinks*)(h->ws + M.ltab);
+    V.ltab = (const int32_t*)(h->ws + M.ltab);
+    V.lstride = M.nb_max;
     V.nb = (long long)bcells[d].size();
     V.uin_f = (const float4*)(h->ws + M.uin_f);
     V.uin_d = (const double*)(h->ws + M.uin_d);
@@ -700,8 +702,16 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     if (e == cudaSuccess) e = up(M.cls, classes[d].data(), classes[d].size());
     if (e == cudaSuccess && !bcells[d].empty())
       e = up(M.bcell, bcells[d].data(), sizeof(int32_t) * bcells[d].size());
-    if (e == cudaSuccess && !ltabs[d].empty())
-      e = up(M.ltab, ltabs[d].data(), sizeof(ListedLinks) * ltabs[d].size());
+    if (e == cudaSuccess && !ltabs[d].empty()) {
+      // transpose the records: word w of cell k at [w * nb_max + k]
+      const size_t nbm = (size_t)M.nb_max, n = ltabs[d].size();
+      ltab_words[d].assign(nbm * kListedWords, -1);
+      for (size_t k = 0; k < n; ++k) {
+        const int32_t* rec = reinterpret_cast<const int32_t*>(&ltabs[d][k]);
+        for (int w = 0; w < kListedWords; ++w) ltab_words[d][(size_t)w * nbm + k] = rec[w];
+      }
+      e = up(M.ltab, ltab_words[d].data(), sizeof(int32_t) * ltab_words[d].size());
+    }
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
     if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
     if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());

@@ -296,18 +296,31 @@ __device__ __forceinline__ void fast_push(S* base, LinkWord lw, int pc, int sy, 
 }
 
 // ------------------------------------------------------------ listed cells
+// Word w of the compiled rules of listed cell li (transposed records).
+struct ListedRef {
+  const int32_t* p;
+  long long stride;
+  __device__ __forceinline__ int word(int w) const { return __ldg(p + w * stride); }
+};
+__device__ __forceinline__ ListedRef listed_ref(const DevDomain& D, long long li) {
+  ListedRef L;
+  L.p = D.ltab + li;
+  L.stride = D.lstride;
+  return L;
+}
+
 // Pull of the odd AA level for a listed cell from its compiled rules: g0 is
 // the node's population base, bo its outflow plane (float).
 template <class S, bool CG>
-__device__ __forceinline__ void listed_pull(const ListedLinks* L, const S* g0, const float* bo,
+__device__ __forceinline__ void listed_pull(const ListedRef& L, const S* g0, const float* bo,
                                             typename Store<S>::C ux, typename Store<S>::C uy,
                                             typename Store<S>::C uz, typename Store<S>::C r,
                                             typename Store<S>::C g[kQ]) {
   using T = typename Store<S>::C;
-  const uint32_t bm = L->bout_mask, pm = L->pull_move;
+  const uint32_t bm = (uint32_t)L.word(kWordBoutMask), pm = (uint32_t)L.word(kWordPullMove);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const int s = L->src[i];
+    const int s = L.word(kWordSrc + i);
     T v = ((bm >> i) & 1u) ? T(__ldcg(bo + s)) : LD<S, CG>(g0 + s);
     if ((pm >> i) & 1u) v += wall_term<T>(i, ux, uy, uz, r);
     g[i] = v;
@@ -317,14 +330,14 @@ __device__ __forceinline__ void listed_pull(const ListedLinks* L, const S* g0, c
 // Deliveries of a listed cell's post-collision populations into the node's
 // array g0 (AA in place, or the destination array of a two-array step).
 template <class S>
-__device__ __forceinline__ void listed_push(const ListedLinks* L, S* g0, typename Store<S>::C ux,
+__device__ __forceinline__ void listed_push(const ListedRef& L, S* g0, typename Store<S>::C ux,
                                             typename Store<S>::C uy, typename Store<S>::C uz,
                                             typename Store<S>::C r1, const typename Store<S>::C g[kQ]) {
   using T = typename Store<S>::C;
-  const uint32_t mm = L->push_move;
+  const uint32_t mm = (uint32_t)L.word(kWordPushMove);
 #pragma unroll
   for (int j = 0; j < kQ; ++j) {
-    const int d = L->dst[j];
+    const int d = L.word(kWordDst + j);
     T v = g[j];
     if ((mm >> j) & 1u) v += wall_term<T>(OPP(j), ux, uy, uz, r1);
     if (d >= 0) Store<S>::st(g0 + d, v);
@@ -335,7 +348,7 @@ __device__ __forceinline__ void listed_push(const ListedLinks* L, S* g0, typenam
   for (int e = 0; e < kOutletPops; ++e)
 #pragma unroll
     for (int m = 0; m < kOutletCopies; ++m) {
-      const int d = L->extra[e * kOutletCopies + m];
+      const int d = L.word(kWordExtra + e * kOutletCopies + m);
       if (d >= 0) Store<S>::st(g0 + d, g[kPops[e]]);
     }
 }

@@ -254,11 +254,11 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   const long long k = item - D.bitem_begin;
   const int node = (int)(k / D.nb);
   const long long li = k % D.nb;
-  const ListedLinks* L = D.ltab + li;
+  const ListedRef L = listed_ref(D, li);
   const int z = (int)(__ldg(D.bcell + li) / ((long long)D.nx * D.ny));
   const Node<S> N = node_view<S>(D, node);
   T ux = T(0), uy = T(0), uz = T(0);
-  if (L->pull_move | L->push_move) inflow_velocity<S>(N, z, ux, uy, uz);
+  if (L.word(kWordPullMove) | L.word(kWordPushMove)) inflow_velocity<S>(N, z, ux, uy, uz);
   T g[kQ];
   listed_pull<S, CG>(L, N.g, N.bout, ux, uy, uz, T(r), g);
   collide_p<T, true>(P, g);
@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   if (item >= D.nb) return;
   const long long idx = __ldg(D.bcell + item);
   const int z = (int)(idx / ((long long)D.nx * D.ny));
-  const ListedLinks* L = D.ltab + item;
+  const ListedRef L = listed_ref(D, item);
   Node<double> N;
   N.g = dst;
   N.bout = nullptr;
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
   collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
   double ux = 0.0, uy = 0.0, uz = 0.0;
-  if (L->push_move) inflow_velocity<double>(N, z, ux, uy, uz);
+  if (L.word(kWordPushMove)) inflow_velocity<double>(N, z, ux, uy, uz);
   listed_push<double>(L, dst, ux, uy, uz, r1, g);
 }
 
@@ -802,7 +802,7 @@ __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain
       const T r = T(ramp_at(P, n));
       T ux, uy, uz;
       if (lw & kLinkSlow) {
-        const ListedLinks* L = D.ltab + listed_index(D, idx);
+        const ListedRef L = listed_ref(D, listed_index(D, idx));
         inflow_velocity<S>(N, z, ux, uy, uz);
         listed_pull<S, false>(L, N.g, N.bout, ux, uy, uz, r, g);
       } else {

@@ -70,6 +70,13 @@ struct alignas(16) ListedLinks {
   uint32_t pad[3];
 };
 static_assert(sizeof(ListedLinks) == 256, "ListedLinks is 256 bytes");
+// On the device the records are stored transposed, word w of listed cell li at
+// ltab[w * lstride + li], so a warp over consecutive listed cells reads each
+// word coalesced.
+constexpr int kListedWords = (int)(sizeof(ListedLinks) / 4);
+constexpr int kWordSrc = 0, kWordDst = kQ, kWordExtra = 2 * kQ;
+constexpr int kWordBoutMask = 2 * kQ + kOutletPops * kOutletCopies;
+constexpr int kWordPullMove = kWordBoutMask + 1, kWordPushMove = kWordBoutMask + 2;
 
 // Per-domain view handed to the kernels (plain pointers into the workspace).
 struct DevDomain {
@@ -86,7 +93,8 @@ struct DevDomain {
   void* g2;                 // FP64 plain: array B, else null
   float* bout;              // [nodes][nz*ny][5] outflow plane (AA only)
   const int32_t* bcell;     // [nb] fluid cells with a boundary link or on the outlet (ascending)
-  const ListedLinks* ltab;  // [nb] their compiled link rules
+  const int32_t* ltab;      // [kListedWords][lstride] their compiled link rules (transposed records)
+  long long lstride;
   long long nb;
   long long tiles_x, tiles_y, tiles_z, tiles_per_node;
   long long tile_begin;     // first global tile of this domain
