@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lbm-steps", type=int, default=500, help="time steps per benchmark step")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--workload", default="urban_les_256x128x64_cc3",
+                    choices=["urban_les_256x128x64_cc3", "urban_batched_3domains", "urban_large_512x256x128_cc4"],
+                    help="the benchmark workload; the other two are measured without the extra legs")
     ap.add_argument("--nodes", type=int, default=0,
                     help="profiling case: keep only this many Smolyak levels' worth of nodes (0 = all)")
     ap.add_argument("--skip", default="",
@@ -148,7 +151,7 @@ class Clocks:
 
 def workload_for(args):
     from paper_2508_18202_gb300 import workloads as W
-    wl = dict(W.URBAN_LES)
+    wl = dict({w["name"]: w for w in W.ALL}[args.workload])
     wl["precision"] = {"fp32": W.FP32_SHIFT, "bf16": W.BF16_STORE, "fp16": W.FP16_STORE}[args.precision]
     if args.nodes:
         # profiling case: a coarser sparse grid (fewer nodes), same domain
@@ -232,6 +235,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     skip = set(s for s in args.skip.split(",") if s)
+    if args.workload != "urban_les_256x128x64_cc3":
+        skip |= {"plain", "storage", "e2e", "adjoint", "cpu"}  # legs defined on the default workload
 
     def barrier():
         if world > 1:
@@ -243,11 +248,16 @@ def main():
     cfg = S.make_config(wl)
     ens = S.Ensemble(cfg)
     h = ens.h
-    cells = D["nx"] * D["ny"] * D["nz"]
-    nodes = ens.n_nodes[0]
+    ndom = len(wl["domains"])
+    cells_d = [d["nx"] * d["ny"] * d["nz"] for d in wl["domains"]]
+    nodes_d = [ens.n_nodes[d] for d in range(ndom)]
+    fluid_d = [int((S.sc_lbm_geometry(cfg, d) == 0).sum()) for d in range(ndom)]
+    # lattice updates and fluid updates of all (domain, node) pairs per time step
+    lup_step = sum(c * n for c, n in zip(cells_d, nodes_d))
+    flup_step = sum(f * n for f, n in zip(fluid_d, nodes_d))
+    cells, nodes, fluid = cells_d[0], nodes_d[0], fluid_d[0]
     flags = S.sc_lbm_geometry(cfg, 0)
-    fluid = int((flags == 0).sum())
-    columns = S.sc_lbm_probe_columns(cfg, 0, wl.get("n_columns", 4))
+    columns = [S.sc_lbm_probe_columns(cfg, d, wl.get("n_columns", 4)) for d in range(ndom)]
     if args.tuning:
         bx, by, bz, order, mode, gsteps, variant = (int(v) for v in args.tuning.split(","))
         S.sc_lbm_set_tuning(h, bx, by, bz, order, mode, gsteps, variant)
@@ -264,7 +274,7 @@ def main():
         S.sc_lbm_step(h, L)
         if ev is not None:
             ev[1].record(ens.stream)
-        return ens.moments(0, probes=columns, gpc=P >= 0)
+        return [ens.moments(d, probes=columns[d], gpc=P >= 0) for d in range(ndom)]
 
     for _ in range(args.warmup):
         bench_step()
@@ -290,17 +300,17 @@ def main():
         t = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
-    lups = float(cells) * nodes * L * args.steps * world
+    lups = float(lup_step) * L * args.steps * world
     glups = lups / (ms_total * 1e-3) / 1e9
     launch_ms = ms_kernel / (args.steps * L)
-    alg_bytes = BYTES_PER_LUP[wl["precision"]] * fluid * nodes
+    alg_bytes = BYTES_PER_LUP[wl["precision"]] * flup_step
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     khash = kernel_source_hash()
     traffic = recorded_traffic(khash, wl["name"] + ("" if not args.nodes else "_L%d" % args.nodes))
     extra = {}
     # fields sanity (not timed)
-    out = ens.moments(0, probes=columns, gpc=P >= 0)
+    out = ens.moments(0, probes=columns[0], gpc=P >= 0)
     mean = out["mean"]
     extra["mean_u_fluid"] = float(mean[torch.from_numpy(flags == 0).cuda()].mean().item())
     ens.close()
@@ -362,7 +372,7 @@ def main():
         flags_pinned = torch.from_numpy(flags).pin_memory()
         mean_h = torch.empty(cells, dtype=torch.float64).pin_memory()
         std_h = torch.empty(cells, dtype=torch.float64).pin_memory()
-        prof_h = torch.empty(len(columns) * D["nz"] * 4, dtype=torch.float64).pin_memory()
+        prof_h = torch.empty(len(columns[0]) * D["nz"] * 4, dtype=torch.float64).pin_memory()
         fh = (S.C.c_void_p * 1)(flags_pinned.data_ptr())
         n_e2e = max(2, min(args.steps, 3))
         torch.cuda.synchronize()
@@ -375,15 +385,19 @@ def main():
                 tuning["block_x"], tuning["block_y"], tuning["slab_z"], tuning["tile_order"],
                 tuning["exec_mode"], tuning["graph_steps"])), handle=hh)
             S.sc_lbm_step(hh, L)
-            S.sc_lbm_moments(hh, 0, mean_h, std_h, columns, prof_h, None, None, out_host=True)
+            S.sc_lbm_moments(hh, 0, mean_h, std_h, columns[0], prof_h, None, None, out_host=True)
             S.sc_lbm_destroy(hh)
         dt = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        h2d = cells * (1 + 4) + nodes * D["nz"] * (16 + 24) + nodes * 8 * (1 + 6) + 2 * 8 * (wl["ramp_steps"] + 1)
-        d2h = 2 * 8 * cells + len(columns) * D["nz"] * 4 * 8
+        # geometry flags, link words, class bytes; listed (outlet) cells with their
+        # 256-byte rule records; inflow tables; node weights x gPC basis; ramp tables
+        n_listed = int((flags.reshape(D["nz"], D["ny"], D["nx"])[:, :, -1] == 0).sum())
+        h2d = (cells * (1 + 8 + 1) + n_listed * (4 + 256) + nodes * D["nz"] * (16 + 24)
+               + nodes * 8 * (1 + 6) + 2 * 8 * (wl["ramp_steps"] + 1))
+        d2h = 2 * 8 * cells + len(columns[0]) * D["nz"] * 4 * 8
         e2e = {"value": round(float(cells) * nodes * L * n_e2e * world / dt / 1e9, 4), "unit": "GLUPS",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "note": "per step: sc_lbm_init from pinned host geometry, %d time steps, moments to pinned host" % L}
@@ -441,9 +455,13 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[wl["precision"]], "data": "synthetic",
-            "config": {"workload": wl["name"], "cells": cells, "fluid_cells": fluid, "nodes": nodes,
+            "config": {"workload": wl["name"],
+                       "cells": cells if ndom == 1 else cells_d,
+                       "fluid_cells": fluid if ndom == 1 else fluid_d,
+                       "nodes": nodes if ndom == 1 else nodes_d,
                        "time_steps_per_step": L, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (%.2f GB of populations)" % (cells * nodes * 19 * 4 / 1e9),
+                       "l2": "inputs larger than L2 (%.2f GB of populations)"
+                             % (lup_step * 19 * BYTES_PER_LUP[wl["precision"]] / 152 * 4 / 1e9),
                        "tuning": tuning},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -451,7 +469,7 @@ def main():
                          "kernel": "one time step: aa_even + (aa_odd_bulk + aa_odd_boundary), averaged per level",
                          "bytes_per_fluid_lup": BYTES_PER_LUP[wl["precision"]],
                          "avg_launch_ms": round(launch_ms, 5), "kernel_hash": khash},
-            "fluid_glups": round(glups * fluid / cells, 4),
+            "fluid_glups": round(glups * flup_step / lup_step, 4),
             "plain_fp64": plain, "storage": storage or None,
             "adjoint": adjoint,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(k1 - k0),

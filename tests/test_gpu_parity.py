@@ -251,6 +251,33 @@ def test_full_size_single_step_from_exported_state(O, cuda):
     ens.close()
 
 
+@pytest.mark.parametrize("name", ["urban_batched_3domains", "urban_large_512x256x128_cc4"])
+def test_other_full_size_workloads_single_step(O, cuda, name):
+    """The batched ensemble (128x64x48 / 192x96x64 / 320x160x64 with 13 / 29 /
+    5 nodes in one launch) and the large one (512x256x128, 69 nodes, 89.7 GB):
+    one GPU step from the exported state of a sampled node of every domain
+    equals one oracle step, at both parities during the ramp."""
+    wl = {w["name"]: w for w in W.ALL}[name]
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(300)
+    doms = range(len(wl["domains"]))
+    oracle = [oracle_domain(O, wl, d) for d in doms]
+    nodes = [oracle_nodes(O, wl, d) for d in doms]
+    for n in (300, 301):
+        pick = [(n + 7 * d) % len(nodes[d][1]) for d in doms]
+        f0 = [gpu_state(ens, d, pick[d]) for d in doms]
+        ens.step(1)
+        for d in doms:
+            p, flags = oracle[d]
+            fl = fluid_mask(flags)
+            f1 = gpu_state(ens, d, pick[d])
+            O.run(p, flags, oracle_uin(O, wl, d, nodes[d][0][pick[d]]), f0[d], n, 1)
+            assert np.max(np.abs(f1[:, fl] - f0[d][:, fl])) < 2e-6, (name, d, n)
+            del f1
+        del f0
+    ens.close()
+
+
 def test_ensemble_moments_match_exported_fields(O, cuda):
     """Property at full size: the on-device FP64 reduction equals the oracle's
     two-pass moments of the per-node |u| fields the GPU exports."""
