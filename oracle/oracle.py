@@ -23,10 +23,13 @@ Z95 = 1.959963984540054
 class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("bc", C.c_int * 6), ("tau0", C.c_double), ("csmag", C.c_double),
-                ("ramp_steps", C.c_int), ("force", C.c_double * 3)]
+                ("ramp_steps", C.c_int), ("force", C.c_double * 3), ("collision", C.c_int)]
 
 
-def params(nx, ny, nz, bc, tau0, csmag=0.0, ramp_steps=0, force=(0.0, 0.0, 0.0)):
+BGK, RR = 0, 1  # collision: BGK, or recursive regularized with the third-order equilibrium
+
+
+def params(nx, ny, nz, bc, tau0, csmag=0.0, ramp_steps=0, force=(0.0, 0.0, 0.0), collision=BGK):
     p = Params()
     p.nx, p.ny, p.nz = nx, ny, nz
     for k in range(6):
@@ -34,6 +37,7 @@ def params(nx, ny, nz, bc, tau0, csmag=0.0, ramp_steps=0, force=(0.0, 0.0, 0.0))
     p.tau0, p.csmag, p.ramp_steps = float(tau0), float(csmag), int(ramp_steps)
     for a in range(3):
         p.force[a] = float(force[a])
+    p.collision = int(collision)
     return p
 
 
@@ -52,6 +56,7 @@ def lib():
         pp = C.POINTER(Params)
         L.oc_lattice.argtypes = [ip, ip, ip, C.POINTER(C.c_double), ip]
         L.oc_equilibrium.argtypes = [C.c_double, dp, dp]
+        L.oc_equilibrium3.argtypes = [C.c_double, dp, dp]
         L.oc_collide_cell.argtypes = [pp, dp, dp, C.POINTER(C.c_double)]
         L.oc_ramp.argtypes = [C.c_int, C.c_longlong]
         L.oc_ramp.restype = C.c_double
@@ -102,6 +107,13 @@ def lattice():
 def equilibrium(rho, u):
     feq = np.zeros(19)
     lib().oc_equilibrium(float(rho), np.ascontiguousarray(u, np.float64), feq)
+    return feq
+
+
+def equilibrium3(rho, u):
+    """Third-order D3Q19 equilibrium of the recursive regularized model."""
+    feq = np.zeros(19)
+    lib().oc_equilibrium3(float(rho), np.ascontiguousarray(u, np.float64), feq)
     return feq
 
 

@@ -11,9 +11,12 @@
  * What it restates, in the paper's order and notation:
  *   - D3Q19 velocity set and c_s^2 = 1/3 (Sec. 2.2, Fig. 1); the weights are
  *     not printed in the paper and are the standard 1/3, 1/18, 1/36.
- *   - Lattice Boltzmann equation (Sec. 2.2, Eq. deterministicLBE) in BGK form:
- *     f_i(x + c_i, t + 1) = f_i^eq + (1 - 1/tau_eff) (f_i - f_i^eq), with the
- *     second-order Hermite equilibrium and rho, u from Sec. 2.2.
+ *   - Lattice Boltzmann equation (Sec. 2.2, Eq. deterministicLBE):
+ *     f_i(x + c_i, t + 1) = f_i^eq + (1 - 1/tau_eff) f_i^(1), in two forms:
+ *     BGK (f^(1) = f - f^eq, second-order Hermite equilibrium) and the
+ *     paper's recursive regularized form (third-order equilibrium on the
+ *     D3Q19-supported Hermite polynomials; f^(1) rebuilt from its second-order
+ *     Hermite coefficient and the third-order one obtained recursively).
  *   - Effective relaxation time and Smagorinsky-Lilly viscosity (Sec. 2.2,
  *     Eqs. tauEff and turbVisc), |S| evaluated from the local non-equilibrium
  *     stress (the paper does not say how S is evaluated).
@@ -149,6 +152,130 @@ void equilibrium(const T& rho, const T u[3], T feq[Q]) {
   }
 }
 
+// ---------------------------------------------------------------- Hermite basis
+// Hermite polynomials of the discrete velocity c_i (Sec. 2.2, with
+// c_s^2 = 1/3):
+//   H^(2)_ab  = c_a c_b - cs2 d_ab,
+//   H^(3)_abg = c_a c_b c_g - cs2 (c_a d_bg + c_b d_ag + c_g d_ab).
+// Of the third-order ones, D3Q19 carries only the six with two equal indices,
+// and only the combinations
+//   H_xxy + H_yzz, H_xzz + H_xyy, H_yyz + H_xxz,
+//   H_xxy - H_yzz, H_xzz - H_xyy, H_yyz - H_xxz
+// are mutually orthogonal under its weights (the "correct orthogonality for
+// D3Q19 only" of the paper's reference).  A third-order term of the model is
+// the lattice projection onto these six: w_i sum_k h_k(c_i) A_k / N_k with
+// A_k the matching combination of a^(3) and N_k = sum_i w_i h_k(c_i)^2, so
+// that the lattice moments sum_i h_k(c_i) f_i reproduce A_k exactly.
+const double CS2 = 1.0 / 3.0;
+
+double hermite2(int i, int a, int b) {
+  return (double)(comp(i, a) * comp(i, b)) - (a == b ? CS2 : 0.0);
+}
+
+double hermite3(int i, int a, int b, int g) {
+  double v = (double)(comp(i, a) * comp(i, b) * comp(i, g));
+  if (b == g) v -= CS2 * comp(i, a);
+  if (a == g) v -= CS2 * comp(i, b);
+  if (a == b) v -= CS2 * comp(i, g);
+  return v;
+}
+
+// The six supported combinations: k = 0..2 sums, 3..5 differences of the
+// index triples (x,x,y)/(y,z,z), (x,z,z)/(x,y,y), (y,y,z)/(x,x,z).
+const int TRIP[3][2][3] = {{{0, 0, 1}, {1, 2, 2}}, {{0, 2, 2}, {0, 1, 1}}, {{1, 1, 2}, {0, 0, 2}}};
+
+double hermite3_comb(int i, int k) {
+  const int (*t)[3] = TRIP[k % 3];
+  const double s = k < 3 ? 1.0 : -1.0;
+  return hermite3(i, t[0][0], t[0][1], t[0][2]) + s * hermite3(i, t[1][0], t[1][1], t[1][2]);
+}
+
+double hermite3_norm(int k) {
+  double n = 0.0;
+  for (int i = 0; i < Q; ++i) n += weight(i) * hermite3_comb(i, k) * hermite3_comb(i, k);
+  return n;
+}
+
+// The combination k of a symmetric third-order tensor a[3][3][3].
+template <class T>
+T comb3(const T a[3][3][3], int k) {
+  const int (*t)[3] = TRIP[k % 3];
+  const T s = T(k < 3 ? 1.0 : -1.0);
+  return a[t[0][0]][t[0][1]][t[0][2]] + s * a[t[1][0]][t[1][1]][t[1][2]];
+}
+
+// Third-order equilibrium (Sec. 2.2, the equilibrium expanded up to order
+// three): the second-order one plus the lattice projection of
+// a^(3)_eq = rho u_a u_b u_g.
+template <class T>
+void equilibrium3(const T& rho, const T u[3], T feq[Q]) {
+  equilibrium(rho, u, feq);
+  T a3[3][3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int g = 0; g < 3; ++g) a3[a][b][g] = rho * u[a] * u[b] * u[g];
+  for (int k = 0; k < 6; ++k) {
+    const T A = comb3(a3, k) / T(hermite3_norm(k));
+    for (int i = 0; i < Q; ++i) feq[i] += T(weight(i) * hermite3_comb(i, k)) * A;
+  }
+}
+
+// One recursive regularized collision (Sec. 2.2, Eq. deterministicLBE with
+// the regularized non-equilibrium):
+//   f^eq third order;
+//   a_1^(2)_ab = sum_i H^(2)_ab(c_i) (f_i - f^eq_i)      (Eq. hermiteCoeff, n = 2);
+//   a_1^(3)_abg = u_a a_1^(2)_bg + u_b a_1^(2)_ag + u_g a_1^(2)_ab  (recursive);
+//   f^(1)_i = w_i [H^(2)(c_i) : a_1^(2) / (2 cs4) + lattice projection of a_1^(3)];
+//   tau_eff from Pi^neq = a_1^(2) exactly as in the BGK form;
+//   f*_i = f^eq_i + (1 - 1/tau_eff) f^(1)_i.
+template <class T>
+void collide_rr(const oc_params* p, const T f[Q], T fpost[Q], double* tau_out) {
+  T rho(0.0), j[3] = {T(0.0), T(0.0), T(0.0)};
+  for (int i = 0; i < Q; ++i) {
+    rho += f[i];
+    j[0] += T((double)CX[i]) * f[i];
+    j[1] += T((double)CY[i]) * f[i];
+    j[2] += T((double)CZ[i]) * f[i];
+  }
+  T u[3];
+  for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+  T feq[Q];
+  equilibrium3(rho, u, feq);
+  T a2[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      a2[a][b] = T(0.0);
+      for (int i = 0; i < Q; ++i) a2[a][b] += T(hermite2(i, a, b)) * (f[i] - feq[i]);
+    }
+  T a3[3][3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int g = 0; g < 3; ++g) a3[a][b][g] = u[a] * a2[b][g] + u[b] * a2[a][g] + u[g] * a2[a][b];
+  T f1[Q];
+  for (int i = 0; i < Q; ++i) {
+    T s2(0.0);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) s2 += T(hermite2(i, a, b)) * a2[a][b];
+    f1[i] = T(weight(i)) * s2 / T(2.0 * CS2 * CS2);
+  }
+  for (int k = 0; k < 6; ++k) {
+    const T A = comb3(a3, k) / T(hermite3_norm(k));
+    for (int i = 0; i < Q; ++i) f1[i] += T(weight(i) * hermite3_comb(i, k)) * A;
+  }
+  T tau(p->tau0);
+  if (p->csmag != 0.0) {
+    T PiPi(0.0);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) PiPi += a2[a][b] * a2[a][b];
+    T Pin = sqrt(T(2.0) * PiPi + T(1e-30));
+    double c2 = p->csmag * p->csmag;
+    tau = T(0.5) * (T(p->tau0) + sqrt(T(p->tau0 * p->tau0) + T(18.0 * c2) * Pin / rho));
+  }
+  if (tau_out) *tau_out = value(tau);
+  const T keep = T(1.0) - T(1.0) / tau;
+  for (int i = 0; i < Q; ++i) fpost[i] = feq[i] + keep * f1[i];
+}
+
 // One BGK(+Smagorinsky) collision of one cell (Sec. 2.2):
 //   rho = sum f, u = sum c f / rho,
 //   Pi^neq = sum c c (f - f^eq),
@@ -160,6 +287,10 @@ void equilibrium(const T& rho, const T u[3], T feq[Q]) {
 // Guo's scheme (only the Poiseuille pin uses it).
 template <class T>
 void collide(const oc_params* p, const T f[Q], T fpost[Q], double* tau_out) {
+  if (p->collision == 1) {
+    collide_rr(p, f, fpost, tau_out);
+    return;
+  }
   T rho(0.0), j[3] = {T(0.0), T(0.0), T(0.0)};
   for (int i = 0; i < Q; ++i) {
     rho += f[i];
@@ -345,6 +476,8 @@ int check_params(const oc_params* p) {
   for (int k = 0; k < 6; ++k)
     if (p->bc[k] < 0 || p->bc[k] > 4) return -1;
   if (!(p->tau0 > 0.5)) return -1;
+  if (p->collision != 0 && p->collision != 1) return -1;
+  if (p->collision == 1 && (p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0)) return -1;
   return 0;
 }
 
@@ -456,8 +589,14 @@ int oc_equilibrium(double rho, const double* u, double* feq) {
   return 0;
 }
 
+int oc_equilibrium3(double rho, const double* u, double* feq) {
+  double uu[3] = {u[0], u[1], u[2]};
+  equilibrium3<double>(rho, uu, feq);
+  return 0;
+}
+
 int oc_collide_cell(const oc_params* p, const double* f, double* fpost, double* tau_eff) {
-  if (!p || !f || !fpost) return -1;
+  if (!p || !f || !fpost || check_params(p)) return -1;
   collide<double>(p, f, fpost, tau_eff);
   return 0;
 }
@@ -486,7 +625,8 @@ int oc_init_equilibrium(const oc_params* p, const uint8_t* flags, const double* 
     double r = 1.0;
     if (rho) r = rho[c];
     if (u) { uc[0] = u[c]; uc[1] = u[n + c]; uc[2] = u[2 * n + c]; }
-    equilibrium<double>(r, uc, fe);
+    if (p->collision == 1) equilibrium3<double>(r, uc, fe);
+    else equilibrium<double>(r, uc, fe);
     for (int i = 0; i < Q; ++i) f[(long long)i * n + c] = flags[c] ? 0.0 : fe[i];
   }
   return 0;

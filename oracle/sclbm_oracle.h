@@ -31,11 +31,15 @@ typedef struct {
   int ramp_steps;   /* T_r of the start-up ramp, 0 = impulsive           */
   double force[3];  /* body force (Guo); zero for the method, used only by
                        the Poiseuille pin                                 */
+  int collision;    /* 0: BGK, second-order equilibrium; 1: recursive
+                       regularized, third-order D3Q19 equilibrium         */
 } oc_params;
 
 int oc_lattice(int* cx, int* cy, int* cz, double* w, int* opp);
 int oc_equilibrium(double rho, const double* u, double* feq);
 int oc_collide_cell(const oc_params* p, const double* f, double* fpost, double* tau_eff);
+/* Third-order D3Q19 Hermite equilibrium of the recursive regularized model. */
+int oc_equilibrium3(double rho, const double* u, double* feq);
 double oc_ramp(int ramp_steps, long long m);
 
 int oc_init_equilibrium(const oc_params* p, const uint8_t* flags,
