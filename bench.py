@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--nodes", type=int, default=0,
                     help="profiling case: keep only this many Smolyak levels' worth of nodes (0 = all)")
     ap.add_argument("--skip", default="",
-                    help="comma list of extra legs to skip: plain,storage,cpu,e2e,tune,adjoint")
+                    help="comma list of extra legs to skip: plain,storage,rr,cpu,e2e,tune,adjoint")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shape block_x,block_y,slab_z,tile_order,exec_mode,graph_steps,variant "
                          "instead of the autotuner")
@@ -236,7 +236,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     skip = set(s for s in args.skip.split(",") if s)
     if args.workload != "urban_les_256x128x64_cc3":
-        skip |= {"plain", "storage", "e2e", "adjoint", "cpu"}  # legs defined on the default workload
+        skip |= {"plain", "storage", "rr", "e2e", "adjoint", "cpu"}  # legs defined on the default workload
 
     def barrier():
         if world > 1:
@@ -364,6 +364,30 @@ def main():
             del se
             torch.cuda.empty_cache()
 
+    # ---- the paper's collision (recursive regularized, third-order equilibrium)
+    regularized = None
+    if "rr" not in skip and rank == 0 and args.precision == "fp32":
+        rwl = dict(W.URBAN_LES_RR, precision=wl["precision"])
+        re_ = S.Ensemble(S.make_config(rwl))
+        S.sc_lbm_set_tuning(re_.h, **{k: tuning[k] for k in ("block_x", "block_y", "slab_z", "tile_order")},
+                            exec_mode=tuning["exec_mode"], graph_steps=tuning["graph_steps"],
+                            variant=tuning["variant"])
+        S.sc_lbm_step(re_.h, 4)
+        re_.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(re_.stream)
+        S.sc_lbm_step(re_.h, 400)
+        e1.record(re_.stream)
+        re_.stream.synchronize()
+        re_.sync()
+        rms = e0.elapsed_time(e1)
+        g = cells * nodes * 400 / (rms * 1e-3) / 1e9
+        regularized = {"value": round(g, 3), "unit": "GLUPS", "workload": rwl["name"],
+                       "hbm_frac": round(152 * fluid * nodes / (rms / 400 * 1e-3) / 1e9 / peak, 4)}
+        re_.close()
+        del re_
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if "e2e" not in skip:
@@ -470,7 +494,7 @@ def main():
                          "bytes_per_fluid_lup": BYTES_PER_LUP[wl["precision"]],
                          "avg_launch_ms": round(launch_ms, 5), "kernel_hash": khash},
             "fluid_glups": round(glups * flup_step / lup_step, 4),
-            "plain_fp64": plain, "storage": storage or None,
+            "plain_fp64": plain, "storage": storage or None, "regularized": regularized,
             "adjoint": adjoint,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(k1 - k0),
             "clocks": clk.summary(), "extra": extra,

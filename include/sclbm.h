@@ -53,6 +53,9 @@ extern "C" {
 #define SC_ERR_SCRATCH (-8)      /* request exceeds the fixed no-alloc scratch */
 
 /* ------------------------------------------------------------ enumerations */
+/* collision model */
+#define SC_COLL_BGK 0  /* BGK (+ Smagorinsky), second-order equilibrium       */
+#define SC_COLL_RR 1   /* recursive regularized, third-order equilibrium      */
 /* boundary kind per face (Sec. 2.2 boundary list; OUTFLOW added for channels) */
 #define SC_BC_VELOCITY 0     /* prescribed inflow velocity (moving-wall links) */
 #define SC_BC_OUTFLOW 1      /* zero-gradient outflow; only on face 1 (+x)     */
@@ -105,7 +108,14 @@ typedef struct {
  * h = z + 1/2 and H = H_ref (H_ref <= 0 selects the domain height nz); each
  * uncertain input k replaces xi, alpha or theta by the node coordinate.
  * ramp_steps: length of the start-up ramp of the inflow (0 = impulsive).
- * gpc_degree: total degree of the Legendre gPC projection, -1 for none.     */
+ * gpc_degree: total degree of the Legendre gPC projection, -1 for none.
+ * collision: SC_COLL_BGK (second-order equilibrium, f* = f - (f - f^eq) /
+ * tau_eff) or SC_COLL_RR, the paper's recursive regularized form (Sec. 2.2,
+ * Eqs. deterministicLBE and hermiteCoeff): third-order equilibrium on the six
+ * third-order Hermite combinations D3Q19 carries, non-equilibrium rebuilt from
+ * its second-order Hermite coefficient and the third-order one obtained by
+ * the recursion a3_abg = u_a a2_bg + u_b a2_ag + u_g a2_ab; tau_eff as for
+ * BGK.  Zero-initialised configs select BGK.                                */
 typedef struct {
   int n_domains;
   const sc_domain_desc* domains; /* host, read during calls only */
@@ -118,6 +128,7 @@ typedef struct {
   int ramp_steps;
   int precision;
   int gpc_degree;
+  int collision;
 } sc_lbm_config;
 
 /* Launch shape of the stream-collide kernels (chosen by sc_lbm_autotune or
@@ -286,7 +297,8 @@ int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_sna
  * bytes (256-byte aligned), caller-owned, overwritten; loss_out: host double;
  * grad_out: host double[2]; u_probe_out: host double [n_probes][3] or NULL.
  * Leaves the handle's populations untouched; synchronises.
- * SC_ERR_UNSUPPORTED when c_smag > 0 (the adjoint covers BGK).            */
+ * SC_ERR_UNSUPPORTED when c_smag > 0 or collision is not SC_COLL_BGK (the
+ * adjoint covers BGK).                                                      */
 int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int n_probes,
                    const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
                    double* loss_out, double* grad_out, double* u_probe_out);

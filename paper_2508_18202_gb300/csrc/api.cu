@@ -73,6 +73,7 @@ int validate(const sc_lbm_config* c, std::string& why) {
   if (c->precision < SC_P_FP64_PLAIN || c->precision > SC_P_FP16_STORE) { why = "bad precision"; return SC_ERR_ARG; }
   if (c->ramp_steps < 0 || c->ramp_steps > 10000000) { why = "bad ramp_steps"; return SC_ERR_ARG; }
   if (c->gpc_degree > 8) { why = "gpc_degree too large"; return SC_ERR_UNSUPPORTED; }
+  if (c->collision != SC_COLL_BGK && c->collision != SC_COLL_RR) { why = "bad collision"; return SC_ERR_ARG; }
   if (c->gpc_degree >= 0 && hn_gpc_size(c->n_inputs, c->gpc_degree) > kMaxGpcP) {
     why = "gPC basis larger than " + std::to_string(kMaxGpcP);
     return SC_ERR_UNSUPPORTED;
@@ -356,7 +357,8 @@ int run_launches(sc_lbm_t h, long long start, int n) {
     StepParams P = h->P;
     P.r_pull = ramp_f(h, lvl);
     P.r_push = ramp_f(h, lvl + 1);
-    int rc = launch_aa_step(P, h->cfg.precision, h->stream, parity);
+    int rc = h->cfg.collision == SC_COLL_RR ? rr::launch_aa_step(P, h->cfg.precision, h->stream, parity)
+                                            : launch_aa_step(P, h->cfg.precision, h->stream, parity);
     if (rc) return cuda_fail(h, (cudaError_t)rc, "aa_step launch");
     h->launches += parity && h->P.tma ? 2 : 1;  // TMA odd levels: bulk + boundary kernels
   }
@@ -390,7 +392,9 @@ int run_graph(sc_lbm_t h, int n) {
     StepParams P = h->P;
     P.r_pull = 1.0f;
     P.r_push = 1.0f;
-    for (int s = 0; s < G && !rc; ++s) rc = launch_aa_step(P, h->cfg.precision, h->stream, s & 1);
+    for (int s = 0; s < G && !rc; ++s)
+      rc = h->cfg.collision == SC_COLL_RR ? rr::launch_aa_step(P, h->cfg.precision, h->stream, s & 1)
+                                          : launch_aa_step(P, h->cfg.precision, h->stream, s & 1);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
       if (g) cudaGraphDestroy(g);
@@ -413,7 +417,8 @@ int run_graph(sc_lbm_t h, int n) {
 int run_persistent(sc_lbm_t h, int n) {
   if (!h->persist_grid) {
     int grid = 0;
-    int rc = aa_persistent_max_grid(h->P, h->cfg.precision, &grid);
+    int rc = h->cfg.collision == SC_COLL_RR ? rr::aa_persistent_max_grid(h->P, h->cfg.precision, &grid)
+                                            : aa_persistent_max_grid(h->P, h->cfg.precision, &grid);
     if (rc || grid < 1) return cuda_fail(h, (cudaError_t)(rc ? rc : cudaErrorInvalidConfiguration), "occupancy");
     h->persist_grid = (int)std::min<long long>(grid, h->P.total_tiles);
   }
@@ -426,7 +431,9 @@ int run_persistent(sc_lbm_t h, int n) {
     P.never_arrive = h->never_arrive;
     P.spin_limit = h->spin_limit;
     CK(cudaMemsetAsync(&h->hdr()->bar_count, 0, sizeof(unsigned int), h->stream));
-    int rc = launch_aa_persistent(P, h->cfg.precision, h->stream, h->persist_grid);
+    int rc = h->cfg.collision == SC_COLL_RR
+                 ? rr::launch_aa_persistent(P, h->cfg.precision, h->stream, h->persist_grid)
+                 : launch_aa_persistent(P, h->cfg.precision, h->stream, h->persist_grid);
     if (rc) return cuda_fail(h, (cudaError_t)rc, "persistent launch");
     ++h->launches;
     done += k;
@@ -441,7 +448,9 @@ int run_plain(sc_lbm_t h, int n) {
       P.plain_domain = d;
       P.plain_node = j;
       for (int s = 0; s < n; ++s) {
-        int rc = launch_plain_step(P, (unsigned long long)(h->steps + s), h->stream);
+        int rc = h->cfg.collision == SC_COLL_RR
+                     ? rr::launch_plain_step(P, (unsigned long long)(h->steps + s), h->stream)
+                     : launch_plain_step(P, (unsigned long long)(h->steps + s), h->stream);
         if (rc) return cuda_fail(h, (cudaError_t)rc, "plain_step launch");
         ++h->launches;
       }
@@ -1143,8 +1152,8 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
                    const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
                    double* loss_out, double* grad_out, double* u_probe_out) {
   if (!h || !probes || !u_target || !loss_out || !grad_out) return SC_ERR_ARG;
-  if (h->cfg.c_smag != 0.0)
-    return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers BGK (c_smag = 0)");
+  if (h->cfg.c_smag != 0.0 || h->cfg.collision != SC_COLL_BGK)
+    return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers BGK (c_smag = 0, SC_COLL_BGK)");
   AdjLayout L;
   int rc = adj_plan(h, domain, n_steps, n_snapshots, n_probes, L);
   if (rc) return fail(h, rc, "bad adjoint arguments");

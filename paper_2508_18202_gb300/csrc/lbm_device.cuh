@@ -186,12 +186,114 @@ __device__ __forceinline__ void collide(T g[kQ], T tau0, T smag18c2, bool smag_o
   }
 }
 
+// ------------------------------------------------------------ regularized collision
+// Component a of c_i, and the Hermite polynomials of c_i (c_s^2 = 1/3):
+//   H2_ab = c_a c_b - d_ab / 3,  H3_abg = c_a c_b c_g - (c_a d_bg + c_b d_ag + c_g d_ab) / 3.
+__host__ __device__ constexpr int CA(int i, int a) { return a == 0 ? CX(i) : (a == 1 ? CY(i) : CZ(i)); }
+__host__ __device__ constexpr double H3(int i, int a, int b, int g) {
+  return (double)(CA(i, a) * CA(i, b) * CA(i, g)) -
+         ((b == g ? CA(i, a) : 0) + (a == g ? CA(i, b) : 0) + (a == b ? CA(i, g) : 0)) / 3.0;
+}
+// The third-order combinations D3Q19 carries, k = 0..2 sums and 3..5
+// differences of (xxy, yzz), (xzz, xyy), (yyz, xxz), divided by their D3Q19
+// norms sum_i w_i h_k(c_i)^2 = 2/27 (sums) and 6/27 (differences).
+__host__ __device__ constexpr double H3K(int i, int k) {
+  return k == 0 ? (H3(i, 0, 0, 1) + H3(i, 1, 2, 2)) * 13.5
+       : k == 1 ? (H3(i, 0, 2, 2) + H3(i, 0, 1, 1)) * 13.5
+       : k == 2 ? (H3(i, 1, 1, 2) + H3(i, 0, 0, 2)) * 13.5
+       : k == 3 ? (H3(i, 0, 0, 1) - H3(i, 1, 2, 2)) * 4.5
+       : k == 4 ? (H3(i, 0, 2, 2) - H3(i, 0, 1, 1)) * 4.5
+                : (H3(i, 1, 1, 2) - H3(i, 0, 0, 2)) * 4.5;
+}
+
+// Recursive regularized collision with the third-order equilibrium (Sec. 2.2,
+// Eq. deterministicLBE, Eq. hermiteCoeff):
+//   f* = f^eq + (1 - 1/tau_eff) f^(1),
+//   f^eq_i  = w_i [rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u^2) + sum_k h_k(c_i) E_k / N_k],
+//   f^(1)_i = w_i [4.5 H2(c_i) : a2 + sum_k h_k(c_i) A_k / N_k],
+// with a2 = Pi^neq (the second-order Hermite coefficient of f - f^eq), E_k the
+// combinations of rho u_a u_b u_g and A_k those of the recursion
+// a3_abg = u_a a2_bg + u_b a2_ag + u_g a2_ab.  tau_eff as in collide.  SHIFT as
+// in collide (the rho part then carries rho - 1).
+template <class T, bool SHIFT>
+__device__ __forceinline__ void collide_rr(T g[kQ], T tau0, T smag18c2, bool smag_on) {
+  T m0 = T(0), jx = T(0), jy = T(0), jz = T(0);
+  T pxx = T(0), pyy = T(0), pzz = T(0), pxy = T(0), pxz = T(0), pyz = T(0);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    m0 += g[i];
+    if (CX(i)) jx += CX(i) > 0 ? g[i] : -g[i];
+    if (CY(i)) jy += CY(i) > 0 ? g[i] : -g[i];
+    if (CZ(i)) jz += CZ(i) > 0 ? g[i] : -g[i];
+    if (CX(i)) pxx += g[i];
+    if (CY(i)) pyy += g[i];
+    if (CZ(i)) pzz += g[i];
+    if (CX(i) * CY(i)) pxy += CX(i) * CY(i) > 0 ? g[i] : -g[i];
+    if (CX(i) * CZ(i)) pxz += CX(i) * CZ(i) > 0 ? g[i] : -g[i];
+    if (CY(i) * CZ(i)) pyz += CY(i) * CZ(i) > 0 ? g[i] : -g[i];
+  }
+  const T rho = SHIFT ? T(1) + m0 : m0;
+  const T inv = recip(rho);
+  const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const T usq = ux * ux + uy * uy + uz * uz;
+  const T third = m0 * T(1.0 / 3.0);
+  const T nxx = pxx - third - rho * ux * ux;
+  const T nyy = pyy - third - rho * uy * uy;
+  const T nzz = pzz - third - rho * uz * uz;
+  const T nxy = pxy - rho * ux * uy;
+  const T nxz = pxz - rho * ux * uz;
+  const T nyz = pyz - rho * uy * uz;
+  T tau = tau0;
+  if (smag_on) {
+    const T pipi = nxx * nxx + nyy * nyy + nzz * nzz + T(2) * (nxy * nxy + nxz * nxz + nyz * nyz);
+    const T pin = sqrt(T(2) * pipi + T(1e-30));
+    tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + smag18c2 * pin * inv));
+  }
+  const T keep = T(1) - recip(tau);
+  // third-order content after collision: E + keep * A per component
+  const T rx = rho * ux, ry = rho * uy, rz = rho * uz;
+  const T t_xxy = rx * ux * uy + keep * (T(2) * ux * nxy + uy * nxx);
+  const T t_yzz = ry * uz * uz + keep * (T(2) * uz * nyz + uy * nzz);
+  const T t_xzz = rx * uz * uz + keep * (T(2) * uz * nxz + ux * nzz);
+  const T t_xyy = rx * uy * uy + keep * (T(2) * uy * nxy + ux * nyy);
+  const T t_yyz = ry * uy * uz + keep * (T(2) * uy * nyz + uz * nyy);
+  const T t_xxz = rx * ux * uz + keep * (T(2) * ux * nxz + uz * nxx);
+  const T k3[6] = {t_xxy + t_yzz, t_xzz + t_xyy, t_yyz + t_xxz, t_xxy - t_yzz, t_xzz - t_xyy, t_yyz - t_xxz};
+  // second-order non-equilibrium, scaled by keep and 4.5 = 1 / (2 c_s^4)
+  const T kxx = T(4.5) * keep * nxx, kyy = T(4.5) * keep * nyy, kzz = T(4.5) * keep * nzz;
+  const T kxy = T(9) * keep * nxy, kxz = T(9) * keep * nxz, kyz = T(9) * keep * nyz;
+  const T base = m0;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const T cu = T(CX(i)) * ux + T(CY(i)) * uy + T(CZ(i)) * uz;
+    T v = base + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+    v += T(CX(i) * CX(i) - 1.0 / 3.0) * kxx + T(CY(i) * CY(i) - 1.0 / 3.0) * kyy +
+         T(CZ(i) * CZ(i) - 1.0 / 3.0) * kzz;
+    if (CX(i) * CY(i)) v += T(CX(i) * CY(i)) * kxy;
+    if (CX(i) * CZ(i)) v += T(CX(i) * CZ(i)) * kxz;
+    if (CY(i) * CZ(i)) v += T(CY(i) * CZ(i)) * kyz;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (H3K(i, k) != 0.0) v += T(H3K(i, k)) * k3[k];
+    g[i] = W<T>(i) * v;
+  }
+}
+
+// The collision of the compiled unit: BGK(+Smagorinsky), or the recursive
+// regularized form in the unit built with SCLBM_RR_UNIT.
 template <class T, bool SHIFT>
 __device__ __forceinline__ void collide_p(const StepParams& P, T g[kQ]) {
+#ifdef SCLBM_RR_UNIT
+  if constexpr (sizeof(T) == 8)
+    collide_rr<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
+  else
+    collide_rr<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+#else
   if constexpr (sizeof(T) == 8)
     collide<T, SHIFT>(g, T(P.tau0_d), T(P.smag18c2_d), P.csmag_on);
   else
     collide<T, SHIFT>(g, T(P.tau0), T(P.smag18c2), P.csmag_on);
+#endif
 }
 
 // ------------------------------------------------------------ boundary helpers

@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
       double g[kQ];
 #pragma unroll
       for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
-      collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
+      collide_p<double, false>(P, g);
       double ux, uy, uz;
       wall_velocity<double>(N, lw, z, ux, uy, uz);
       fast_push<double>(dst + idx, lw, (int)pc, (int)sy, (int)sz, ux, uy, uz, r1, g);
@@ -756,12 +756,13 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   double g[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
-  collide<double, false>(g, P.tau0_d, P.smag18c2_d, P.csmag_on);
+  collide_p<double, false>(P, g);
   double ux = 0.0, uy = 0.0, uz = 0.0;
   if (L.word(kWordPushMove)) inflow_velocity<double>(N, z, ux, uy, uz);
   listed_push<double>(L, dst, ux, uy, uz, r1, g);
 }
 
+#ifndef SCLBM_RR_UNIT
 // ------------------------------------------------------------ initialisation
 // Every slot of every row (padding included): g = 0 (shifted) or f = w.
 template <class S, bool SHIFT>
@@ -988,6 +989,8 @@ __global__ void check_kernel(const __grid_constant__ StepParams P, unsigned long
   }
 }
 
+#endif  // SCLBM_RR_UNIT
+
 int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
   if (g > 152LL * 64) g = 152LL * 64;
@@ -1040,6 +1043,12 @@ int tma_grid(int* grid) {
 }  // namespace
 
 // ======================================================================= launchers
+// The unit built with SCLBM_RR_UNIT (the recursive regularized collision)
+// provides the step launchers in namespace rr; the observables and the
+// initialisation do not depend on the collision and live in the BGK unit only.
+#ifdef SCLBM_RR_UNIT
+namespace rr {
+#endif
 int launch_aa_step(const StepParams& P, int precision, void* stream, int parity) {
   dim3 block(P.bx, P.by);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1115,6 +1124,9 @@ int launch_plain_step(const StepParams& P, unsigned long long n, void* stream) {
   return (int)cudaGetLastError();
 }
 
+#ifdef SCLBM_RR_UNIT
+}  // namespace rr
+#else
 int launch_init_equilibrium(const StepParams& P, int precision, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (int d = 0; d < P.n_domains; ++d) {
@@ -1176,5 +1188,7 @@ int launch_check(const StepParams& P, int precision, unsigned long long* d_count
     return (int)cudaGetLastError();
   });
 }
+
+#endif  // SCLBM_RR_UNIT
 
 }  // namespace sclbm

@@ -156,6 +156,14 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
 int launch_aa_persistent(const StepParams& P, int precision, void* stream, int grid);
 int launch_plain_step(const StepParams& P, unsigned long long n, void* stream);
 int aa_persistent_max_grid(const StepParams& P, int precision, int* grid);
+// The same step launchers with the recursive regularized collision
+// (lbm_kernels_rr.cu).
+namespace rr {
+int launch_aa_step(const StepParams& P, int precision, void* stream, int parity);
+int launch_aa_persistent(const StepParams& P, int precision, void* stream, int grid);
+int launch_plain_step(const StepParams& P, unsigned long long n, void* stream);
+int aa_persistent_max_grid(const StepParams& P, int precision, int* grid);
+}  // namespace rr
 int launch_init_equilibrium(const StepParams& P, int precision, void* stream);
 struct MomentArgs {
   int domain;

@@ -24,6 +24,7 @@ SC_IN_SPEED_REL, SC_IN_ALPHA, SC_IN_ANGLE_DEG = 0, 1, 2
 SC_Q_GL, SC_Q_CC_SMOLYAK = 0, 1
 SC_P_FP64_PLAIN, SC_P_FP32_SHIFT, SC_P_BF16_STORE, SC_P_FP16_STORE = 0, 1, 2, 3
 SC_EXEC_LAUNCH, SC_EXEC_GRAPH, SC_EXEC_PERSISTENT = 0, 1, 2
+SC_COLL_BGK, SC_COLL_RR = 0, 1
 
 _NAMES = {SC_ERR_ARG: "SC_ERR_ARG", SC_ERR_WORKSPACE: "SC_ERR_WORKSPACE", SC_ERR_CUDA: "SC_ERR_CUDA",
           SC_ERR_DIVERGED: "SC_ERR_DIVERGED", SC_ERR_TIMEOUT: "SC_ERR_TIMEOUT",
@@ -51,7 +52,7 @@ class sc_lbm_config(C.Structure):
                 ("alpha", C.c_double), ("angle_deg", C.c_double), ("H_ref", C.c_double),
                 ("n_inputs", C.c_int), ("inputs", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("quad_rule", C.c_int), ("ramp_steps", C.c_int),
-                ("precision", C.c_int), ("gpc_degree", C.c_int)]
+                ("precision", C.c_int), ("gpc_degree", C.c_int), ("collision", C.c_int)]
 
 
 class sc_lbm_tuning(C.Structure):
@@ -139,7 +140,7 @@ class Config:
     """Owns an sc_lbm_config and the arrays it points to."""
 
     def __init__(self, domains, tau0, c_smag, u_ref, alpha, inputs, lo, hi, quad_rule,
-                 precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1):
+                 precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1, collision=SC_COLL_BGK):
         self._doms = (sc_domain_desc * len(domains))()
         self._boxes = []
         for k, d in enumerate(domains):
@@ -167,6 +168,7 @@ class Config:
         for k in range(len(inputs)):
             c.inputs[k], c.lo[k], c.hi[k] = inputs[k], lo[k], hi[k]
         c.quad_rule, c.ramp_steps, c.precision, c.gpc_degree = quad_rule, ramp_steps, precision, gpc_degree
+        c.collision = collision
         self.c = c
         self.domains = [dict(d) for d in domains]
 
@@ -447,7 +449,7 @@ def make_config(workload, **over):
     return Config(w["domains"], w["tau0"], w["c_smag"], w["u_ref"], w["alpha"], w["inputs"], w["lo"],
                   w["hi"], w["quad_rule"], w["precision"], ramp_steps=w["ramp_steps"],
                   angle_deg=w.get("angle_deg", 0.0), H_ref=w.get("H_ref", 0.0),
-                  gpc_degree=w.get("gpc_degree", -1))
+                  gpc_degree=w.get("gpc_degree", -1), collision=w.get("collision", SC_COLL_BGK))
 
 
 # ------------------------------------------------------------------ assimilation

@@ -12,6 +12,7 @@ VEL, OUT, BB, FS, PER = 0, 1, 2, 3, 4
 SPEED, ALPHA, ANGLE = 0, 1, 2
 GL, CC_SMOLYAK = 0, 1
 FP64_PLAIN, FP32_SHIFT, BF16_STORE, FP16_STORE = 0, 1, 2, 3
+BGK, RR = 0, 1   # collision: BGK, or the recursive regularized form with the third-order equilibrium
 
 URBAN_BC = [VEL, OUT, VEL, VEL, BB, FS]     # inlet, outlet, wind on the sides, ground, sky
 CHANNEL_BC = [VEL, OUT, BB, BB, BB, BB]
@@ -83,7 +84,11 @@ URBAN_LARGE = dict(
     n_columns=4,
 )
 
-ALL = [CHANNEL_CUBE, URBAN_LES, URBAN_BATCHED, URBAN_ADJOINT, URBAN_LARGE]
+# The urban LES ensemble with the paper's collision: recursive regularized,
+# third-order equilibrium, Smagorinsky C_S = 0.25.
+URBAN_LES_RR = dict(URBAN_LES, name="urban_les_rr_256x128x64_cc3", collision=RR, c_smag=0.25)
+
+ALL = [CHANNEL_CUBE, URBAN_LES, URBAN_BATCHED, URBAN_ADJOINT, URBAN_LARGE, URBAN_LES_RR]
 
 
 def variant(workload, **over):

@@ -5,7 +5,8 @@ import numpy as np
 
 def oracle_domain(O, wl, d=0):
     D = wl["domains"][d]
-    p = O.params(D["nx"], D["ny"], D["nz"], D["bc"], wl["tau0"], wl["c_smag"], wl["ramp_steps"])
+    p = O.params(D["nx"], D["ny"], D["nz"], D["bc"], wl["tau0"], wl["c_smag"], wl["ramp_steps"],
+                 collision=wl.get("collision", 0))
     flags = O.geometry(D["nx"], D["ny"], D["nz"], D.get("seed", 0), D.get("n_buildings", 0),
                        *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"))
     return p, flags

@@ -76,6 +76,15 @@ def test_adjoint_unsupported_with_smagorinsky(cuda):
     ens.close()
 
 
+def test_adjoint_unsupported_with_regularized_collision(cuda):
+    wl = dict(small_case(), collision=W.RR)
+    ens = S.Ensemble(S.make_config(wl))
+    with pytest.raises(S.ScError) as ei:
+        S.Assimilation(ens, [[9, 5, 3]], [[0.0, 0.0, 0.0]], 10).loss_and_grad(0.05, 0.25)
+    assert ei.value.code == S.SC_ERR_UNSUPPORTED
+    ens.close()
+
+
 def _fp64_probe_velocity(wl, u_ref, alpha, steps, probes):
     cfg = S.make_config(dict(wl, precision=W.FP64_PLAIN, u_ref=u_ref, alpha=alpha))
     ens = S.Ensemble(cfg)

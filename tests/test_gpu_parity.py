@@ -39,12 +39,12 @@ BC_SETS = {
 
 
 def ragged(bc, precision=W.FP32_SHIFT, c_smag=0.14, tau0=0.56, ramp=8, nx=37, ny=19, nz=13,
-           angle=12.0, quad_level=3, boxes=RAGGED_BOXES):
+           angle=12.0, quad_level=3, boxes=RAGGED_BOXES, collision=W.BGK):
     return dict(
         name="ragged", domains=[dict(nx=nx, ny=ny, nz=nz, boxes=boxes, bc=bc, quad_level=quad_level)],
         tau0=tau0, c_smag=c_smag, u_ref=0.05, alpha=0.25, angle_deg=angle, H_ref=0.0,
         inputs=[W.SPEED], lo=[-0.1], hi=[0.1], quad_rule=W.GL, ramp_steps=ramp,
-        precision=precision, gpc_degree=2)
+        precision=precision, gpc_degree=2, collision=collision)
 
 
 def fluid_mask(flags):
@@ -63,15 +63,19 @@ def cuda():
     return torch.device("cuda")
 
 
+@pytest.mark.parametrize("collision", [W.BGK, W.RR], ids=["bgk", "rr"])
 @pytest.mark.parametrize("bcname", list(BC_SETS))
 @pytest.mark.parametrize("precision,tol,nx", [(W.FP32_SHIFT, 2e-6, 37), (W.FP32_SHIFT, 2e-6, 40),
                                               (W.FP64_PLAIN, 1e-13, 37)])
-def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx):
+def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx, collision):
     """Populations after 1..6 and 31 steps (both AA parities) at every fluid
-    cell and node, max abs difference.  nx = 40 runs the TMA-staged kernels
-    (partial last run of 256 cells), nx = 37 the per-thread ones."""
-    wl = ragged(BC_SETS[bcname], precision=precision, nx=nx)
+    cell and node, max abs difference, for both collision forms.  nx = 40 runs
+    the TMA-staged kernels (partial last run of 256 cells), nx = 37 the
+    per-thread ones."""
+    wl = ragged(BC_SETS[bcname], precision=precision, nx=nx, collision=collision)
     ens = S.Ensemble(S.make_config(wl))
+    if nx == 40:
+        S.sc_lbm_set_tuning(ens.h, 128, 2, 1, variant=1)
     p, flags = oracle_domain(O, wl)
     Z, a = oracle_nodes(O, wl)
     fl = fluid_mask(flags)
@@ -97,6 +101,7 @@ def test_reduced_storage_tracks_oracle(O, cuda, precision):
     kernels with 2-byte elements."""
     wl = ragged(BC_SETS["urban"], precision=precision, nx=40)
     ens = S.Ensemble(S.make_config(wl))
+    S.sc_lbm_set_tuning(ens.h, 128, 2, 1, variant=1)
     ens.step(40)
     p, flags, f = oracle_run_node(O, wl, 0, 1, 40)
     _, uo = O.macros(p, flags, f)
@@ -220,6 +225,22 @@ def test_les_full_size_100_steps(O, cuda):
     wl = W.URBAN_LES
     ens = S.Ensemble(S.make_config(wl))
     S.sc_lbm_autotune(ens.h, None)
+    ens.step(100)
+    for j in (0, ens.n_nodes[0] - 1):
+        p, flags, f = oracle_run_node(O, wl, 0, j, 100)
+        _, uo = O.macros(p, flags, f)
+        ug = ens.velocity(0, j).cpu().numpy()
+        fl = fluid_mask(flags)
+        assert rel_l2(ug[:, fl], uo[:, fl]) <= 1e-3
+    ens.close()
+
+
+def test_les_full_size_100_steps_regularized(O, cuda):
+    """The urban LES ensemble with the paper's collision (recursive
+    regularized, third-order equilibrium, C_S = 0.25) at full size: first and
+    last node after 100 steps, relative L2 of u <= 1e-3."""
+    wl = W.URBAN_LES_RR
+    ens = S.Ensemble(S.make_config(wl))
     ens.step(100)
     for j in (0, ens.n_nodes[0] - 1):
         p, flags, f = oracle_run_node(O, wl, 0, j, 100)
