@@ -77,6 +77,9 @@ def lib():
                                           C.POINTER(C.c_longlong)]
         L.oc_profiles.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, i32, dp,
                                   C.c_void_p]
+        L.oc_gpc_basis_family.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
+        L.oc_inflow_log.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, dp]
         L.oc_gpc_basis_size.argtypes = [C.c_int, C.c_int]
         L.oc_gpc_basis.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
         L.oc_gpc_project.argtypes = [C.c_int, C.c_int, C.c_longlong, dp, dp, dp, dp]
@@ -196,7 +199,12 @@ def inflow(nz, u_ref, xi, alpha, H, theta_deg=0.0):
     return uin
 
 
+GL, CC_SMOLYAK, GH = 0, 1, 2
+
+
 def quadrature(rule, d, level, lo, hi):
+    """Nodes Z[n][d] and probability weights w[n].  GL / CC_SMOLYAK: uniform
+    inputs on [lo, hi]; GH: normal inputs, mean lo and standard deviation hi."""
     lo = np.ascontiguousarray(lo, np.float64)
     hi = np.ascontiguousarray(hi, np.float64)
     n = C.c_int(0)
@@ -236,6 +244,26 @@ def gpc_basis(d, degree, s):
     phi = np.zeros((s.shape[0], P))
     _chk(lib().oc_gpc_basis(d, degree, s.shape[0], s, phi), "gpc_basis")
     return phi
+
+
+LEGENDRE, HERMITE = 0, 1
+
+
+def gpc_basis_family(d, degree, family, s):
+    """Orthonormal basis values: Legendre on [-1,1] (family 0) or
+    probabilists' Hermite He_n / sqrt(n!) of standard-normal coordinates
+    (family 1)."""
+    s = np.ascontiguousarray(s, np.float64).reshape(-1, d)
+    P = lib().oc_gpc_basis_size(d, degree)
+    phi = np.zeros((s.shape[0], P))
+    _chk(lib().oc_gpc_basis_family(d, degree, family, s.shape[0], s, phi), "gpc_basis_family")
+    return phi
+
+
+def inflow_log(nz, u_ref, xi, z0, H, theta_deg=0.0):
+    uin = np.zeros((nz, 3))
+    _chk(lib().oc_inflow_log(nz, u_ref, xi, z0, H, theta_deg, uin.reshape(-1)), "inflow_log")
+    return uin
 
 
 def gpc_project(a, Qv, phi):
@@ -289,16 +317,21 @@ def velocity_magnitude(u, flags):
     return q
 
 
-def ensemble(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, keep_u=False):
+def ensemble(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, keep_u=False, z0=None):
     """Run the deterministic solver at every collocation node (Sec. 2.4 steps
-    4-6) and return |u| per node, Q[nq][ncell] (and u per node if asked)."""
+    4-6) and return |u| per node, Q[nq][ncell] (and u per node if asked).
+    z0: None for the power-law profile, else the roughness length of the
+    logarithmic profile (Sec. 3)."""
     n = p.nx * p.ny * p.nz
     nq = Z.shape[0]
     Qv = np.zeros((nq, n))
     us = []
     for j in range(nq):
         xi, al, th = node_inflow_params(Z[j], inputs, u_ref, alpha, theta_deg)
-        uin = inflow(p.nz, u_ref, xi, al, H, th)
+        if z0 is None:
+            uin = inflow(p.nz, u_ref, xi, al, H, th)
+        else:
+            uin = inflow_log(p.nz, u_ref, xi, z0, H, th)
         f = init_equilibrium(p, flags)
         run(p, flags, uin, f, 0, n_steps)
         _, u = macros(p, flags, f)
@@ -312,6 +345,11 @@ def rel_l2(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def normal_s(Z, mean, std):
+    """Normal nodes mapped to standard-normal coordinates: (Z - mean) / std."""
+    return (np.asarray(Z, np.float64) - np.asarray(mean, np.float64)) / np.asarray(std, np.float64)
 
 
 def legendre_s(Z, lo, hi):

@@ -788,11 +788,79 @@ int oc_inflow(int nz, double u_ref, double xi, double alpha, double H, double th
   return 0;
 }
 
-// Quadrature rules on the box prod [lo_t, hi_t] with probability weights.
+// Probabilists' Hermite polynomial He_n(x) by the three-term recurrence
+// He_{k+1} = x He_k - k He_{k-1}.
+static double hermite_e(int n, double x) {
+  double a = 1.0, b = x;
+  if (n == 0) return a;
+  for (int k = 1; k < n; ++k) {
+    double c = x * b - k * a;
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+// n-point Gauss-Hermite rule for the standard normal density (Sec. 2.4 step 3,
+// the dense tensor-product Gauss-Hermite quadrature): nodes are the roots of
+// He_n, found by bisection between the sign changes of He_n on a fine grid;
+// probability weights n! / (n He_{n-1}(x_k))^2.
+static void gauss_hermite(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.clear();
+  w.clear();
+  const double L = std::sqrt(4.0 * n + 2.0) + 1.0;
+  const int grid = 400 * n + 1;
+  double xa = -L, fa = hermite_e(n, xa);
+  for (int g = 1; g < grid; ++g) {
+    double xb = -L + 2.0 * L * g / (grid - 1), fb = hermite_e(n, xb);
+    if (fb == 0.0) {
+      x.push_back(xb);
+    } else if (fa != 0.0 && (fa < 0.0) != (fb < 0.0)) {
+      double lo = xa, hi = xb, flo = fa;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi), fm = hermite_e(n, mid);
+        if (fm == 0.0 || mid == lo || mid == hi) { lo = hi = mid; break; }
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
+        else hi = mid;
+      }
+      x.push_back(0.5 * (lo + hi));
+    }
+    xa = xb;
+    fa = fb;
+  }
+  double fact = 1.0;
+  for (int k = 2; k <= n; ++k) fact *= k;
+  for (double xk : x) {
+    double h = (double)n * hermite_e(n - 1, xk);
+    w.push_back(fact / (h * h));
+  }
+}
+
+// Logarithmic wind profile (Sec. 3): u(h) = u_ref (1 + xi) ln((h + z0)/z0) /
+// ln((H + z0)/z0) (cos theta, sin theta, 0), h = k + 1/2 above the ground
+// face, z0 the roughness length, both in cells.
+int oc_inflow_log(int nz, double u_ref, double xi, double z0, double H, double theta_deg, double* uin) {
+  if (nz < 1 || !(H > 0.0) || !(z0 > 0.0)) return -1;
+  double th = theta_deg * M_PI / 180.0;
+  double den = std::log((H + z0) / z0);
+  for (int k = 0; k < nz; ++k) {
+    double h = (double)k + 0.5;
+    double mag = u_ref * (1.0 + xi) * std::log((h + z0) / z0) / den;
+    uin[3 * k + 0] = mag * std::cos(th);
+    uin[3 * k + 1] = mag * std::sin(th);
+    uin[3 * k + 2] = 0.0;
+  }
+  return 0;
+}
+
+// Quadrature rules with probability weights.
 //   rule 0: tensor Gauss-Legendre, `level` points per dimension (1..5)
 //   rule 1: Clenshaw-Curtis Smolyak sparse grid of level L (1-based):
 //           sum over L <= |i| <= L+d-1 of (-1)^(L+d-1-|i|) C(d-1, L+d-1-|i|)
 //           times the tensor rule of 1-D levels i.
+//   (rules 0 and 1: uniform inputs on prod [lo_t, hi_t])
+//   rule 2: tensor Gauss-Hermite, `level` points per dimension (1..40), for
+//           normal inputs with mean lo_t and standard deviation hi_t.
 // Nodes are returned in lexicographic order of their integer index on the
 // finest 1-D grid (first coordinate most significant).  Z[n][d], w[n].
 // With Z == NULL only the count is returned.
@@ -851,6 +919,20 @@ int oc_quadrature(int rule, int d, int level, const double* lo, const double* hi
       while (t >= 0 && ++i[t] > level) { i[t] = 1; --t; }
       if (t < 0) break;
     }
+  } else if (rule == 2) {
+    if (level > 40) return -1;
+    std::vector<double> w1;
+    gauss_hermite(level, finest_x, w1);
+    if ((int)finest_x.size() != level) return -1;
+    std::vector<int> k(d, 0);
+    while (true) {
+      double prod = 1.0;
+      for (int t = 0; t < d; ++t) prod *= w1[k[t]];
+      acc[k] += prod;
+      int t = d - 1;
+      while (t >= 0 && ++k[t] == level) { k[t] = 0; --t; }
+      if (t < 0) break;
+    }
   } else {
     return -1;
   }
@@ -862,7 +944,8 @@ int oc_quadrature(int rule, int d, int level, const double* lo, const double* hi
   for (const auto& kv : acc) {
     for (int t = 0; t < d; ++t) {
       double x = finest_x[kv.first[t]];
-      Z[(long long)j * d + t] = 0.5 * (lo[t] + hi[t]) + 0.5 * (hi[t] - lo[t]) * x;
+      Z[(long long)j * d + t] = rule == 2 ? lo[t] + hi[t] * x
+                                          : 0.5 * (lo[t] + hi[t]) + 0.5 * (hi[t] - lo[t]) * x;
     }
     w[j] = kv.second;
     ++j;
@@ -986,6 +1069,30 @@ int oc_gpc_basis(int d, int degree, int nq, const double* s, double* phi) {
       phi[(long long)j * P + al] = v;
     }
   }
+  return 0;
+}
+
+// The same basis with a polynomial family per run: family 0 Legendre as
+// above (s in [-1,1]), family 1 orthonormal probabilists' Hermite
+// He_n(x) / sqrt(n!) for standard-normal x (the paper's Gaussian inputs,
+// Sec. 2.3-2.4); products over dimensions in the same graded order.
+int oc_gpc_basis_family(int d, int degree, int family, int nq, const double* s, double* phi) {
+  if (family == 0) return oc_gpc_basis(d, degree, nq, s, phi);
+  if (family != 1) return -1;
+  std::vector<std::vector<int>> mi;
+  multi_indices(d, degree, mi);
+  int P = (int)mi.size();
+  for (int j = 0; j < nq; ++j)
+    for (int al = 0; al < P; ++al) {
+      double v = 1.0;
+      for (int t = 0; t < d; ++t) {
+        int n = mi[al][t];
+        double fact = 1.0;
+        for (int k = 2; k <= n; ++k) fact *= k;
+        v *= hermite_e(n, s[(long long)j * d + t]) / std::sqrt(fact);
+      }
+      phi[(long long)j * P + al] = v;
+    }
   return 0;
 }
 

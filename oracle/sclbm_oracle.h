@@ -69,6 +69,8 @@ int oc_profiles(int nq, int nx, int ny, int nz, const double* a, const double* Q
                 int n_p, const int32_t* xy, double* prof, double* prof_nodes);
 int oc_gpc_basis_size(int d, int degree);
 int oc_gpc_basis(int d, int degree, int nq, const double* s, double* phi);
+int oc_gpc_basis_family(int d, int degree, int family, int nq, const double* s, double* phi);
+int oc_inflow_log(int nz, double u_ref, double xi, double z0, double H, double theta_deg, double* uin);
 int oc_gpc_project(int nq, int P, long long ncell, const double* a,
                    const double* Q, const double* phi, double* coef);
 
