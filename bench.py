@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--lbm-steps", type=int, default=500, help="time steps per benchmark step")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--workload", default="urban_les_256x128x64_cc3",
-                    choices=["urban_les_256x128x64_cc3", "urban_batched_3domains", "urban_large_512x256x128_cc4"],
+                    choices=["urban_les_256x128x64_cc3", "urban_batched_3domains", "urban_large_512x256x128_cc4",
+                             "urban_les_rr_256x128x64_cc3", "urban_gh121_256x128x64_rr"],
                     help="the benchmark workload; the other two are measured without the extra legs")
     ap.add_argument("--nodes", type=int, default=0,
                     help="profiling case: keep only this many Smolyak levels' worth of nodes (0 = all)")

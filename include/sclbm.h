@@ -71,6 +71,12 @@ extern "C" {
 /* quadrature rules (Sec. 2.3-2.4)                                            */
 #define SC_Q_GL 0            /* tensor Gauss-Legendre, quad_level points/dim   */
 #define SC_Q_CC_SMOLYAK 1    /* Clenshaw-Curtis Smolyak grid, level (1-based)  */
+#define SC_Q_GH 2            /* tensor Gauss-Hermite, quad_level points/dim,
+                                for normal inputs (Sec. 2.4 step 3)            */
+
+/* inflow profile shape (Sec. 3) */
+#define SC_PROFILE_POWER 0   /* u_ref (1 + xi) (h/H)^alpha                     */
+#define SC_PROFILE_LOG 1     /* u_ref (1 + xi) ln((h+z0)/z0) / ln((H+z0)/z0)   */
 
 /* population precision                                                       */
 #define SC_P_FP64_PLAIN 0    /* FP64, unshifted, two arrays, one node per launch */
@@ -90,8 +96,9 @@ extern "C" {
 /* One simulation domain (a box of nx*ny*nz cells, lattice units dx = dt = 1).
  * Geometry: the half-open boxes [x0,x1)x[y0,y1)x[z0,z1) in `boxes` when
  * n_boxes > 0, else n_buildings seeded rectangular blocks standing on the
- * ground (see sc_lbm_geometry).  quad_level: points per dimension (SC_Q_GL)
- * or the sparse-grid level (SC_Q_CC_SMOLYAK) used for this domain.          */
+ * ground (see sc_lbm_geometry).  quad_level: points per dimension (SC_Q_GL,
+ * 1..5; SC_Q_GH, 1..40) or the sparse-grid level (SC_Q_CC_SMOLYAK) used for
+ * this domain.                                                              */
 typedef struct {
   int nx, ny, nz;
   uint64_t geom_seed;
@@ -115,7 +122,16 @@ typedef struct {
  * third-order Hermite combinations D3Q19 carries, non-equilibrium rebuilt from
  * its second-order Hermite coefficient and the third-order one obtained by
  * the recursion a3_abg = u_a a2_bg + u_b a2_ag + u_g a2_ab; tau_eff as for
- * BGK.  Zero-initialised configs select BGK.                                */
+ * BGK.  Zero-initialised configs select BGK.
+ * Inputs: with SC_Q_GL / SC_Q_CC_SMOLYAK input k is uniform on [lo[k], hi[k]]
+ * and the gPC basis is orthonormal Legendre; with SC_Q_GH it is normal with
+ * mean lo[k] and standard deviation hi[k] (the paper's Gaussian speed and
+ * direction perturbations, Eq. mult_noise: SC_IN_SPEED_REL with mean 0 and
+ * std 0.1 is zeta_1 - 1, SC_IN_ANGLE_DEG with std 6 is zeta_2 in degrees)
+ * and the basis is orthonormal probabilists' Hermite He_n / sqrt(n!).
+ * profile: SC_PROFILE_POWER (default) or SC_PROFILE_LOG, the paper's
+ * logarithmic wind profile with roughness length z0 > 0 in cells (alpha
+ * unused).                                                                  */
 typedef struct {
   int n_domains;
   const sc_domain_desc* domains; /* host, read during calls only */
@@ -129,6 +145,8 @@ typedef struct {
   int precision;
   int gpc_degree;
   int collision;
+  int profile;
+  double z0;
 } sc_lbm_config;
 
 /* Launch shape of the stream-collide kernels (chosen by sc_lbm_autotune or
@@ -297,8 +315,8 @@ int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_sna
  * bytes (256-byte aligned), caller-owned, overwritten; loss_out: host double;
  * grad_out: host double[2]; u_probe_out: host double [n_probes][3] or NULL.
  * Leaves the handle's populations untouched; synchronises.
- * SC_ERR_UNSUPPORTED when c_smag > 0 or collision is not SC_COLL_BGK (the
- * adjoint covers BGK).                                                      */
+ * SC_ERR_UNSUPPORTED when c_smag > 0, collision is not SC_COLL_BGK (the
+ * adjoint covers BGK) or profile is not SC_PROFILE_POWER.                  */
 int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int n_probes,
                    const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
                    double* loss_out, double* grad_out, double* u_probe_out);

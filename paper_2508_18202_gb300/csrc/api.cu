@@ -67,9 +67,19 @@ int validate(const sc_lbm_config* c, std::string& why) {
       why = "bad input kind";
       return SC_ERR_ARG;
     }
-    if (!(c->hi[k] > c->lo[k])) { why = "input range must have hi > lo"; return SC_ERR_ARG; }
+    if (c->quad_rule == SC_Q_GH) {
+      if (!(c->hi[k] > 0.0)) { why = "normal inputs need a standard deviation hi > 0"; return SC_ERR_ARG; }
+    } else if (!(c->hi[k] > c->lo[k])) {
+      why = "input range must have hi > lo";
+      return SC_ERR_ARG;
+    }
   }
-  if (c->quad_rule != SC_Q_GL && c->quad_rule != SC_Q_CC_SMOLYAK) { why = "bad quad_rule"; return SC_ERR_ARG; }
+  if (c->quad_rule != SC_Q_GL && c->quad_rule != SC_Q_CC_SMOLYAK && c->quad_rule != SC_Q_GH) {
+    why = "bad quad_rule";
+    return SC_ERR_ARG;
+  }
+  if (c->profile != SC_PROFILE_POWER && c->profile != SC_PROFILE_LOG) { why = "bad profile"; return SC_ERR_ARG; }
+  if (c->profile == SC_PROFILE_LOG && !(c->z0 > 0.0)) { why = "log profile needs z0 > 0"; return SC_ERR_ARG; }
   if (c->precision < SC_P_FP64_PLAIN || c->precision > SC_P_FP16_STORE) { why = "bad precision"; return SC_ERR_ARG; }
   if (c->ramp_steps < 0 || c->ramp_steps > 10000000) { why = "bad ramp_steps"; return SC_ERR_ARG; }
   if (c->gpc_degree > 8) { why = "gpc_degree too large"; return SC_ERR_UNSUPPORTED; }
@@ -652,15 +662,17 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
         if (c.inputs[t] == SC_IN_SPEED_REL) xi = zt;
         else if (c.inputs[t] == SC_IN_ALPHA) al = zt;
         else th = zt;
-        s[t] = (2.0 * zt - c.lo[t] - c.hi[t]) / (c.hi[t] - c.lo[t]);
+        // basis coordinate: [-1, 1] (uniform inputs) or standard normal
+        s[t] = c.quad_rule == SC_Q_GH ? (zt - c.lo[t]) / c.hi[t]
+                                      : (2.0 * zt - c.lo[t] - c.hi[t]) / (c.hi[t] - c.lo[t]);
       }
       double* ud = &uind[d][(size_t)j * D.nz * 3];
-      hn_inflow(D.nz, c.u_ref, xi, al, H, th, ud);
+      hn_inflow(D.nz, c.u_ref, xi, al, H, th, ud, c.profile, c.z0);
       for (int k = 0; k < D.nz; ++k)
         for (int a = 0; a < 3; ++a) uinf[d][((size_t)j * D.nz + k) * 4 + a] = (float)ud[3 * k + a];
       abt[d][(size_t)j * (h->gpcP + 1)] = w[j];
       if (h->gpcP > 0) {
-        hn_gpc_basis(c.n_inputs, c.gpc_degree, s, phi.data());
+        hn_gpc_basis(c.n_inputs, c.gpc_degree, s, phi.data(), c.quad_rule == SC_Q_GH);
         for (int a = 0; a < h->gpcP; ++a) abt[d][(size_t)j * (h->gpcP + 1) + 1 + a] = w[j] * phi[a];
       }
     }
@@ -1076,7 +1088,7 @@ static void node_inflow(const sc_lbm_config& c, const std::vector<double>& Z, in
     else th = zt;
   }
   const double H = c.H_ref > 0 ? c.H_ref : (double)nz;
-  hn_inflow(nz, c.u_ref, xi, al, H, th, ud);
+  hn_inflow(nz, c.u_ref, xi, al, H, th, ud, c.profile, c.z0);
   if (alpha_out) *alpha_out = al;
 }
 
@@ -1154,6 +1166,8 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
   if (!h || !probes || !u_target || !loss_out || !grad_out) return SC_ERR_ARG;
   if (h->cfg.c_smag != 0.0 || h->cfg.collision != SC_COLL_BGK)
     return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers BGK (c_smag = 0, SC_COLL_BGK)");
+  if (h->cfg.profile != SC_PROFILE_POWER)
+    return fail(h, SC_ERR_UNSUPPORTED, "the adjoint's parameters are those of the power-law profile");
   AdjLayout L;
   int rc = adj_plan(h, domain, n_steps, n_snapshots, n_probes, L);
   if (rc) return fail(h, rc, "bad adjoint arguments");

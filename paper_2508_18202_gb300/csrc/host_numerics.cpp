@@ -119,6 +119,85 @@ long long choose(int n, int k) {
 
 // Accumulator keyed by the finest-grid integer index, filled in enumeration
 // order (so each node's weight is summed in the order of contributions).
+// Orthonormal probabilists' Hermite polynomials p_0..p_{n-1} at x:
+// p_0 = 1, p_1 = x, sqrt(k+1) p_{k+1} = x p_k - sqrt(k) p_{k-1}.
+double christoffel_sum(int n, double x) {
+  double a = 1.0, b = x, s = 1.0;
+  if (n > 1) s += b * b;
+  for (int k = 1; k + 1 < n; ++k) {
+    const double c = (x * b - sqrt((double)k) * a) / sqrt((double)(k + 1));
+    a = b;
+    b = c;
+    s += c * c;
+  }
+  return s;
+}
+
+// n-point Gauss-Hermite rule for the standard normal density by the
+// Golub-Welsch construction: the nodes are the eigenvalues of the symmetric
+// tridiagonal Jacobi matrix of the orthonormal probabilists' Hermite
+// polynomials (zero diagonal, off-diagonal sqrt(k)), found by cyclic Jacobi
+// rotations (n <= 40, so cost is no concern) and polished by Newton steps on
+// the recurrence.  The probability weights are
+// the reciprocal Christoffel sums 1 / sum_{k<n} p_k(x)^2 at the nodes, which
+// keeps the tiny tail weights accurate in relative terms.  Nodes are then
+// made exactly antisymmetric and the weights symmetric.
+bool gh_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  if (n < 1 || n > 40) return false;
+  std::vector<double> A((size_t)n * n, 0.0);
+  for (int k = 1; k < n; ++k) A[(size_t)k * n + k - 1] = A[(size_t)(k - 1) * n + k] = sqrt((double)k);
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+    if (off < 1e-60) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        // rotation angle zeroing A[p][q]: tan(2 phi) = 2 apq / (aqq - app)
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  x.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) x[k] = A[(size_t)k * n + k];
+  std::sort(x.begin(), x.end());
+  // two Newton steps on p_n (p_n' = sqrt(n) p_{n-1}) polish the eigenvalues
+  for (int k = 0; k < n; ++k)
+    for (int it = 0; it < 2; ++it) {
+      double a = 1.0, b = x[k];
+      for (int m = 1; m < n; ++m) {
+        const double c = (x[k] * b - sqrt((double)m) * a) / sqrt((double)(m + 1));
+        a = b;
+        b = c;
+      }
+      if (n > 1 && a != 0.0) x[k] -= b / (sqrt((double)n) * a);
+    }
+  for (int k = 0; k < n / 2; ++k) {
+    const double xs = 0.5 * (x[n - 1 - k] - x[k]);
+    x[k] = -xs;
+    x[n - 1 - k] = xs;
+  }
+  if (n & 1) x[n / 2] = 0.0;
+  w.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) w[k] = 1.0 / christoffel_sum(n, x[k]);
+  for (int k = 0; k < n / 2; ++k) w[k] = w[n - 1 - k] = 0.5 * (w[k] + w[n - 1 - k]);
+  return true;
+}
+
 struct NodeAcc {
   int d;
   std::vector<int> keys;       // [count][d]
@@ -206,6 +285,22 @@ int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi
         acc.add(key, prod);
       }
     }
+  } else if (rule == SC_Q_GH) {
+    std::vector<double> w1;
+    if (!gh_rule(level, fine_x, w1)) return SC_ERR_ARG;
+    int total = 1;
+    for (int t = 0; t < d; ++t) total *= level;
+    for (int flat = 0; flat < total; ++flat) {
+      int key[3];
+      int rem = flat;
+      for (int t = d - 1; t >= 0; --t) {
+        key[t] = rem % level;
+        rem /= level;
+      }
+      double prod = 1.0;
+      for (int t = 0; t < d; ++t) prod *= w1[key[t]];
+      acc.add(key, prod);
+    }
   } else {
     return SC_ERR_ARG;
   }
@@ -224,7 +319,8 @@ int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi
     const int e = order[r];
     for (int t = 0; t < d; ++t) {
       double x = fine_x[acc.keys[(size_t)e * d + t]];
-      Z[(size_t)r * d + t] = 0.5 * (lo[t] + hi[t]) + 0.5 * (hi[t] - lo[t]) * x;
+      Z[(size_t)r * d + t] = rule == SC_Q_GH ? lo[t] + hi[t] * x  // normal: mean lo, std hi
+                                             : 0.5 * (lo[t] + hi[t]) + 0.5 * (hi[t] - lo[t]) * x;
     }
     w[r] = acc.weight[e];
   }
@@ -599,11 +695,14 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
 }
 
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
-               double* uin) {
+               double* uin, int profile, double z0) {
   const double theta = theta_deg * M_PI / 180.0;
   const double c = cos(theta), s = sin(theta);
+  const double lden = profile == SC_PROFILE_LOG ? log((H + z0) / z0) : 1.0;
   for (int k = 0; k < nz; ++k) {
-    const double speed = u_ref * (1.0 + xi) * pow(((double)k + 0.5) / H, alpha);
+    const double h = (double)k + 0.5;
+    const double speed = profile == SC_PROFILE_LOG ? u_ref * (1.0 + xi) * log((h + z0) / z0) / lden
+                                                   : u_ref * (1.0 + xi) * pow(h / H, alpha);
     uin[3 * k + 0] = speed * c;
     uin[3 * k + 1] = speed * s;
     uin[3 * k + 2] = 0.0;
@@ -624,14 +723,24 @@ int hn_gpc_size(int d, int degree) {
 // Orthonormal Legendre products on [-1, 1]^d, graded order: total degree
 // ascending; within a degree the exponent of the first input descending, then
 // of the second, ...
-void hn_gpc_basis(int d, int degree, const double* s, double* phi) {
+void hn_gpc_basis(int d, int degree, const double* s, double* phi, bool hermite) {
   double leg[3][16];
   for (int t = 0; t < d; ++t) {
     leg[t][0] = 1.0;
     if (degree >= 1) leg[t][1] = s[t];
-    for (int n = 1; n < degree; ++n)
-      leg[t][n + 1] = ((2 * n + 1) * s[t] * leg[t][n] - n * leg[t][n - 1]) / (double)(n + 1);
-    for (int n = 0; n <= degree; ++n) leg[t][n] *= sqrt(2.0 * n + 1.0);
+    if (hermite) {
+      // orthonormal probabilists' Hermite: He_{n+1} = x He_n - n He_{n-1}, / sqrt(n!)
+      for (int n = 1; n < degree; ++n) leg[t][n + 1] = s[t] * leg[t][n] - n * leg[t][n - 1];
+      double fact = 1.0;
+      for (int n = 0; n <= degree; ++n) {
+        if (n > 1) fact *= n;
+        leg[t][n] /= sqrt(fact);
+      }
+    } else {
+      for (int n = 1; n < degree; ++n)
+        leg[t][n + 1] = ((2 * n + 1) * s[t] * leg[t][n] - n * leg[t][n - 1]) / (double)(n + 1);
+      for (int n = 0; n <= degree; ++n) leg[t][n] *= sqrt(2.0 * n + 1.0);
+    }
   }
   int out = 0;
   for (int tot = 0; tot <= degree; ++tot) {

@@ -15,7 +15,7 @@ namespace sclbm {
 
 constexpr int kQ = 19;
 constexpr int kMaxDomains = SC_MAX_DOMAINS;
-constexpr int kMaxGpcP = 20;     // largest gPC basis the reduction kernel keeps in registers
+constexpr int kMaxGpcP = 28;     // largest gPC basis the reduction kernel keeps in registers
 constexpr int kRun = 256;        // cells per run of the TMA-staged kernels; the row pitch is a multiple
 
 // Link word per cell (64 bits).  Bits 2i, 2i+1 give the kind of link i, the
@@ -144,10 +144,10 @@ void hn_boundary_cells(const std::vector<LinkWord>& link, std::vector<int32_t>& 
 void hn_cell_classes(const std::vector<LinkWord>& link, std::vector<uint8_t>& cls);
 void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::vector<LinkWord>& link,
                      const std::vector<int32_t>& cells, long long pitch, std::vector<ListedLinks>& tab);
-void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
-               double* uin /*[nz][3]*/);
+void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg, double* uin,
+               int profile = 0, double z0 = 0.1);
 int hn_gpc_size(int d, int degree);
-void hn_gpc_basis(int d, int degree, const double* s /*[d]*/, double* phi /*[P]*/);
+void hn_gpc_basis(int d, int degree, const double* s /*[d]*/, double* phi /*[P]*/, bool hermite = false);
 double hn_ramp(int ramp_steps, long long m);
 
 // ------------------------------------------------------------ kernel launchers

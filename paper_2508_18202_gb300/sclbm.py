@@ -21,7 +21,8 @@ SC_ERR_SCRATCH = -8
 SC_NOALLOC_MAX_NODES = 1024
 SC_BC_VELOCITY, SC_BC_OUTFLOW, SC_BC_BOUNCE_BACK, SC_BC_FREE_SLIP, SC_BC_PERIODIC = 0, 1, 2, 3, 4
 SC_IN_SPEED_REL, SC_IN_ALPHA, SC_IN_ANGLE_DEG = 0, 1, 2
-SC_Q_GL, SC_Q_CC_SMOLYAK = 0, 1
+SC_Q_GL, SC_Q_CC_SMOLYAK, SC_Q_GH = 0, 1, 2
+SC_PROFILE_POWER, SC_PROFILE_LOG = 0, 1
 SC_P_FP64_PLAIN, SC_P_FP32_SHIFT, SC_P_BF16_STORE, SC_P_FP16_STORE = 0, 1, 2, 3
 SC_EXEC_LAUNCH, SC_EXEC_GRAPH, SC_EXEC_PERSISTENT = 0, 1, 2
 SC_COLL_BGK, SC_COLL_RR = 0, 1
@@ -52,7 +53,8 @@ class sc_lbm_config(C.Structure):
                 ("alpha", C.c_double), ("angle_deg", C.c_double), ("H_ref", C.c_double),
                 ("n_inputs", C.c_int), ("inputs", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("quad_rule", C.c_int), ("ramp_steps", C.c_int),
-                ("precision", C.c_int), ("gpc_degree", C.c_int), ("collision", C.c_int)]
+                ("precision", C.c_int), ("gpc_degree", C.c_int), ("collision", C.c_int),
+                ("profile", C.c_int), ("z0", C.c_double)]
 
 
 class sc_lbm_tuning(C.Structure):
@@ -140,7 +142,8 @@ class Config:
     """Owns an sc_lbm_config and the arrays it points to."""
 
     def __init__(self, domains, tau0, c_smag, u_ref, alpha, inputs, lo, hi, quad_rule,
-                 precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1, collision=SC_COLL_BGK):
+                 precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1, collision=SC_COLL_BGK,
+                 profile=SC_PROFILE_POWER, z0=0.1):
         self._doms = (sc_domain_desc * len(domains))()
         self._boxes = []
         for k, d in enumerate(domains):
@@ -169,6 +172,7 @@ class Config:
             c.inputs[k], c.lo[k], c.hi[k] = inputs[k], lo[k], hi[k]
         c.quad_rule, c.ramp_steps, c.precision, c.gpc_degree = quad_rule, ramp_steps, precision, gpc_degree
         c.collision = collision
+        c.profile, c.z0 = profile, z0
         self.c = c
         self.domains = [dict(d) for d in domains]
 
@@ -449,7 +453,8 @@ def make_config(workload, **over):
     return Config(w["domains"], w["tau0"], w["c_smag"], w["u_ref"], w["alpha"], w["inputs"], w["lo"],
                   w["hi"], w["quad_rule"], w["precision"], ramp_steps=w["ramp_steps"],
                   angle_deg=w.get("angle_deg", 0.0), H_ref=w.get("H_ref", 0.0),
-                  gpc_degree=w.get("gpc_degree", -1), collision=w.get("collision", SC_COLL_BGK))
+                  gpc_degree=w.get("gpc_degree", -1), collision=w.get("collision", SC_COLL_BGK),
+                  profile=w.get("profile", SC_PROFILE_POWER), z0=w.get("z0", 0.1))
 
 
 # ------------------------------------------------------------------ assimilation

@@ -10,7 +10,8 @@ import copy
 
 VEL, OUT, BB, FS, PER = 0, 1, 2, 3, 4
 SPEED, ALPHA, ANGLE = 0, 1, 2
-GL, CC_SMOLYAK = 0, 1
+GL, CC_SMOLYAK, GH = 0, 1, 2
+PROFILE_POWER, PROFILE_LOG = 0, 1
 FP64_PLAIN, FP32_SHIFT, BF16_STORE, FP16_STORE = 0, 1, 2, 3
 BGK, RR = 0, 1   # collision: BGK, or the recursive regularized form with the third-order equilibrium
 
@@ -88,7 +89,20 @@ URBAN_LARGE = dict(
 # third-order equilibrium, Smagorinsky C_S = 0.25.
 URBAN_LES_RR = dict(URBAN_LES, name="urban_les_rr_256x128x64_cc3", collision=RR, c_smag=0.25)
 
-ALL = [CHANNEL_CUBE, URBAN_LES, URBAN_BATCHED, URBAN_ADJOINT, URBAN_LARGE, URBAN_LES_RR]
+# The paper's uncertainty setup on the synthetic urban block (Sec. 2.1, Sec. 3,
+# Sec. 2.4): Gaussian speed factor zeta_1 ~ N(1, 0.1^2) (speed error mean 0,
+# std 0.1) and direction perturbation zeta_2 ~ N(0, 6^2) degrees on the dense
+# 11 x 11 Gauss-Hermite rule (121 nodes), logarithmic profile with roughness
+# length 0.1 cells, Hermite gPC of total degree 5, the recursive regularized
+# collision with C_S = 0.25.
+URBAN_GH121 = dict(
+    URBAN_LES, name="urban_gh121_256x128x64_rr",
+    domains=[dict(URBAN_LES["domains"][0], quad_level=11)],
+    inputs=[SPEED, ANGLE], lo=[0.0, 0.0], hi=[0.1, 6.0], quad_rule=GH, collision=RR, c_smag=0.25,
+    profile=PROFILE_LOG, z0=0.1, gpc_degree=5, n_columns=4,
+)
+
+ALL = [CHANNEL_CUBE, URBAN_LES, URBAN_BATCHED, URBAN_ADJOINT, URBAN_LARGE, URBAN_LES_RR, URBAN_GH121]
 
 
 def variant(workload, **over):

@@ -45,13 +45,33 @@ def _oracle_rule(O, cfg, d):
 
 @pytest.mark.parametrize("wl", W.ALL, ids=lambda w: w["name"])
 def test_quadrature_bit_exact_with_oracle(O, wl):
+    """Gauss-Legendre and Clenshaw-Curtis Smolyak rules are a bit-exact
+    contract; Gauss-Hermite nodes come from an eigenproblem in the library and
+    from bisection in the oracle, so they agree to rounding."""
     cfg = S.make_config(wl)
     for d in range(len(wl["domains"])):
         Z, w = S.sc_lbm_quadrature(cfg, d)
         Zo, wo = _oracle_rule(O, cfg, d)
         assert Z.shape == Zo.shape
-        assert Z.tobytes() == Zo.tobytes()
-        assert w.tobytes() == wo.tobytes()
+        if wl["quad_rule"] == W.GH:
+            scale = np.abs(np.asarray(wl["hi"]))[None, :]
+            assert np.max(np.abs(Z - Zo) / scale) < 1e-13
+            assert np.max(np.abs(w - wo) / wo) < 1e-12
+        else:
+            assert Z.tobytes() == Zo.tobytes()
+            assert w.tobytes() == wo.tobytes()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 7, 11, 16, 25, 40])
+def test_gauss_hermite_library_rule(O, n):
+    """The library's Golub-Welsch rule against the oracle's bisection rule."""
+    cfg = S.make_config(dict(W.URBAN_GH121, domains=[dict(W.URBAN_GH121["domains"][0], quad_level=n)],
+                             inputs=[W.SPEED], lo=[0.0], hi=[1.0], gpc_degree=-1))
+    Z, w = S.sc_lbm_quadrature(cfg, 0)
+    Zo, wo = O.quadrature(W.GH, 1, n, [0.0], [1.0])
+    assert np.max(np.abs(Z - Zo)) < 1e-13
+    assert np.max(np.abs(w - wo) / wo) < 1e-12
+    assert np.all(Z[:, 0] == -Z[::-1, 0]) and np.all(w == w[::-1])
 
 
 @pytest.mark.parametrize("rule,d,level", [(0, 1, n) for n in range(1, 6)] + [(0, 2, 3), (0, 3, 2)]
@@ -98,7 +118,11 @@ def test_workspace_size_scales_with_precision():
     (dict(lo=[0.1, 0.15], hi=[-0.1, 0.35]), S.SC_ERR_ARG),
     (dict(quad_rule=7), S.SC_ERR_ARG),
     (dict(precision=9), S.SC_ERR_ARG),
-    (dict(gpc_degree=6), S.SC_ERR_UNSUPPORTED),
+    (dict(gpc_degree=7), S.SC_ERR_UNSUPPORTED),
+    (dict(collision=3), S.SC_ERR_ARG),
+    (dict(profile=5), S.SC_ERR_ARG),
+    (dict(profile=W.PROFILE_LOG, z0=0.0), S.SC_ERR_ARG),
+    (dict(quad_rule=W.GH, lo=[0.0, 0.0], hi=[0.1, 0.0]), S.SC_ERR_ARG),
     (dict(domain_over=dict(bc=[W.OUT, W.VEL, W.VEL, W.VEL, W.BB, W.FS])), S.SC_ERR_UNSUPPORTED),
     (dict(domain_over=dict(bc=[W.PER, W.OUT, W.VEL, W.VEL, W.BB, W.FS])), S.SC_ERR_ARG),
     (dict(domain_over=dict(nx=0)), S.SC_ERR_ARG),

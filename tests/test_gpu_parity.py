@@ -157,6 +157,36 @@ def test_channel_ensemble_statistics(O, cuda, precision, tol):
     ens.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(W.FP64_PLAIN, 1e-11), (W.FP32_SHIFT, 1e-5)])
+def test_gaussian_inputs_ensemble_statistics(O, cuda, precision, tol):
+    """The paper's input model on the cube channel: speed factor and wind
+    direction normal (std 0.1 and 6 degrees) on a 3 x 3 Gauss-Hermite rule,
+    logarithmic profile, recursive regularized collision; mean / std / profile
+    band and the Hermite gPC coefficients against the oracle."""
+    wl = dict(W.CHANNEL_CUBE, precision=precision, inputs=[W.SPEED, W.ANGLE], lo=[0.0, 0.0],
+              hi=[0.1, 6.0], quad_rule=W.GH, profile=W.PROFILE_LOG, z0=0.1, collision=W.RR,
+              gpc_degree=2, domains=[dict(W.CHANNEL_CUBE["domains"][0], quad_level=3)])
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(wl["steps"])
+    out = ens.moments(0, probes=wl["columns"], nodes_profiles=True, gpc=True)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    assert Z.shape == (9, 2)
+    Qv = O.ensemble(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, wl["steps"],
+                    z0=wl["z0"])
+    mean, std, _ = O.moments_two_pass(a, Qv)
+    fl = fluid_mask(flags)
+    assert rel_l2(out["mean"].cpu().numpy()[fl], mean[fl]) <= tol
+    assert rel_l2(out["std"].cpu().numpy()[fl], std[fl]) <= tol * 10
+    prof, _ = O.profiles(a, Qv, p.nx, p.ny, p.nz, wl["columns"])
+    assert rel_l2(out["prof"].cpu().numpy(), prof) <= tol * 10
+    coef = O.gpc_project(a, Qv, O.gpc_basis_family(2, 2, O.HERMITE, O.normal_s(Z, wl["lo"], wl["hi"])))
+    cg = out["coef"].cpu().numpy()
+    for k in range(coef.shape[0]):
+        assert rel_l2(cg[k][fl], coef[k][fl]) <= tol * 10, k
+    ens.close()
+
+
 @pytest.mark.parametrize("nx2", [29, 32])
 def test_batched_uneven_domains_match_oracle(O, cuda, nx2):
     """Three domains of different sizes and node counts advance in one launch;
