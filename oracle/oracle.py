@@ -360,3 +360,59 @@ def legendre_s(Z, lo, hi):
 
 
 PI = math.pi
+
+
+def qcriterion(u, flags, nx, ny, nz, bc):
+    """Q-criterion of a velocity field u[3][ncell] (cell index x + nx (y + ny z)):
+    Q = (|Omega|^2 - |S|^2) / 2 with S, Omega the symmetric and antisymmetric
+    parts of grad u.  Per axis: central difference where both neighbours are
+    fluid cells, one-sided where only one is, zero where none is; axes whose
+    faces are periodic (bc[2a] == 4) wrap.  Solid cells give 0."""
+    U = np.asarray(u, np.float64).reshape(3, nz, ny, nx)
+    fluid = (np.asarray(flags).reshape(nz, ny, nx) == 0)
+    J = np.zeros((3, 3, nz, ny, nx))
+    for a in range(3):
+        ax = 2 - a                      # array axis of x, y, z
+        periodic = bc[2 * a] == 4
+        n = U.shape[1 + ax]
+        idx = np.arange(n)
+        shape = [1, 1, 1]
+        shape[ax] = n
+        inside_p = (idx + 1 < n).reshape(shape) | periodic
+        inside_m = (idx - 1 >= 0).reshape(shape) | periodic
+        ok_p = inside_p & np.roll(fluid, -1, axis=ax)
+        ok_m = inside_m & np.roll(fluid, 1, axis=ax)
+        for i in range(3):
+            up = np.roll(U[i], -1, axis=ax)
+            um = np.roll(U[i], 1, axis=ax)
+            d = np.where(ok_p & ok_m, 0.5 * (up - um),
+                         np.where(ok_p, up - U[i], np.where(ok_m, U[i] - um, 0.0)))
+            J[i, a] = d
+    S = 0.5 * (J + J.transpose(1, 0, 2, 3, 4))
+    Wm = 0.5 * (J - J.transpose(1, 0, 2, 3, 4))
+    Q = 0.5 * ((Wm ** 2).sum((0, 1)) - (S ** 2).sum((0, 1)))
+    Q[~fluid] = 0.0
+    return Q.reshape(-1)
+
+
+def ensemble_time_average(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_warm, n_samples, every,
+                          z0=None):
+    """Per-node time average of |u| (Sec. 2.4 step 6): after n_warm steps,
+    n_samples samples of |u|, the first at level n_warm, then every `every`
+    steps.  Returns A[nq][ncell]."""
+    n = p.nx * p.ny * p.nz
+    A = np.zeros((Z.shape[0], n))
+    for j in range(Z.shape[0]):
+        xi, al, th = node_inflow_params(Z[j], inputs, u_ref, alpha, theta_deg)
+        uin = inflow(p.nz, u_ref, xi, al, H, th) if z0 is None else inflow_log(p.nz, u_ref, xi, z0, H, th)
+        f = init_equilibrium(p, flags)
+        run(p, flags, uin, f, 0, n_warm)
+        t = n_warm
+        for s in range(n_samples):
+            if s:
+                run(p, flags, uin, f, t, every)
+                t += every
+            _, u = macros(p, flags, f)
+            A[j] += velocity_magnitude(u, flags)
+        A[j] /= n_samples
+    return A
