@@ -131,7 +131,9 @@ typedef struct {
  * and the basis is orthonormal probabilists' Hermite He_n / sqrt(n!).
  * profile: SC_PROFILE_POWER (default) or SC_PROFILE_LOG, the paper's
  * logarithmic wind profile with roughness length z0 > 0 in cells (alpha
- * unused).                                                                  */
+ * unused).
+ * time_average: 1 reserves FP64 accumulators (8 B per cell and node) for the
+ * time-averaged |u| fields (sc_lbm_average_*), 0 none.                     */
 typedef struct {
   int n_domains;
   const sc_domain_desc* domains; /* host, read during calls only */
@@ -147,6 +149,7 @@ typedef struct {
   int collision;
   int profile;
   double z0;
+  int time_average;
 } sc_lbm_config;
 
 /* Launch shape of the stream-collide kernels (chosen by sc_lbm_autotune or
@@ -245,6 +248,31 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev,
 /* Velocity of one node at the current time: d_u device float [3][ncell],
  * solid cells 0.                                                            */
 int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u);
+
+/* Time-averaged velocity magnitude fields (Sec. 2.4 step 6, the paper's
+ * time-averaged QoI), for configurations with time_average = 1 (else
+ * SC_ERR_STATE).  sc_lbm_average_reset zeroes the accumulators;
+ * sc_lbm_average_add adds |u| of every node of every domain at the current
+ * time level as one sample (FP64 sums); sc_lbm_average_moments is
+ * sc_lbm_moments (same arguments and outputs) applied to the per-node time
+ * averages Q_j = sum over samples / samples; sc_lbm_average_field writes the
+ * time average of one node into d_q (device double [ncell]).  Both readers
+ * need at least one sample (else SC_ERR_STATE).  Asynchronous on the
+ * handle's stream except where out_host = 1.                               */
+int sc_lbm_average_reset(sc_lbm_t h);
+int sc_lbm_average_add(sc_lbm_t h);
+int sc_lbm_average_samples(sc_lbm_t h, long long* samples);
+int sc_lbm_average_moments(sc_lbm_t h, int domain, double* mean, double* stdev,
+                           const int32_t* probe_xy, int n_p, double* prof, float* prof_nodes,
+                           double* gpc_coef, int out_host);
+int sc_lbm_average_field(sc_lbm_t h, int domain, int node, double* d_q);
+
+/* Q-criterion of a velocity field (the vortex identification of the paper's
+ * Q-criterion figures): d_u device float [3][ncell] (for instance from
+ * sc_lbm_velocity), d_q device float [ncell] receives
+ * Q = (|Omega|^2 - |S|^2) / 2 of grad u by central differences (dx = 1),
+ * one-sided next to solid cells and non-periodic faces; solid cells 0.     */
+int sc_lbm_qcriterion(sc_lbm_t h, int domain, const float* d_u, float* d_q);
 
 /* Populations f_i (unshifted, natural layout) of one node at the current
  * time: d_f device double [19][ncell]; solid cells 0.  Velocity order:

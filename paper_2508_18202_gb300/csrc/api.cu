@@ -38,6 +38,7 @@ struct DomLayout {
   size_t guard = 0;
   long long nb_max = 0;
   size_t flags = 0, link = 0, cls = 0, bcell = 0, ltab = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
+  size_t avg = 0;  // time-averaged |u| accumulators [nq][ncell] (FP64), when configured
 };
 struct Layout {
   size_t hdr = 0, ramp_f = 0, ramp_d = 0, probes = 0;
@@ -84,6 +85,7 @@ int validate(const sc_lbm_config* c, std::string& why) {
   if (c->ramp_steps < 0 || c->ramp_steps > 10000000) { why = "bad ramp_steps"; return SC_ERR_ARG; }
   if (c->gpc_degree > 8) { why = "gpc_degree too large"; return SC_ERR_UNSUPPORTED; }
   if (c->collision != SC_COLL_BGK && c->collision != SC_COLL_RR) { why = "bad collision"; return SC_ERR_ARG; }
+  if (c->time_average != 0 && c->time_average != 1) { why = "time_average must be 0 or 1"; return SC_ERR_ARG; }
   if (c->gpc_degree >= 0 && hn_gpc_size(c->n_inputs, c->gpc_degree) > kMaxGpcP) {
     why = "gPC basis larger than " + std::to_string(kMaxGpcP);
     return SC_ERR_UNSUPPORTED;
@@ -169,6 +171,7 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     if (c->precision == SC_P_FP64_PLAIN) M.g2 = take(sb * kQ * (size_t)M.pitch * M.nq);
     else M.bout = take(sizeof(float) * 5 * (size_t)D.nz * D.ny * M.nq);
     M.ab = take(sizeof(double) * (size_t)M.nq * (P + 1));
+    if (c->time_average) M.avg = take(sizeof(double) * (size_t)M.nq * (size_t)M.ncell);
     max_cell = std::max(max_cell, M.ncell);
     max_nz = std::max(max_nz, D.nz);
     max_nq = std::max(max_nq, M.nq);
@@ -274,6 +277,8 @@ struct sc_lbm_s {
   int gpcP = 0;
   sc_lbm_tuning tune;
   long long steps = 0, launches = 0;
+  long long avg_samples = 0;                  // samples in the time-average accumulators
+  const double* avg_read = nullptr;           // set while the moments read the time average
   std::string err;
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
@@ -736,6 +741,8 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
     if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
     if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());
+    if (e == cudaSuccess && M.avg)
+      e = cudaMemsetAsync(h->ws + M.avg, 0, sizeof(double) * (size_t)M.nq * (size_t)M.ncell, h->stream);
     if (e == cudaSuccess && M.bout)
       e = cudaMemsetAsync(h->ws + M.bout, 0, sizeof(float) * 5 * (size_t)c.domains[d].nz * c.domains[d].ny * M.nq, h->stream);
   }
@@ -794,6 +801,8 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   A.n_p = n_p;
   A.prof = out_host ? (double*)(h->ws + L.st_prof) : prof;
   A.prof_nodes = out_host ? (prof_nodes ? (float*)(h->ws + L.st_pnodes) : nullptr) : prof_nodes;
+  A.avg = h->avg_read;
+  A.avg_scale = h->avg_samples > 0 ? 1.0 / (double)h->avg_samples : 0.0;
   if (n_p > 0)
     CK(cudaMemcpyAsync(h->ws + L.probes, probe_xy, sizeof(int32_t) * 2 * n_p, cudaMemcpyHostToDevice,
                        h->stream));
@@ -816,6 +825,68 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   rc = read_err(h, &bits);
   if (rc) return rc;
   return err_status(h, bits);
+}
+
+int sc_lbm_average_reset(sc_lbm_t h) {
+  if (!h) return SC_ERR_ARG;
+  if (!h->cfg.time_average) return fail(h, SC_ERR_STATE, "time_average = 0 in the configuration");
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    const DomLayout& M = h->L.dom[d];
+    CK(cudaMemsetAsync(h->ws + M.avg, 0, sizeof(double) * (size_t)M.nq * (size_t)M.ncell, h->stream));
+  }
+  h->avg_samples = 0;
+  return SC_OK;
+}
+
+int sc_lbm_average_add(sc_lbm_t h) {
+  if (!h) return SC_ERR_ARG;
+  if (!h->cfg.time_average) return fail(h, SC_ERR_STATE, "time_average = 0 in the configuration");
+  for (int d = 0; d < h->P.n_domains; ++d) {
+    int rc = launch_average_add(params_now(h), h->cfg.precision, d, (double*)(h->ws + h->L.dom[d].avg),
+                                h->stream);
+    if (rc) return cuda_fail(h, (cudaError_t)rc, "average launch");
+    ++h->launches;
+  }
+  ++h->avg_samples;
+  return SC_OK;
+}
+
+int sc_lbm_average_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const int32_t* probe_xy,
+                           int n_p, double* prof, float* prof_nodes, double* gpc_coef, int out_host) {
+  if (!h || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (!h->cfg.time_average) return fail(h, SC_ERR_STATE, "time_average = 0 in the configuration");
+  if (h->avg_samples < 1) return fail(h, SC_ERR_STATE, "no samples in the time average");
+  h->avg_read = (const double*)(h->ws + h->L.dom[domain].avg);
+  const int rc = sc_lbm_moments(h, domain, mean, stdev, probe_xy, n_p, prof, prof_nodes, gpc_coef, out_host);
+  h->avg_read = nullptr;
+  return rc;
+}
+
+int sc_lbm_average_field(sc_lbm_t h, int domain, int node, double* d_q) {
+  if (!h || !d_q || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (node < 0 || node >= h->P.dom[domain].nodes) return SC_ERR_ARG;
+  if (!h->cfg.time_average) return fail(h, SC_ERR_STATE, "time_average = 0 in the configuration");
+  if (h->avg_samples < 1) return fail(h, SC_ERR_STATE, "no samples in the time average");
+  const DomLayout& M = h->L.dom[domain];
+  const double* acc = (const double*)(h->ws + M.avg) + (size_t)node * (size_t)M.ncell;
+  int rc = launch_scale(acc, 1.0 / (double)h->avg_samples, d_q, M.ncell, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "average field launch");
+  ++h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_average_samples(sc_lbm_t h, long long* samples) {
+  if (!h || !samples) return SC_ERR_ARG;
+  *samples = h->avg_samples;
+  return SC_OK;
+}
+
+int sc_lbm_qcriterion(sc_lbm_t h, int domain, const float* d_u, float* d_q) {
+  if (!h || !d_u || !d_q || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  int rc = launch_qcriterion(params_now(h), domain, d_u, d_q, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "qcriterion launch");
+  ++h->launches;
+  return SC_OK;
 }
 
 int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u) {

@@ -852,12 +852,18 @@ __global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs 
     for (int a = 0; a < kMaxGpcP; ++a) coef[a] = 0.0;
     if (!(lw & kLinkSolid)) {
       for (int j = 0; j < A.nq; ++j) {
-        T g[kQ];
-        gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
-        T rho, ux, uy, uz;
-        macro<T>(g, rho, ux, uy, uz);
-        if (!(rho > T(0)) || !isfinite(double(ux + uy + uz)) || !isfinite(double(rho))) bad = true;
-        const double q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+        double q;
+        if (A.avg) {
+          q = A.avg[(long long)j * D.ncell + c] * A.avg_scale;
+          if (!isfinite(q)) bad = true;
+        } else {
+          T g[kQ];
+          gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
+          T rho, ux, uy, uz;
+          macro<T>(g, rho, ux, uy, uz);
+          if (!(rho > T(0)) || !isfinite(double(ux + uy + uz)) || !isfinite(double(rho))) bad = true;
+          q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+        }
         const double* ab = A.ab + (long long)j * A.stride;
         const double aq = ab[0] * q;
         s1 += aq;
@@ -898,11 +904,15 @@ __global__ void profiles_kernel(const __grid_constant__ StepParams P, MomentArgs
   for (int j = lane; j < A.nq; j += 32) {
     double q = 0.0;
     if (!(lw & kLinkSolid)) {
-      T g[kQ];
-      gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
-      T rho, ux, uy, uz;
-      macro<T>(g, rho, ux, uy, uz);
-      q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+      if (A.avg) {
+        q = A.avg[(long long)j * D.ncell + c] * A.avg_scale;
+      } else {
+        T g[kQ];
+        gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
+        T rho, ux, uy, uz;
+        macro<T>(g, rho, ux, uy, uz);
+        q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+      }
     }
     if (A.prof_nodes) A.prof_nodes[((long long)p * A.nq + j) * D.nz + z] = float(q);
     const double a = A.ab[(long long)j * A.stride];
@@ -962,6 +972,88 @@ __global__ void export_kernel(const __grid_constant__ StepParams P, int domain, 
 // Count cells whose stored populations sum to a non-finite or non-positive
 // density (layout-independent: the stored 19 values of a cell always carry
 // its density at the current or previous time level).
+// Time average of |u| (the paper's time-averaged velocity magnitude fields,
+// Sec. 2.4 step 6): adds |u| at the current level, per (node, cell), in FP64.
+template <class S, bool SHIFT>
+__global__ void average_add_kernel(const __grid_constant__ StepParams P, int domain, double* avg) {
+  using T = typename Store<S>::C;
+  const DevDomain& D = P.dom[domain];
+  const long long total = D.ncell * D.nodes;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / D.ncell);
+    const long long c = k - (long long)j * D.ncell;
+    const LinkWord lw = __ldg(D.link + c);
+    if (lw & kLinkSolid) continue;
+    const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
+    T g[kQ];
+    gather_pops<S, SHIFT>(P, D, j, P.n_host, x, y, z, c, lw, g);
+    T rho, ux, uy, uz;
+    macro<T>(g, rho, ux, uy, uz);
+    avg[k] += sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+  }
+}
+
+// Q-criterion (the vortex identification of the paper's figures):
+// Q = (|Omega|^2 - |S|^2) / 2 with S and Omega the symmetric and antisymmetric
+// parts of grad u, by central differences (dx = 1) where both neighbours
+// along an axis are fluid, one-sided where one is, zero where none is;
+// periodic axes wrap; solid cells get 0.
+__device__ void qcriterion_cell(const DevDomain& D, const float* __restrict__ u, float* __restrict__ q,
+                                long long c) {
+  if (D.flags[c]) {
+    q[c] = 0.0f;
+    return;
+  }
+  const int xyz[3] = {(int)(c % D.nx), (int)((c / D.nx) % D.ny), (int)(c / ((long long)D.nx * D.ny))};
+  const int dim[3] = {D.nx, D.ny, D.nz};
+  double J[3][3];  // J[i][a] = d u_i / d x_a
+  for (int a = 0; a < 3; ++a) {
+    long long nb[2];
+    bool ok[2];
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      int p[3] = {xyz[0], xyz[1], xyz[2]};
+      p[a] += sgn ? 1 : -1;
+      ok[sgn] = true;
+      if (p[a] < 0 || p[a] >= dim[a]) {
+        if (D.bc[2 * a] == SC_BC_PERIODIC) p[a] = (p[a] + dim[a]) % dim[a];
+        else ok[sgn] = false;
+      }
+      nb[sgn] = ok[sgn] ? cidx(D, p[0], p[1], p[2]) : c;
+      if (ok[sgn] && D.flags[nb[sgn]]) ok[sgn] = false;
+    }
+    for (int i = 0; i < 3; ++i) {
+      const float* ui = u + (long long)i * D.ncell;
+      double d = 0.0;
+      if (ok[0] && ok[1]) d = 0.5 * ((double)ui[nb[1]] - (double)ui[nb[0]]);
+      else if (ok[1]) d = (double)ui[nb[1]] - (double)ui[c];
+      else if (ok[0]) d = (double)ui[c] - (double)ui[nb[0]];
+      J[i][a] = d;
+    }
+  }
+  double s2 = 0.0, w2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double sv = 0.5 * (J[i][a] + J[a][i]), wv = 0.5 * (J[i][a] - J[a][i]);
+      s2 += sv * sv;
+      w2 += wv * wv;
+    }
+  q[c] = (float)(0.5 * (w2 - s2));
+}
+
+__global__ void qcriterion_kernel(const __grid_constant__ StepParams P, int domain, const float* __restrict__ u,
+                                  float* __restrict__ q) {
+  const DevDomain& D = P.dom[domain];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncell;
+       c += (long long)gridDim.x * blockDim.x)
+    qcriterion_cell(D, u, q, c);
+}
+
+__global__ void scale_kernel(const double* __restrict__ in, double sc, double* __restrict__ out, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    out[k] = in[k] * sc;
+}
+
 template <class S, bool SHIFT>
 __global__ void check_kernel(const __grid_constant__ StepParams P, unsigned long long* count) {
   unsigned long long local = 0;
@@ -1177,6 +1269,28 @@ int launch_export(const StepParams& P, int precision, int domain, int node, doub
     export_kernel<S, SH><<<(unsigned)((D.ncell + 255) / 256), 256, 0, s>>>(P, domain, node, d_f, d_u);
     return (int)cudaGetLastError();
   });
+}
+
+int launch_average_add(const StepParams& P, int precision, int domain, double* avg, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevDomain& D = P.dom[domain];
+  return dispatch(precision, [&](auto tag) -> int {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    constexpr bool SH = !std::is_same_v<S, double>;
+    average_add_kernel<S, SH><<<grid_for(D.ncell * D.nodes, 256), 256, 0, s>>>(P, domain, avg);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_scale(const double* in, double s, double* out, long long n, void* stream) {
+  scale_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, s, out, n);
+  return (int)cudaGetLastError();
+}
+
+int launch_qcriterion(const StepParams& P, int domain, const float* u, float* q, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  qcriterion_kernel<<<grid_for(P.dom[domain].ncell, 256), 256, 0, s>>>(P, domain, u, q);
+  return (int)cudaGetLastError();
 }
 
 int launch_check(const StepParams& P, int precision, unsigned long long* d_count, void* stream) {

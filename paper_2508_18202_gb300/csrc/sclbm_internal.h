@@ -178,10 +178,18 @@ struct MomentArgs {
   int n_p;
   double* prof;            // device
   float* prof_nodes;       // device or null
+  const double* avg;       // [nq][ncell] time-accumulated |u|, or null for the current |u|
+  double avg_scale;        // 1 / samples
 };
 int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void* stream);
 int launch_export(const StepParams& P, int precision, int domain, int node, double* d_f,
                   float* d_u, void* stream);
+// Adds |u| of every node of a domain at the current time level to avg[nq][ncell].
+int launch_average_add(const StepParams& P, int precision, int domain, double* avg, void* stream);
+// out[k] = s * in[k], k < n.
+int launch_scale(const double* in, double s, double* out, long long n, void* stream);
+// Q-criterion of a velocity field u[3][ncell] of a domain into q[ncell].
+int launch_qcriterion(const StepParams& P, int domain, const float* u, float* q, void* stream);
 int launch_check(const StepParams& P, int precision, unsigned long long* d_count, void* stream);
 
 // Adjoint of one node's time step (adjoint.cu).

@@ -54,7 +54,7 @@ class sc_lbm_config(C.Structure):
                 ("n_inputs", C.c_int), ("inputs", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("quad_rule", C.c_int), ("ramp_steps", C.c_int),
                 ("precision", C.c_int), ("gpc_degree", C.c_int), ("collision", C.c_int),
-                ("profile", C.c_int), ("z0", C.c_double)]
+                ("profile", C.c_int), ("z0", C.c_double), ("time_average", C.c_int)]
 
 
 class sc_lbm_tuning(C.Structure):
@@ -78,6 +78,12 @@ SIGNATURES = {
     "sc_lbm_step": (C.c_int, [_H, C.c_int]),
     "sc_lbm_moments": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int]),
     "sc_lbm_velocity": (C.c_int, [_H, C.c_int, C.c_int, _P]),
+    "sc_lbm_average_reset": (C.c_int, [_H]),
+    "sc_lbm_average_add": (C.c_int, [_H]),
+    "sc_lbm_average_samples": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
+    "sc_lbm_average_moments": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int]),
+    "sc_lbm_average_field": (C.c_int, [_H, C.c_int, C.c_int, _P]),
+    "sc_lbm_qcriterion": (C.c_int, [_H, C.c_int, _P, _P]),
     "sc_lbm_populations": (C.c_int, [_H, C.c_int, C.c_int, _P]),
     "sc_lbm_autotune": (C.c_int, [_H, C.c_char_p]),
     "sc_lbm_set_tuning": (C.c_int, [_H, C.POINTER(sc_lbm_tuning)]),
@@ -143,7 +149,7 @@ class Config:
 
     def __init__(self, domains, tau0, c_smag, u_ref, alpha, inputs, lo, hi, quad_rule,
                  precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1, collision=SC_COLL_BGK,
-                 profile=SC_PROFILE_POWER, z0=0.1):
+                 profile=SC_PROFILE_POWER, z0=0.1, time_average=0):
         self._doms = (sc_domain_desc * len(domains))()
         self._boxes = []
         for k, d in enumerate(domains):
@@ -173,6 +179,7 @@ class Config:
         c.quad_rule, c.ramp_steps, c.precision, c.gpc_degree = quad_rule, ramp_steps, precision, gpc_degree
         c.collision = collision
         c.profile, c.z0 = profile, z0
+        c.time_average = time_average
         self.c = c
         self.domains = [dict(d) for d in domains]
 
@@ -252,6 +259,40 @@ def sc_lbm_moments(h, domain, mean, std, probes=None, prof=None, prof_nodes=None
 
 def sc_lbm_velocity(h, domain, node, u):
     _call("sc_lbm_velocity", h, domain, node, _ptr(u), handle=h)
+
+
+def sc_lbm_average_reset(h):
+    _call("sc_lbm_average_reset", h, handle=h)
+
+
+def sc_lbm_average_add(h):
+    _call("sc_lbm_average_add", h, handle=h)
+
+
+def sc_lbm_average_samples(h):
+    n = C.c_longlong(0)
+    _call("sc_lbm_average_samples", h, C.byref(n), handle=h)
+    return n.value
+
+
+def sc_lbm_average_moments(h, domain, mean, std, probes=None, prof=None, prof_nodes=None, coef=None,
+                           out_host=False):
+    n_p = 0
+    pp = None
+    if probes is not None:
+        probes = np.ascontiguousarray(np.asarray(probes, np.int32).reshape(-1, 2))
+        n_p = probes.shape[0]
+        pp = probes.ctypes.data
+    _call("sc_lbm_average_moments", h, domain, _ptr(mean), _ptr(std), pp, n_p, _ptr(prof), _ptr(prof_nodes),
+          _ptr(coef), 1 if out_host else 0, handle=h)
+
+
+def sc_lbm_average_field(h, domain, node, q):
+    _call("sc_lbm_average_field", h, domain, node, _ptr(q), handle=h)
+
+
+def sc_lbm_qcriterion(h, domain, u, q):
+    _call("sc_lbm_qcriterion", h, domain, _ptr(u), _ptr(q), handle=h)
 
 
 def sc_lbm_populations(h, domain, node, f):
@@ -399,7 +440,7 @@ class Ensemble:
     def step(self, n):
         sc_lbm_step(self.h, n)
 
-    def moments(self, domain=0, probes=None, nodes_profiles=False, gpc=False):
+    def moments(self, domain=0, probes=None, nodes_profiles=False, gpc=False, _reader=None):
         t = self.torch
         n = self.ncell(domain)
         nz = self.cfg.domains[domain]["nz"]
@@ -414,7 +455,7 @@ class Ensemble:
             from math import comb
             P = comb(self.cfg.c.gpc_degree + self.cfg.c.n_inputs, self.cfg.c.n_inputs)
             coef = self._out(P, n)
-        sc_lbm_moments(self.h, domain, mean, std, probes, prof, pn, coef)
+        (_reader or sc_lbm_moments)(self.h, domain, mean, std, probes, prof, pn, coef)
         self._hand_over(mean, std, prof, pn, coef)
         return dict(mean=mean, std=std, prof=prof, prof_nodes=pn, coef=coef)
 
@@ -423,6 +464,25 @@ class Ensemble:
         sc_lbm_velocity(self.h, domain, node, u)
         self._hand_over(u)
         return u
+
+    def average_moments(self, domain=0, probes=None, nodes_profiles=False, gpc=False):
+        """moments() of the time-averaged |u| fields (configurations with
+        time_average = 1)."""
+        return self.moments(domain, probes, nodes_profiles, gpc, _reader=sc_lbm_average_moments)
+
+    def average_field(self, domain, node):
+        q = self._out(self.ncell(domain))
+        sc_lbm_average_field(self.h, domain, node, q)
+        self._hand_over(q)
+        return q
+
+    def qcriterion(self, domain, u):
+        """Q-criterion of a velocity field u[3][ncell] (device float)."""
+        q = self._out(self.ncell(domain), dtype=self.torch.float32)
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        sc_lbm_qcriterion(self.h, domain, u, q)
+        self._hand_over(q)
+        return q
 
     def populations(self, domain, node):
         f = self._out(19, self.ncell(domain))
@@ -454,7 +514,8 @@ def make_config(workload, **over):
                   w["hi"], w["quad_rule"], w["precision"], ramp_steps=w["ramp_steps"],
                   angle_deg=w.get("angle_deg", 0.0), H_ref=w.get("H_ref", 0.0),
                   gpc_degree=w.get("gpc_degree", -1), collision=w.get("collision", SC_COLL_BGK),
-                  profile=w.get("profile", SC_PROFILE_POWER), z0=w.get("z0", 0.1))
+                  profile=w.get("profile", SC_PROFILE_POWER), z0=w.get("z0", 0.1),
+                  time_average=w.get("time_average", 0))
 
 
 # ------------------------------------------------------------------ assimilation

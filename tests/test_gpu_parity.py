@@ -187,6 +187,68 @@ def test_gaussian_inputs_ensemble_statistics(O, cuda, precision, tol):
     ens.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(W.FP64_PLAIN, 1e-11), (W.FP32_SHIFT, 1e-5)])
+def test_time_averaged_fields(O, cuda, precision, tol):
+    """Time-averaged |u| per node (5 samples, 15 steps apart, after 150
+    steps) and its quadrature statistics against the oracle."""
+    wl = dict(W.CHANNEL_CUBE, precision=precision, time_average=1)
+    ens = S.Ensemble(S.make_config(wl))
+    with pytest.raises(S.ScError):
+        ens.average_field(0, 0)          # no sample yet
+    ens.step(150)
+    S.sc_lbm_average_add(ens.h)          # discarded by the reset below
+    S.sc_lbm_average_reset(ens.h)
+    for k in range(5):
+        if k:
+            ens.step(15)
+        S.sc_lbm_average_add(ens.h)
+    assert S.sc_lbm_average_samples(ens.h) == 5
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    A = O.ensemble_time_average(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, 150, 5, 15)
+    fl = fluid_mask(flags)
+    for j in (0, len(a) - 1):
+        assert rel_l2(ens.average_field(0, j).cpu().numpy()[fl], A[j][fl]) <= tol
+    out = ens.average_moments(0, probes=wl["columns"], gpc=True)
+    mean, std, _ = O.moments_two_pass(a, A)
+    assert rel_l2(out["mean"].cpu().numpy()[fl], mean[fl]) <= tol
+    assert rel_l2(out["std"].cpu().numpy()[fl], std[fl]) <= tol * 10
+    prof, _ = O.profiles(a, A, p.nx, p.ny, p.nz, wl["columns"])
+    assert rel_l2(out["prof"].cpu().numpy(), prof) <= tol * 10
+    ens.close()
+    # configurations without accumulators reject the calls
+    plain = S.Ensemble(S.make_config(W.CHANNEL_CUBE))
+    with pytest.raises(S.ScError) as ei:
+        S.sc_lbm_average_add(plain.h)
+    assert ei.value.code == S.SC_ERR_STATE
+    plain.close()
+
+
+def test_qcriterion(O, cuda):
+    """Q of an exported velocity field of the ragged urban case (solid blocks,
+    velocity, outflow and free-slip faces) against the oracle's stencil, and
+    the closed form Omega^2 of a solid-body rotation around the blocks."""
+    wl = ragged(BC_SETS["urban"])
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(20)
+    u = ens.velocity(0, 1)
+    q = ens.qcriterion(0, u).cpu().numpy()
+    p, flags = oracle_domain(O, wl)
+    bc = wl["domains"][0]["bc"]
+    qo = O.qcriterion(u.cpu().numpy(), flags, p.nx, p.ny, p.nz, bc)
+    assert np.max(np.abs(q - qo)) <= 1e-6 * max(np.max(np.abs(qo)), 1e-30)
+    nx, ny, nz = p.nx, p.ny, p.nz
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    Wr = 0.01
+    ur = np.stack([-Wr * yy.reshape(-1), Wr * xx.reshape(-1), 0.0 * xx.reshape(-1)]).astype(np.float32)
+    qr = ens.qcriterion(0, torch.from_numpy(ur).cuda()).cpu().numpy()
+    fl = fluid_mask(flags)
+    # every fluid cell of this domain has a fluid neighbour along each axis
+    np.testing.assert_allclose(qr[fl], Wr * Wr, rtol=1e-5)
+    assert np.all(qr[~fl] == 0)
+    ens.close()
+
+
 @pytest.mark.parametrize("nx2", [29, 32])
 def test_batched_uneven_domains_match_oracle(O, cuda, nx2):
     """Three domains of different sizes and node counts advance in one launch;
