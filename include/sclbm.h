@@ -133,7 +133,13 @@ typedef struct {
  * logarithmic wind profile with roughness length z0 > 0 in cells (alpha
  * unused).
  * time_average: 1 reserves FP64 accumulators (8 B per cell and node) for the
- * time-averaged |u| fields (sc_lbm_average_*), 0 none.                     */
+ * time-averaged |u| fields (sc_lbm_average_*), 0 none.
+ * node_begin, node_count: the collocation nodes this handle runs, the range
+ * [node_begin, node_begin + node_count) of every domain's rule (node_count 0:
+ * to the end).  The nodes are independent runs (Sec. 2.4 step 5), so an
+ * ensemble shards across processes / GPUs by node ranges; each shard adds
+ * its sc_lbm_moment_sums to the others' and finishes with
+ * sc_lbm_moments_from_sums.  Default 0, 0: all nodes.                       */
 typedef struct {
   int n_domains;
   const sc_domain_desc* domains; /* host, read during calls only */
@@ -150,6 +156,7 @@ typedef struct {
   int profile;
   double z0;
   int time_average;
+  int node_begin, node_count;
 } sc_lbm_config;
 
 /* Launch shape of the stream-collide kernels (chosen by sc_lbm_autotune or
@@ -248,6 +255,19 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev,
 /* Velocity of one node at the current time: d_u device float [3][ncell],
  * solid cells 0.                                                            */
 int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u);
+
+/* Sharded ensembles: the raw FP64 sums of the handle's nodes,
+ * d_s1 = sum_j a_j Q_j, d_s2 = sum_j a_j Q_j^2 (device double [ncell]) and,
+ * if d_gpc_sums is not NULL, sum_j a_j Q_j Phi_alpha(Z_j) ([P][ncell]);
+ * sc_lbm_weight_sum gives the handle's sum_j a_j (host).  After the shards'
+ * sums and weight sums are added (an all-reduce), sc_lbm_moments_from_sums
+ * writes mean = S1 / W and std = sqrt(max(S2 / W - mean^2, 0)) (Eq.
+ * quad_moments) into d_mean, d_stdev (device double [ncell]).  The gPC
+ * coefficients are the summed gPC sums themselves.  Asynchronous.          */
+int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, double* d_gpc_sums);
+int sc_lbm_weight_sum(sc_lbm_t h, int domain, double* wsum);
+int sc_lbm_moments_from_sums(sc_lbm_t h, int domain, const double* d_s1, const double* d_s2, double wsum,
+                             double* d_mean, double* d_stdev);
 
 /* Time-averaged velocity magnitude fields (Sec. 2.4 step 6, the paper's
  * time-averaged QoI), for configurations with time_average = 1 (else

@@ -86,6 +86,7 @@ int validate(const sc_lbm_config* c, std::string& why) {
   if (c->gpc_degree > 8) { why = "gpc_degree too large"; return SC_ERR_UNSUPPORTED; }
   if (c->collision != SC_COLL_BGK && c->collision != SC_COLL_RR) { why = "bad collision"; return SC_ERR_ARG; }
   if (c->time_average != 0 && c->time_average != 1) { why = "time_average must be 0 or 1"; return SC_ERR_ARG; }
+  if (c->node_begin < 0 || c->node_count < 0) { why = "node range must be non-negative"; return SC_ERR_ARG; }
   if (c->gpc_degree >= 0 && hn_gpc_size(c->n_inputs, c->gpc_degree) > kMaxGpcP) {
     why = "gPC basis larger than " + std::to_string(kMaxGpcP);
     return SC_ERR_UNSUPPORTED;
@@ -122,6 +123,20 @@ int node_count(const sc_lbm_config* c, int d, std::vector<double>* Z, std::vecto
   return (int)ww.size();
 }
 
+// The collocation nodes a handle runs: [node_begin, node_begin + node_count)
+// of the full rule (node_count 0: to the end).  Ranks of a sharded ensemble
+// each run one such range and add their moment sums.
+int shard_nodes(const sc_lbm_config* c, int d, std::vector<double>* Z, std::vector<double>* w) {
+  std::vector<double> z, ww;
+  const int n = node_count(c, d, &z, &ww);
+  if (n < 0) return -1;
+  const int b = c->node_begin, cnt = c->node_count > 0 ? c->node_count : n - c->node_begin;
+  if (b < 0 || b >= n || cnt < 1 || b + cnt > n) return -1;
+  if (Z) Z->assign(z.begin() + (size_t)b * c->n_inputs, z.begin() + (size_t)(b + cnt) * c->n_inputs);
+  if (w) w->assign(ww.begin() + b, ww.begin() + b + cnt);
+  return cnt;
+}
+
 int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
   int rc = validate(c, why);
   if (rc) return rc;
@@ -142,7 +157,8 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
   for (int d = 0; d < c->n_domains; ++d) {
     const sc_domain_desc& D = c->domains[d];
     DomLayout& M = L.dom[d];
-    M.nq = node_count(c, d, nullptr, nullptr);
+    M.nq = shard_nodes(c, d, nullptr, nullptr);
+    if (M.nq < 0) { why = "node range outside the quadrature rule"; return SC_ERR_ARG; }
     if (M.nq < 1) { why = "quadrature level not supported"; return SC_ERR_ARG; }
     if (M.nq > SC_MAX_NODES) { why = "too many collocation nodes"; return SC_ERR_UNSUPPORTED; }
     M.P = P;
@@ -647,7 +663,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     }
     hn_listed_links(D, flags[d].data(), links[d], bcells[d], L.dom[d].pitch, ltabs[d]);
     std::vector<double> Z, w;
-    node_count(&c, d, &Z, &w);
+    shard_nodes(&c, d, &Z, &w);
     const int nq = (int)w.size();
     h->nq[d] = nq;
     h->Z.push_back(Z);
@@ -803,6 +819,7 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   A.prof_nodes = out_host ? (prof_nodes ? (float*)(h->ws + L.st_pnodes) : nullptr) : prof_nodes;
   A.avg = h->avg_read;
   A.avg_scale = h->avg_samples > 0 ? 1.0 / (double)h->avg_samples : 0.0;
+  A.raw = 0;
   if (n_p > 0)
     CK(cudaMemcpyAsync(h->ws + L.probes, probe_xy, sizeof(int32_t) * 2 * n_p, cudaMemcpyHostToDevice,
                        h->stream));
@@ -825,6 +842,48 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   rc = read_err(h, &bits);
   if (rc) return rc;
   return err_status(h, bits);
+}
+
+int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, double* d_gpc_sums) {
+  if (!h || !d_s1 || !d_s2 || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (d_gpc_sums && h->gpcP == 0) return fail(h, SC_ERR_ARG, "gpc_degree < 0 in the configuration");
+  MomentArgs A;
+  A.domain = domain;
+  A.ab = (const double*)(h->ws + h->L.dom[domain].ab);
+  A.nq = h->nq[domain];
+  A.stride = h->gpcP + 1;
+  A.P = d_gpc_sums ? h->gpcP : 0;
+  A.wsum = h->wsum[domain];
+  A.mean = d_s1;
+  A.stdev = d_s2;
+  A.coef = d_gpc_sums;
+  A.probes = nullptr;
+  A.n_p = 0;
+  A.prof = nullptr;
+  A.prof_nodes = nullptr;
+  A.avg = nullptr;
+  A.avg_scale = 0.0;
+  A.raw = 1;
+  int rc = launch_moments(params_now(h), h->cfg.precision, A, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "moment sums launch");
+  ++h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_weight_sum(sc_lbm_t h, int domain, double* wsum) {
+  if (!h || !wsum || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  *wsum = h->wsum[domain];
+  return SC_OK;
+}
+
+int sc_lbm_moments_from_sums(sc_lbm_t h, int domain, const double* d_s1, const double* d_s2, double wsum,
+                             double* d_mean, double* d_stdev) {
+  if (!h || !d_s1 || !d_s2 || !d_mean || !d_stdev || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (!(wsum > 0.0)) return fail(h, SC_ERR_ARG, "weight sum must be positive");
+  int rc = launch_finalize_moments(d_s1, d_s2, wsum, d_mean, d_stdev, h->P.dom[domain].ncell, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "finalize launch");
+  ++h->launches;
+  return SC_OK;
 }
 
 int sc_lbm_average_reset(sc_lbm_t h) {

@@ -873,11 +873,16 @@ __global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs 
           if (a < A.P) coef[a] += ab[1 + a] * q;
       }
     }
-    const double mean = s1 / A.wsum;
-    double var = s2 / A.wsum - mean * mean;
-    if (var < 0.0) var = 0.0;
-    A.mean[c] = mean;
-    A.stdev[c] = sqrt(var);
+    if (A.raw) {
+      A.mean[c] = s1;
+      A.stdev[c] = s2;
+    } else {
+      const double mean = s1 / A.wsum;
+      double var = s2 / A.wsum - mean * mean;
+      if (var < 0.0) var = 0.0;
+      A.mean[c] = mean;
+      A.stdev[c] = sqrt(var);
+    }
     if (A.coef)
       for (int a = 0; a < A.P; ++a) A.coef[(long long)a * D.ncell + c] = coef[a];
   }
@@ -1047,6 +1052,19 @@ __global__ void qcriterion_kernel(const __grid_constant__ StepParams P, int doma
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncell;
        c += (long long)gridDim.x * blockDim.x)
     qcriterion_cell(D, u, q, c);
+}
+
+// The quadrature moments from (possibly all-reduced) sums, as the moment
+// kernel finishes them.
+__global__ void finalize_moments_kernel(const double* __restrict__ s1, const double* __restrict__ s2, double wsum,
+                                        double* __restrict__ mean, double* __restrict__ stdev, long long n) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double m = s1[c] / wsum;
+    double var = s2[c] / wsum - m * m;
+    if (var < 0.0) var = 0.0;
+    mean[c] = m;
+    stdev[c] = sqrt(var);
+  }
 }
 
 __global__ void scale_kernel(const double* __restrict__ in, double sc, double* __restrict__ out, long long n) {
@@ -1280,6 +1298,12 @@ int launch_average_add(const StepParams& P, int precision, int domain, double* a
     average_add_kernel<S, SH><<<grid_for(D.ncell * D.nodes, 256), 256, 0, s>>>(P, domain, avg);
     return (int)cudaGetLastError();
   });
+}
+
+int launch_finalize_moments(const double* s1, const double* s2, double wsum, double* mean, double* stdev,
+                            long long n, void* stream) {
+  finalize_moments_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(s1, s2, wsum, mean, stdev, n);
+  return (int)cudaGetLastError();
 }
 
 int launch_scale(const double* in, double s, double* out, long long n, void* stream) {

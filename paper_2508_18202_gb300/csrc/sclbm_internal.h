@@ -180,12 +180,16 @@ struct MomentArgs {
   float* prof_nodes;       // device or null
   const double* avg;       // [nq][ncell] time-accumulated |u|, or null for the current |u|
   double avg_scale;        // 1 / samples
+  int raw;                 // 1: write the sums S1, S2 (and gPC sums) into mean / stdev / coef
 };
 int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void* stream);
 int launch_export(const StepParams& P, int precision, int domain, int node, double* d_f,
                   float* d_u, void* stream);
 // Adds |u| of every node of a domain at the current time level to avg[nq][ncell].
 int launch_average_add(const StepParams& P, int precision, int domain, double* avg, void* stream);
+// mean = s1 / wsum, stdev = sqrt(max(s2 / wsum - mean^2, 0)), n cells.
+int launch_finalize_moments(const double* s1, const double* s2, double wsum, double* mean, double* stdev,
+                            long long n, void* stream);
 // out[k] = s * in[k], k < n.
 int launch_scale(const double* in, double s, double* out, long long n, void* stream);
 // Q-criterion of a velocity field u[3][ncell] of a domain into q[ncell].

@@ -54,7 +54,8 @@ class sc_lbm_config(C.Structure):
                 ("n_inputs", C.c_int), ("inputs", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("quad_rule", C.c_int), ("ramp_steps", C.c_int),
                 ("precision", C.c_int), ("gpc_degree", C.c_int), ("collision", C.c_int),
-                ("profile", C.c_int), ("z0", C.c_double), ("time_average", C.c_int)]
+                ("profile", C.c_int), ("z0", C.c_double), ("time_average", C.c_int),
+                ("node_begin", C.c_int), ("node_count", C.c_int)]
 
 
 class sc_lbm_tuning(C.Structure):
@@ -78,6 +79,9 @@ SIGNATURES = {
     "sc_lbm_step": (C.c_int, [_H, C.c_int]),
     "sc_lbm_moments": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int]),
     "sc_lbm_velocity": (C.c_int, [_H, C.c_int, C.c_int, _P]),
+    "sc_lbm_moment_sums": (C.c_int, [_H, C.c_int, _P, _P, _P]),
+    "sc_lbm_weight_sum": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
+    "sc_lbm_moments_from_sums": (C.c_int, [_H, C.c_int, _P, _P, C.c_double, _P, _P]),
     "sc_lbm_average_reset": (C.c_int, [_H]),
     "sc_lbm_average_add": (C.c_int, [_H]),
     "sc_lbm_average_samples": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
@@ -149,7 +153,7 @@ class Config:
 
     def __init__(self, domains, tau0, c_smag, u_ref, alpha, inputs, lo, hi, quad_rule,
                  precision, ramp_steps=0, angle_deg=0.0, H_ref=0.0, gpc_degree=-1, collision=SC_COLL_BGK,
-                 profile=SC_PROFILE_POWER, z0=0.1, time_average=0):
+                 profile=SC_PROFILE_POWER, z0=0.1, time_average=0, node_begin=0, node_count=0):
         self._doms = (sc_domain_desc * len(domains))()
         self._boxes = []
         for k, d in enumerate(domains):
@@ -180,6 +184,7 @@ class Config:
         c.collision = collision
         c.profile, c.z0 = profile, z0
         c.time_average = time_average
+        c.node_begin, c.node_count = node_begin, node_count
         self.c = c
         self.domains = [dict(d) for d in domains]
 
@@ -259,6 +264,32 @@ def sc_lbm_moments(h, domain, mean, std, probes=None, prof=None, prof_nodes=None
 
 def sc_lbm_velocity(h, domain, node, u):
     _call("sc_lbm_velocity", h, domain, node, _ptr(u), handle=h)
+
+
+def sc_lbm_moment_sums(h, domain, s1, s2, gpc_sums=None):
+    _call("sc_lbm_moment_sums", h, domain, _ptr(s1), _ptr(s2), _ptr(gpc_sums), handle=h)
+
+
+def sc_lbm_weight_sum(h, domain):
+    w = C.c_double(0.0)
+    _call("sc_lbm_weight_sum", h, domain, C.byref(w), handle=h)
+    return w.value
+
+
+def sc_lbm_moments_from_sums(h, domain, s1, s2, wsum, mean, std):
+    _call("sc_lbm_moments_from_sums", h, domain, _ptr(s1), _ptr(s2), float(wsum), _ptr(mean), _ptr(std),
+          handle=h)
+
+
+def shard_nodes(n_nodes, world, rank):
+    """Contiguous, balanced node range (begin, count) of `rank` among `world`
+    shards of an n_nodes rule (the first n_nodes % world shards take one
+    more node)."""
+    if not (0 <= rank < world) or n_nodes < world:
+        raise ValueError("need 0 <= rank < world <= n_nodes")
+    base, extra = divmod(n_nodes, world)
+    begin = rank * base + min(rank, extra)
+    return begin, base + (1 if rank < extra else 0)
 
 
 def sc_lbm_average_reset(h):
@@ -416,7 +447,10 @@ class Ensemble:
         with torch.cuda.stream(self.stream):
             self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         self.h = sc_lbm_init(cfg, self.ws.data_ptr(), self.nbytes, self.stream.cuda_stream, flags_host)
-        self.n_nodes = [sc_lbm_quadrature(cfg, d)[1].size for d in range(cfg.c.n_domains)]
+        # nodes this handle runs (its node range of every domain's rule)
+        full = [sc_lbm_quadrature(cfg, d)[1].size for d in range(cfg.c.n_domains)]
+        b, c = cfg.c.node_begin, cfg.c.node_count
+        self.n_nodes = [c if c > 0 else n - b for n in full]
 
     def _out(self, *shape, dtype=None):
         with self.torch.cuda.stream(self.stream):
@@ -464,6 +498,31 @@ class Ensemble:
         sc_lbm_velocity(self.h, domain, node, u)
         self._hand_over(u)
         return u
+
+    def sharded_moments(self, domain=0, group=None, gpc=False):
+        """Quadrature mean / std (and gPC coefficients) of an ensemble whose
+        nodes are sharded over the processes of a torch.distributed group:
+        this handle's moment sums and weight sum are all-reduced (sum), then
+        finished by the library."""
+        t = self.torch
+        import torch.distributed as dist
+        n = self.ncell(domain)
+        s1, s2 = self._out(n), self._out(n)
+        gs = None
+        if gpc:
+            from math import comb
+            gs = self._out(comb(self.cfg.c.gpc_degree + self.cfg.c.n_inputs, self.cfg.c.n_inputs), n)
+        sc_lbm_moment_sums(self.h, domain, s1, s2, gs)
+        self._hand_over(s1, s2, gs)
+        w = t.tensor([sc_lbm_weight_sum(self.h, domain)], dtype=t.float64, device=s1.device)
+        for x in (s1, s2, gs, w):
+            if x is not None:
+                dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
+        mean, std = self._out(n), self._out(n)
+        self.stream.wait_stream(t.cuda.current_stream(self.device))
+        sc_lbm_moments_from_sums(self.h, domain, s1, s2, float(w.item()), mean, std)
+        self._hand_over(mean, std)
+        return dict(mean=mean, std=std, coef=gs)
 
     def average_moments(self, domain=0, probes=None, nodes_profiles=False, gpc=False):
         """moments() of the time-averaged |u| fields (configurations with
@@ -515,7 +574,8 @@ def make_config(workload, **over):
                   angle_deg=w.get("angle_deg", 0.0), H_ref=w.get("H_ref", 0.0),
                   gpc_degree=w.get("gpc_degree", -1), collision=w.get("collision", SC_COLL_BGK),
                   profile=w.get("profile", SC_PROFILE_POWER), z0=w.get("z0", 0.1),
-                  time_average=w.get("time_average", 0))
+                  time_average=w.get("time_average", 0), node_begin=w.get("node_begin", 0),
+                  node_count=w.get("node_count", 0))
 
 
 # ------------------------------------------------------------------ assimilation

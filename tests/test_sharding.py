@@ -1,0 +1,143 @@
+"""Node-sharded ensembles (the path's multi-process form): the collocation
+nodes are independent runs (Sec. 2.4 step 5), so an ensemble splits into
+contiguous node ranges, one per process, whose moment sums S1 = sum a_j Q_j,
+S2 = sum a_j Q_j^2 and weight sums are added by an all-reduce and finished as
+mean = S1/W, var = S2/W - mean^2 (Eq. quad_moments).
+
+CPU tests: the partition, the configuration checks, and a world-size-2 gloo
+run of the exchange on oracle shards against the unsharded oracle moments.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2508_18202_gb300 import sclbm as S
+from paper_2508_18202_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 13, 29, 69, 121])
+def test_shard_partition_covers_the_rule(n):
+    for world in range(1, min(n, 9) + 1):
+        ranges = [S.shard_nodes(n, world, r) for r in range(world)]
+        assert ranges[0][0] == 0
+        for (b0, c0), (b1, _) in zip(ranges, ranges[1:]):
+            assert b0 + c0 == b1
+        assert sum(c for _, c in ranges) == n
+        assert max(c for _, c in ranges) - min(c for _, c in ranges) <= 1
+    with pytest.raises(ValueError):
+        S.shard_nodes(3, 4, 0)
+
+
+def test_node_range_checked():
+    wl = W.URBAN_LES   # 13 nodes
+    assert S.sc_lbm_workspace_size(S.make_config(wl, node_begin=5, node_count=8)) < \
+        S.sc_lbm_workspace_size(S.make_config(wl))
+    for b, c in ((13, 0), (5, 9), (-1, 2)):
+        with pytest.raises(S.ScError) as ei:
+            S.sc_lbm_workspace_size(S.make_config(wl, node_begin=b, node_count=c))
+        assert ei.value.code == S.SC_ERR_ARG
+    Z, a = S.sc_lbm_quadrature(S.make_config(wl, node_begin=5, node_count=8), 0)
+    assert len(a) == 13   # the rule itself is always reported whole
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    from oracle import oracle as O
+    from helpers import oracle_domain, oracle_nodes
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    O.set_threads(1)
+    wl = dict(W.CHANNEL_CUBE, domains=[dict(nx=24, ny=12, nz=12, boxes=[[6, 4, 0, 10, 8, 6]],
+                                            bc=W.CHANNEL_BC, quad_level=5)], steps=40)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    b, c = S.shard_nodes(len(a), world, rank)
+    Q = O.ensemble(p, flags, Z[b:b + c], wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, wl["steps"])
+    w = a[b:b + c]
+    s1 = torch.from_numpy(w @ Q)
+    s2 = torch.from_numpy(w @ (Q * Q))
+    ws = torch.tensor([w.sum()], dtype=torch.float64)
+    for t in (s1, s2, ws):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    mean = s1.numpy() / ws.item()
+    std = np.sqrt(np.maximum(s2.numpy() / ws.item() - mean * mean, 0.0))
+    if rank == 0:
+        Qa = O.ensemble(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, wl["steps"])
+        m_ref, s_ref, _ = O.moments_two_pass(a, Qa)
+        np.savez(out_path, mean=mean, std=std, m_ref=m_ref, s_ref=s_ref)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_two_rank_exchange(tmp_path):
+    """Two gloo ranks run their node shards, all-reduce the sums and finish
+    the moments; the result equals the unsharded oracle moments."""
+    import sys
+    import torch.multiprocessing as mp
+    here = os.path.dirname(os.path.abspath(__file__))
+    sys.path.insert(0, here)
+    out = str(tmp_path / "moments.npz")
+    mp.start_processes(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    r = np.load(out)
+    assert np.max(np.abs(r["mean"] - r["m_ref"])) < 1e-14
+    assert np.max(np.abs(r["std"] - r["s_ref"])) < 1e-9
+
+
+@pytest.mark.gpu
+def test_shards_on_one_gpu_match_the_whole_ensemble():
+    """Two node-range handles on one GPU (an all-reduce emulated by adding
+    their sums) reproduce the whole ensemble's moments and gPC coefficients;
+    a one-process NCCL group runs the same exchange through sharded_moments."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = dict(W.CHANNEL_CUBE, precision=W.FP32_SHIFT)
+    full = S.Ensemble(S.make_config(wl))
+    full.step(120)
+    ref = full.moments(0, gpc=True)
+    n = full.ncell(0)
+    s1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s2 = torch.zeros_like(s1)
+    gs = torch.zeros((5, n), dtype=torch.float64, device="cuda")
+    wsum = 0.0
+    for r in range(2):
+        b, c = S.shard_nodes(5, 2, r)
+        sh = S.Ensemble(S.make_config(wl, node_begin=b, node_count=c))
+        assert sh.n_nodes[0] == c
+        sh.step(120)
+        a1, a2, ag = (torch.empty_like(x) for x in (s1, s2, gs))
+        S.sc_lbm_moment_sums(sh.h, 0, a1, a2, ag)
+        sh.sync()
+        s1 += a1
+        s2 += a2
+        gs += ag
+        wsum += S.sc_lbm_weight_sum(sh.h, 0)
+        sh.close()
+    mean, std = torch.empty_like(s1), torch.empty_like(s1)
+    S.sc_lbm_moments_from_sums(full.h, 0, s1, s2, wsum, mean, std)
+    full.sync()
+    assert torch.max(torch.abs(mean - ref["mean"])).item() < 1e-12
+    assert torch.max(torch.abs(std - ref["std"])).item() < 1e-9
+    assert torch.max(torch.abs(gs - ref["coef"])).item() < 1e-12
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(_free_port())
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        out = full.sharded_moments(0, gpc=True)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(out["mean"] - ref["mean"])).item() < 1e-12
+        assert torch.max(torch.abs(out["coef"] - ref["coef"])).item() < 1e-12
+    finally:
+        dist.destroy_process_group()
+    full.close()
