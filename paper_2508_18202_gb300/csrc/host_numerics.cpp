@@ -581,6 +581,7 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
     const LinkWord lw = link[(size_t)idx];
     ListedLinks& L = tab[k];
     memset(&L, 0, sizeof(L));
+    L.z = z;
     for (int i = 0; i < kQ; ++i) {
       const long long own = (long long)i * pitch + idx;
       long long src = own;

@@ -254,11 +254,12 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   const long long k = item - D.bitem_begin;
   const int node = (int)(k / D.nb);
   const long long li = k % D.nb;
+  // every load below depends only on the record's words, so the cell costs
+  // two rounds of memory latency (words, then populations and inflow)
   const ListedRef L = listed_ref(D, li);
-  const int z = (int)(__ldg(D.bcell + li) / ((long long)D.nx * D.ny));
   const Node<S> N = node_view<S>(D, node);
-  T ux = T(0), uy = T(0), uz = T(0);
-  if (L.word(kWordPullMove) | L.word(kWordPushMove)) inflow_velocity<S>(N, z, ux, uy, uz);
+  T ux, uy, uz;
+  inflow_velocity<S>(N, L.word(kWordZ), ux, uy, uz);
   T g[kQ];
   listed_pull<S, CG>(L, N.g, N.bout, ux, uy, uz, T(r), g);
   collide_p<T, true>(P, g);

@@ -67,7 +67,8 @@ struct alignas(16) ListedLinks {
   uint32_t bout_mask;                                  // bit i: src[i] is in the outflow plane
   uint32_t pull_move;                                  // bit i: pull of link i adds 6 w_i (c_i.u) r
   uint32_t push_move;                                  // bit j: delivery of f*_j adds the term of opp(j)
-  uint32_t pad[3];
+  int32_t z;                                           // the cell's layer (inflow table row)
+  uint32_t pad[2];
 };
 static_assert(sizeof(ListedLinks) == 256, "ListedLinks is 256 bytes");
 // On the device the records are stored transposed, word w of listed cell li at
@@ -77,6 +78,7 @@ constexpr int kListedWords = (int)(sizeof(ListedLinks) / 4);
 constexpr int kWordSrc = 0, kWordDst = kQ, kWordExtra = 2 * kQ;
 constexpr int kWordBoutMask = 2 * kQ + kOutletPops * kOutletCopies;
 constexpr int kWordPullMove = kWordBoutMask + 1, kWordPushMove = kWordBoutMask + 2;
+constexpr int kWordZ = kWordBoutMask + 3;
 
 // Per-domain view handed to the kernels (plain pointers into the workspace).
 struct DevDomain {
