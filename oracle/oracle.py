@@ -416,3 +416,77 @@ def ensemble_time_average(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_war
             A[j] += velocity_magnitude(u, flags)
         A[j] /= n_samples
     return A
+
+
+def unwrap_directions(dir_deg):
+    """Directions of a series of targets made continuous: each step from one
+    target to the next is taken along the shorter arc, in (-180, 180] read
+    as [-180, 180) (a half turn goes clockwise, negative)."""
+    d = [float(dir_deg[0])]
+    for k in range(1, len(dir_deg)):
+        step = (float(dir_deg[k]) - float(dir_deg[k - 1]) + 180.0) % 360.0 - 180.0
+        d.append(d[-1] + step)
+    return d
+
+
+def series_at(speed, dir_deg, steps_per_target, interp_steps, m):
+    """Wind speed factor s(m) and direction offset delta(m) (degrees) of the
+    inflow at time level m under a series of targets (Sec. 2.2: the boundary
+    velocity is moved from one target magnitude and direction to the next
+    over an interpolation interval; Sec. 2.4 step 1 and Sec. 3: one target
+    per hour of measurements).
+
+    Target 0 holds from level 0.  Target k >= 1 takes over at level
+    k * steps_per_target: over the following interp_steps levels magnitude
+    and direction move linearly from target k - 1 to target k, lam =
+    min(o, interp_steps) / interp_steps at offset o into the interval (lam =
+    1 at once when interp_steps = 0); then target k holds until the next one
+    takes over.  After the last target the series holds it."""
+    K = len(speed)
+    D = unwrap_directions(dir_deg)
+    k = m // steps_per_target
+    if k <= 0:
+        return float(speed[0]), D[0]
+    if k >= K:
+        return float(speed[K - 1]), D[K - 1]
+    o = m - k * steps_per_target
+    lam = 1.0 if interp_steps == 0 else min(o, interp_steps) / interp_steps
+    return (float(speed[k - 1]) + lam * (float(speed[k]) - float(speed[k - 1])),
+            D[k - 1] + lam * (D[k] - D[k - 1]))
+
+
+def run_series(p, flags, f, n0, n_steps, inflow_at):
+    """Advance f by n_steps from level n0 with an inflow that changes from
+    level to level: inflow_at(m) is uin[nz][3] of arrival level m, start-up
+    ramp included (the stepping itself is run() with no ramp)."""
+    q = params(p.nx, p.ny, p.nz, list(p.bc), p.tau0, p.csmag, 0, tuple(p.force), p.collision)
+    for s in range(n_steps):
+        m = n0 + s + 1
+        run(q, flags, inflow_at(m), f, m - 1, 1)
+    return f
+
+
+def ensemble_series(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, series, z0=None):
+    """The ensemble of ensemble() under a time-varying inflow (Sec. 3): at
+    node j and arrival level m the profile is that of reference speed
+    u_ref * s(m) and direction theta + delta(m) with the node's perturbations
+    (speed factor 1 + xi, direction offset) applied on top, times the ramp
+    r(m).  series = (speed, dir_deg, steps_per_target, interp_steps).
+    Returns u[nq][3][ncell]."""
+    speed, dirs, per, interp = series
+    out = []
+    for j in range(Z.shape[0]):
+        xi, al, th = node_inflow_params(Z[j], inputs, u_ref, alpha, theta_deg)
+
+        def inflow_at(m, xi=xi, al=al, th=th):
+            s, d = series_at(speed, dirs, per, interp, m)
+            if z0 is None:
+                prof = inflow(p.nz, u_ref * s, xi, al, H, th + d)
+            else:
+                prof = inflow_log(p.nz, u_ref * s, xi, z0, H, th + d)
+            return ramp(p.ramp_steps, m) * np.asarray(prof)
+
+        f = init_equilibrium(p, flags)
+        run_series(p, flags, f, 0, n_steps, inflow_at)
+        out.append(macros(p, flags, f)[1])
+    return np.array(out)
