@@ -67,6 +67,7 @@ def lib():
         L.oc_splitmix64.argtypes = [C.c_uint64, C.c_int, np.ctypeslib.ndpointer(dtype=np.uint64)]
         L.oc_geometry.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int,
                                   C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, u8]
+        L.oc_mark_mantle.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, u8]
         L.oc_probe_columns.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, u8, C.c_int, i32]
         L.oc_probe_points.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, u8, C.c_int, i32]
         L.oc_inflow.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -168,7 +169,9 @@ def splitmix64(seed, n):
 
 
 def geometry(nx, ny, nz, seed=0, n_buildings=0, fp_min=1, fp_max=1, h_min=1, h_max=1,
-             boxes=None):
+             boxes=None, disk_radius=0.0):
+    """Solid flags (1) of the buildings; with disk_radius > 0 the cells beyond
+    the circular mantle get flag 2 (Sec. 2.2 circular domain)."""
     flags = np.zeros(nx * ny * nz, np.uint8)
     nb = 0
     bptr = None
@@ -178,6 +181,8 @@ def geometry(nx, ny, nz, seed=0, n_buildings=0, fp_min=1, fp_max=1, h_min=1, h_m
         bptr = b.ctypes.data
     _chk(lib().oc_geometry(nx, ny, nz, C.c_uint64(seed), n_buildings, fp_min, fp_max, h_min,
                            h_max, bptr, nb, flags), "geometry")
+    if disk_radius > 0:
+        _chk(lib().oc_mark_mantle(nx, ny, nz, float(disk_radius), flags), "mark_mantle")
     return flags
 
 
@@ -466,15 +471,16 @@ def run_series(p, flags, f, n0, n_steps, inflow_at):
     return f
 
 
-def ensemble_series(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, series, z0=None):
+def ensemble_series(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, series, z0=None,
+                    keep_f=False):
     """The ensemble of ensemble() under a time-varying inflow (Sec. 3): at
     node j and arrival level m the profile is that of reference speed
     u_ref * s(m) and direction theta + delta(m) with the node's perturbations
     (speed factor 1 + xi, direction offset) applied on top, times the ramp
     r(m).  series = (speed, dir_deg, steps_per_target, interp_steps).
-    Returns u[nq][3][ncell]."""
+    Returns u[nq][3][ncell] (and f[nq][19][ncell] with keep_f)."""
     speed, dirs, per, interp = series
-    out = []
+    out, fs = [], []
     for j in range(Z.shape[0]):
         xi, al, th = node_inflow_params(Z[j], inputs, u_ref, alpha, theta_deg)
 
@@ -489,4 +495,6 @@ def ensemble_series(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, se
         f = init_equilibrium(p, flags)
         run_series(p, flags, f, 0, n_steps, inflow_at)
         out.append(macros(p, flags, f)[1])
-    return np.array(out)
+        if keep_f:
+            fs.append(f)
+    return (np.array(out), np.array(fs)) if keep_f else np.array(out)

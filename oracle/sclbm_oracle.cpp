@@ -56,6 +56,7 @@ const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1}
 const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 
 enum { VELOCITY = 0, OUTFLOW = 1, BOUNCE_BACK = 2, FREE_SLIP = 3, PERIODIC = 4 };
+constexpr uint8_t MANTLE = 2;  // cell flag: beyond the circular domain's mantle
 
 double weight(int i) {
   int c2 = CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i];
@@ -356,6 +357,8 @@ bool is_periodic_axis(const oc_params* p, int a) { return p->bc[2 * a] == PERIOD
 //   source p = x - c_i (periodic axes wrapped);
 //   p inside and fluid            -> f*_i(p)                   (streaming)
 //   p inside and solid            -> f*_opp(i)(x)              (bounce-back)
+//   p inside and beyond the mantle (flag 2, the circular domain's local
+//     velocity boundary)          -> the VELOCITY rule below
 //   p across exactly one face of kind
 //     BOUNCE_BACK                 -> f*_opp(i)(x)
 //     VELOCITY                    -> f*_opp(i)(x) + 6 w_i rho_w (c_i . u_w(z)) r(m)
@@ -372,6 +375,15 @@ bool is_periodic_axis(const oc_params* p, int a) { return p->bc[2 * a] == PERIOD
 //                                    crossed (FREE_SLIP + FREE_SLIP is thus
 //                                    bounce-back, OUTFLOW + FREE_SLIP a
 //                                    reflection in the cell itself).
+// The moving-wall rule of a velocity boundary: f*_opp(i)(x) + 6 w_i
+// (c_i . u_w(z)) r(m), rho_w = 1.
+template <class T>
+T velocity_link(const T* fpost, const Lat& L, const T* uin, double r, long long xi, int z, int i) {
+  T cu = T((double)CX[i]) * uin[3 * z + 0] + T((double)CY[i]) * uin[3 * z + 1] +
+         T((double)CZ[i]) * uin[3 * z + 2];
+  return fpost[(long long)opposite(i) * L.ncell + xi] + T(6.0 * weight(i) * r) * cu;
+}
+
 template <class T>
 T pull(const Lat& L, const uint8_t* flags, const T* fpost, const T* uin, double r,
        int x, int y, int z, int i) {
@@ -394,6 +406,7 @@ T pull(const Lat& L, const uint8_t* flags, const T* fpost, const T* uin, double 
   if (nc == 0) {
     long long si = L.idx(s[0], s[1], s[2]);
     if (flags[si] == 0) return fpost[(long long)i * L.ncell + si];
+    if (flags[si] == MANTLE) return velocity_link(fpost, L, uin, r, xi, z, i);
     return fpost[(long long)oi * L.ncell + xi];
   }
   int kind;
@@ -414,11 +427,7 @@ T pull(const Lat& L, const uint8_t* flags, const T* fpost, const T* uin, double 
     kind = bb ? BOUNCE_BACK : VELOCITY;
   }
   if (kind == BOUNCE_BACK) return fpost[(long long)oi * L.ncell + xi];
-  if (kind == VELOCITY) {
-    T cu = T((double)CX[i]) * uin[3 * z + 0] + T((double)CY[i]) * uin[3 * z + 1] +
-           T((double)CZ[i]) * uin[3 * z + 2];
-    return fpost[(long long)oi * L.ncell + xi] + T(6.0 * weight(i) * r) * cu;
-  }
+  if (kind == VELOCITY) return velocity_link(fpost, L, uin, r, xi, z, i);
   // single face: FREE_SLIP or OUTFLOW; s = x - c_i with the normal component removed
   const int a = crossed[0] / 2;
   int src[3] = {xc[0] - CX[i], xc[1] - CY[i], xc[2] - CZ[i]};
@@ -428,6 +437,7 @@ T pull(const Lat& L, const uint8_t* flags, const T* fpost, const T* uin, double 
   long long si = L.idx(src[0], src[1], src[2]);
   if (kind == FREE_SLIP) {
     if (flags[si] == 0) return fpost[(long long)reflect(i, a) * L.ncell + si];
+    if (flags[si] == MANTLE) return velocity_link(fpost, L, uin, r, xi, z, i);
     return fpost[(long long)oi * L.ncell + xi];
   }
   // OUTFLOW
@@ -726,6 +736,21 @@ int oc_geometry(int nx, int ny, int nz, uint64_t seed, int n_buildings, int fp_m
 // Probe columns (x, y) for vertical profiles: SplitMix64 stream seeded with
 // seed + 1; draw x ~ U{nx/8..nx-1}, y ~ U{0..ny-1}; accept when the ground
 // cell (x, y, 0) is fluid and the column is new.
+// Circular domain (Sec. 2.2: a disk of radius R whose mantle carries a local
+// velocity boundary): every cell whose centre (x + 1/2, y + 1/2) lies more
+// than R from the axis (nx / 2, ny / 2) is beyond the mantle, flag 2, in all
+// layers (buildings there included).
+int oc_mark_mantle(int nx, int ny, int nz, double radius, uint8_t* flags) {
+  if (nx < 1 || ny < 1 || nz < 1 || !flags || !(radius > 0.0)) return -1;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const double dx = x + 0.5 - 0.5 * nx, dy = y + 0.5 - 0.5 * ny;
+      if (dx * dx + dy * dy <= radius * radius) continue;
+      for (int z = 0; z < nz; ++z) flags[x + (long long)nx * (y + (long long)ny * z)] = MANTLE;
+    }
+  return 0;
+}
+
 int oc_probe_columns(int nx, int ny, int nz, uint64_t seed, const uint8_t* flags, int n,
                      int32_t* xy) {
   (void)nz;

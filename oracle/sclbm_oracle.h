@@ -11,7 +11,8 @@
  *   cell index     c = x + nx*(y + ny*z)
  *   populations    f[i*ncell + c], i = 0..18, unshifted FP64, "natural"
  *                  layout: f_i(x, t) after streaming into time level t.
- *   flags          uint8 per cell, 0 = fluid, 1 = solid.
+ *   flags          uint8 per cell, 0 = fluid, 1 = solid, 2 = beyond the
+ *                  mantle of a circular domain (velocity boundary).
  *   faces          0:-x 1:+x 2:-y 3:+y 4:-z 5:+z
  *   face kinds     0 VELOCITY, 1 OUTFLOW, 2 BOUNCE_BACK, 3 FREE_SLIP, 4 PERIODIC
  * Every function returns 0 on success and a negative value on bad input.
@@ -53,6 +54,9 @@ int oc_splitmix64(uint64_t seed, int n, uint64_t* out);
 int oc_geometry(int nx, int ny, int nz, uint64_t seed, int n_buildings,
                 int fp_min, int fp_max, int h_min, int h_max,
                 const int32_t* boxes, int n_boxes, uint8_t* flags);
+/* Circular domain: flag 2 for every cell whose centre lies more than radius
+ * from the axis (nx/2, ny/2); links into such cells take the velocity rule. */
+int oc_mark_mantle(int nx, int ny, int nz, double radius, uint8_t* flags);
 int oc_probe_columns(int nx, int ny, int nz, uint64_t seed, const uint8_t* flags,
                      int n, int32_t* xy);
 int oc_probe_points(int nx, int ny, int nz, uint64_t seed, const uint8_t* flags,

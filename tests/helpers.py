@@ -8,7 +8,8 @@ def oracle_domain(O, wl, d=0):
     p = O.params(D["nx"], D["ny"], D["nz"], D["bc"], wl["tau0"], wl["c_smag"], wl["ramp_steps"],
                  collision=wl.get("collision", 0))
     flags = O.geometry(D["nx"], D["ny"], D["nz"], D.get("seed", 0), D.get("n_buildings", 0),
-                       *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"))
+                       *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"),
+                       disk_radius=D.get("disk_radius", 0.0))
     return p, flags
 
 
