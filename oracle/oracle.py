@@ -498,3 +498,20 @@ def ensemble_series(p, flags, Z, inputs, u_ref, alpha, theta_deg, H, n_steps, se
         if keep_f:
             fs.append(f)
     return (np.array(out), np.array(fs)) if keep_f else np.array(out)
+
+
+def gpc_quantiles(coef, phi_samples, q):
+    """Empirical quantiles of the gPC surrogate at every cell (Sec. 2.4 step
+    7: confidence intervals from the expansion coefficients).  The surrogate
+    sum_a c_a(x) Phi_a(s_m) is evaluated at M given input samples s_m
+    (phi_samples[m][a] = Phi_a(s_m)); the q-quantile is its k-th smallest
+    value, k = ceil(q M) in double arithmetic, clamped to [1, M].
+    coef [P][ncell] -> [n_q][ncell]."""
+    Y = np.asarray(phi_samples, np.float64) @ np.asarray(coef, np.float64)   # [M][ncell]
+    Y = np.sort(Y, axis=0)
+    M = Y.shape[0]
+    out = []
+    for qq in q:
+        k = min(M, max(1, int(math.ceil(float(qq) * M))))
+        out.append(Y[k - 1])
+    return np.array(out)
