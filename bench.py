@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--workload", default="urban_les_256x128x64_cc3",
                     choices=["urban_les_256x128x64_cc3", "urban_batched_3domains", "urban_large_512x256x128_cc4",
-                             "urban_les_rr_256x128x64_cc3", "urban_gh121_256x128x64_rr"],
+                             "urban_les_rr_256x128x64_cc3", "urban_gh121_256x128x64_rr",
+                             "urban_disk_540x540x40_gh121"],
                     help="the benchmark workload; the other two are measured without the extra legs")
     ap.add_argument("--nodes", type=int, default=0,
                     help="profiling case: keep only this many Smolyak levels' worth of nodes (0 = all)")
     ap.add_argument("--skip", default="",
-                    help="comma list of extra legs to skip: plain,storage,rr,cpu,e2e,tune,adjoint")
+                    help="comma list of extra legs to skip: plain,storage,rr,series,paper,cpu,e2e,tune,adjoint")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shape block_x,block_y,slab_z,tile_order,exec_mode,graph_steps,variant "
                          "instead of the autotuner")
@@ -168,9 +169,11 @@ def time_oracle(wl, budget_s=15.0, threads=None):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     nthreads = O.set_threads(threads or os.cpu_count() or 1)
     D = wl["domains"][0]
-    p = O.params(D["nx"], D["ny"], D["nz"], D["bc"], wl["tau0"], wl["c_smag"], wl["ramp_steps"])
+    p = O.params(D["nx"], D["ny"], D["nz"], D["bc"], wl["tau0"], wl["c_smag"], wl["ramp_steps"],
+                 collision=wl.get("collision", 0))
     flags = O.geometry(D["nx"], D["ny"], D["nz"], D.get("seed", 0), D.get("n_buildings", 0),
-                       *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"))
+                       *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"),
+                       disk_radius=D.get("disk_radius", 0.0))
     Z, a = O.quadrature(wl["quad_rule"], len(wl["inputs"]), D["quad_level"], wl["lo"], wl["hi"])
     xi, al, th = O.node_inflow_params(Z[0], wl["inputs"], wl["u_ref"], wl["alpha"], wl.get("angle_deg", 0.0))
     uin = O.inflow(D["nz"], wl["u_ref"], xi, al, D["nz"], th)
@@ -237,7 +240,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     skip = set(s for s in args.skip.split(",") if s)
     if args.workload != "urban_les_256x128x64_cc3":
-        skip |= {"plain", "storage", "rr", "e2e", "adjoint", "cpu"}  # legs defined on the default workload
+        skip |= {"plain", "storage", "rr", "series", "paper", "e2e", "adjoint", "cpu"}  # legs of the default workload
 
     def barrier():
         if world > 1:
@@ -389,6 +392,75 @@ def main():
         del re_
         torch.cuda.empty_cache()
 
+    # ---- hourly inflow series: targets every 100 levels, 25-level moves
+    # between them (synthetic speed factors and a random walk of directions)
+    inflow_series = None
+    if "series" not in skip and rank == 0 and args.precision == "fp32":
+        per, interp, n_t, n_time = 100, 25, 12, 400
+        rng = np.random.default_rng(2024)
+        speed = np.clip(1.0 + 0.15 * rng.standard_normal(n_t), 0.5, 1.5)
+        dirs = np.cumsum(20.0 * rng.standard_normal(n_t))
+        ie = S.Ensemble(S.make_config(wl))
+        S.sc_lbm_set_tuning(ie.h, **{k: tuning[k] for k in ("block_x", "block_y", "slab_z", "tile_order")},
+                            exec_mode=tuning["exec_mode"], graph_steps=tuning["graph_steps"],
+                            variant=tuning["variant"])
+        ie.set_inflow_series(speed, dirs, per, interp)
+        S.sc_lbm_step(ie.h, wl["ramp_steps"] + 4)   # past the start-up ramp, untimed
+        ie.sync()
+        _, c0 = S.sc_lbm_counters(ie.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ie.stream)
+        S.sc_lbm_step(ie.h, n_time)
+        e1.record(ie.stream)
+        ie.stream.synchronize()
+        ie.sync()
+        _, c1 = S.sc_lbm_counters(ie.h)
+        ims = e0.elapsed_time(e1)
+        g = lup_step * n_time / (ims * 1e-3) / 1e9
+        inflow_series = {"value": round(g, 3), "unit": "GLUPS", "targets": n_t, "steps_per_target": per,
+                         "interp_steps": interp, "levels": [wl["ramp_steps"] + 4, wl["ramp_steps"] + 4 + n_time],
+                         "kernel_launches": int(c1 - c0),
+                         "hbm_frac": round(BYTES_PER_LUP[wl["precision"]] * flup_step / (ims / n_time * 1e-3) / 1e9
+                                           / peak, 4)}
+        ie.close()
+        del ie
+        torch.cuda.empty_cache()
+
+    # ---- the paper's case at full size: disk of radius 270 and height 40,
+    # 121 Gauss-Hermite nodes, regularized collision (default launch shape)
+    paper_case = None
+    if "paper" not in skip and rank == 0 and args.precision == "fp32":
+        pw = W.URBAN_DISK_PAPER
+        pcfg = S.make_config(pw)
+        pe = S.Ensemble(pcfg)
+        pcells = pw["domains"][0]["nx"] * pw["domains"][0]["ny"] * pw["domains"][0]["nz"]
+        pfluid = int((S.sc_lbm_geometry(pcfg, 0) == 0).sum())
+        pnodes = pe.n_nodes[0]
+        S.sc_lbm_step(pe.h, 4)
+        pe.sync()
+        n_time = 40
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(pe.stream)
+        S.sc_lbm_step(pe.h, n_time)
+        e1.record(pe.stream)
+        pe.moments(0, gpc=True)
+        e2.record(pe.stream)
+        pe.stream.synchronize()
+        pe.sync()
+        pms = e0.elapsed_time(e1)
+        rc_chk, nbad = S.sc_lbm_check(pe.h)
+        paper_case = {"value": round(pcells * pnodes * n_time / (pms * 1e-3) / 1e9, 3), "unit": "GLUPS",
+                      "workload": pw["name"], "nodes": pnodes, "fluid_cells": pfluid,
+                      "fluid_glups": round(pfluid * pnodes * n_time / (pms * 1e-3) / 1e9, 3),
+                      "hbm_frac": round(152 * pfluid * pnodes / (pms / n_time * 1e-3) / 1e9 / peak, 4),
+                      "ms_per_time_step": round(pms / n_time, 3),
+                      "moments_gpc_ms": round(e1.elapsed_time(e2), 3),
+                      "populations_gb": round(pcells * pnodes * 19 * 4 / 1e9, 1),
+                      "state_ok": rc_chk == S.SC_OK and nbad == 0}
+        pe.close()
+        del pe
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if "e2e" not in skip:
@@ -496,6 +568,7 @@ def main():
                          "avg_launch_ms": round(launch_ms, 5), "kernel_hash": khash},
             "fluid_glups": round(glups * flup_step / lup_step, 4),
             "plain_fp64": plain, "storage": storage or None, "regularized": regularized,
+            "inflow_series": inflow_series, "paper_case": paper_case,
             "adjoint": adjoint,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(k1 - k0),
             "clocks": clk.summary(), "extra": extra,

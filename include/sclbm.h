@@ -98,7 +98,16 @@ extern "C" {
  * n_boxes > 0, else n_buildings seeded rectangular blocks standing on the
  * ground (see sc_lbm_geometry).  quad_level: points per dimension (SC_Q_GL,
  * 1..5; SC_Q_GH, 1..40) or the sparse-grid level (SC_Q_CC_SMOLYAK) used for
- * this domain.                                                              */
+ * this domain.
+ * disk_radius > 0 makes the domain the paper's cylinder (Sec. 2.2: a disk of
+ * radius R around the buildings whose mantle carries a local velocity
+ * boundary): every column whose centre (x + 1/2, y + 1/2) lies more than R
+ * from (nx / 2, ny / 2) is outside (flag 2), and a link from a fluid cell
+ * into it takes the velocity rule of a VELOCITY face with the inflow of the
+ * cell's layer.  The box faces still apply where the disk reaches them; a
+ * circular domain takes no OUTFLOW face (SC_ERR_UNSUPPORTED).  0 (the
+ * zero-initialised default): the plain box.  Negative or non-finite:
+ * SC_ERR_ARG.                                                              */
 typedef struct {
   int nx, ny, nz;
   uint64_t geom_seed;
@@ -107,6 +116,7 @@ typedef struct {
   int n_boxes;
   int bc[6];
   int quad_level;
+  double disk_radius;
 } sc_domain_desc;
 
 /* The ensemble.  tau0 = 3 nu + 1/2 (Eq. tauEff with dx = dt = 1); c_smag is
@@ -193,7 +203,8 @@ int sc_lbm_workspace_size(const sc_lbm_config* cfg, size_t* bytes_out);
 int sc_lbm_quadrature(const sc_lbm_config* cfg, int domain, int* n_nodes, double* Z,
                       double* w, int cap);
 
-/* Solid flags (1 solid, 0 fluid) of `domain` into host uint8 [nz*ny*nx].
+/* Cell flags (0 fluid, 1 solid, 2 beyond the mantle of a circular domain)
+ * of `domain` into host uint8 [nz*ny*nx].
  * Seeded blocks use SplitMix64 (Steele, Lea & Flood 2014) on geom_seed; per
  * block, in this order: wx, wy ~ U{fp_min..fp_max}; h ~ U{h_min..min(h_max,
  * nz-4)}; x0 ~ U{nx/8 .. nx - nx/8 - wx}; y0 ~ U{2 .. ny - 2 - wy}; with
@@ -218,7 +229,8 @@ int sc_lbm_probe_points(const sc_lbm_config* cfg, int domain, int n, int32_t* xy
  * aligned) on `cuda_stream` (a cudaStream_t, NULL = legacy default stream),
  * and sets every node's populations to the equilibrium at rho = 1, u = 0
  * (Sec. 2.2).  flags_host, if non-NULL, supplies host uint8 solid flags per
- * domain (flags_host[d] of [nz*ny*nx]) instead of the configured geometry.
+ * domain (flags_host[d] of [nz*ny*nx], nonzero = solid) instead of the
+ * configured geometry; a circular domain's mantle is applied on top.
  * The workspace must stay allocated until sc_lbm_destroy.                  */
 int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_stream,
                 const uint8_t* const* flags_host, sc_lbm_t* out);
@@ -287,6 +299,31 @@ int sc_lbm_average_moments(sc_lbm_t h, int domain, double* mean, double* stdev,
                            double* gpc_coef, int out_host);
 int sc_lbm_average_field(sc_lbm_t h, int domain, int node, double* d_q);
 
+/* Confidence bounds from the gPC surrogate (Sec. 2.4 step 7: confidence
+ * intervals from the expansion coefficients; Sec. 4 profile bands).  For
+ * each of n_cells cells (host int32 cell indices c = x + nx (y + ny z) of
+ * `domain`) the surrogate Q(s) = sum_a c_a(x) Phi_a(s) is evaluated at
+ * n_samples input samples and the q-quantile is its k-th smallest value,
+ * k = ceil(q n_samples) in double arithmetic, clamped to [1, n_samples].
+ * d_coef: device double [P][ncell], the coefficients sc_lbm_moments or
+ * sc_lbm_average_moments wrote for this domain.  samples: host double
+ * [n_samples][n_inputs] in the basis's standard coordinates: s = (2 Z - lo
+ * - hi) / (hi - lo) in [-1, 1] for the Legendre basis (SC_Q_GL,
+ * SC_Q_CC_SMOLYAK), s = (Z - lo) / hi, standard normal, for the Hermite
+ * basis (SC_Q_GH).  The caller draws them (any design: random, midpoints).
+ * q: host double [n_q], each in [0, 1].  d_out: device double
+ * [n_q][n_cells].  Asynchronous on the handle's stream (the host arrays may
+ * be reused when the call returns).  SC_ERR_ARG for a configuration with
+ * gpc_degree < 0, n_cells outside [0, SC_QUANTILE_MAX_CELLS], n_samples
+ * outside [1, SC_QUANTILE_MAX_SAMPLES], n_q outside [1, SC_QUANTILE_MAX_Q],
+ * a cell outside the domain, q outside [0, 1], a non-finite sample or a
+ * null array.                                                              */
+#define SC_QUANTILE_MAX_SAMPLES 8192
+#define SC_QUANTILE_MAX_CELLS 65536
+#define SC_QUANTILE_MAX_Q 16
+int sc_lbm_gpc_quantiles(sc_lbm_t h, int domain, const double* d_coef, int n_cells, const int32_t* cells,
+                         int n_samples, const double* samples, int n_q, const double* q, double* d_out);
+
 /* Q-criterion of a velocity field (the vortex identification of the paper's
  * Q-criterion figures): d_u device float [3][ncell] (for instance from
  * sc_lbm_velocity), d_q device float [ncell] receives
@@ -345,6 +382,48 @@ int sc_lbm_load(sc_lbm_t h, const void* host_buf, size_t bytes);
  * rebuild every node's inflow table.  Synchronises the handle's stream.    */
 int sc_lbm_set_inflow(sc_lbm_t h, double u_ref, double alpha, double angle_deg);
 
+/* ------------------------------------------------------------ time-varying inflow
+ * Hourly targets of wind speed and direction joined by an interpolation
+ * interval (Sec. 2.2: after the start-up ramp the boundary velocity moves
+ * gradually to the next target magnitude and direction; Sec. 2.4 step 1 and
+ * Sec. 3: one measured target per hour, perturbed per node as
+ * U_H(t) zeta_1 and Theta(t) + zeta_2).
+ *
+ * speed[k]: target k's wind speed relative to the configuration's u_ref
+ * (factor >= 0); dir_deg[k]: its direction relative to the configuration's
+ * (degrees).  Target 0 holds from level 0; target k >= 1 takes over at
+ * level k * steps_per_target: over the next interp_steps levels the speed
+ * factor s and the direction offset delta move linearly from target k - 1
+ * to target k (the direction along the shorter arc, a half turn clockwise),
+ * lam = min(o, interp_steps) / interp_steps at offset o (a jump when
+ * interp_steps = 0); after the last target it holds.  At time level m every
+ * node's inflow table u(z) is used as (a u_x - b u_y, b u_x + a u_y, m_ u_z)
+ * with a = r s cos(delta), b = r s sin(delta), m_ = r s and r the start-up
+ * ramp: the node's speed factor and direction offset, applied to U_H(m)
+ * and Theta(m), give exactly this.
+ *
+ * Levels count from the handle's level 0 (sc_lbm_reset keeps the series).
+ * The call copies the arrays (host memory, n_targets each); it takes effect
+ * from the next step.  n_targets = 0 removes the series (steady inflow).
+ * Stretches of levels over which the factor stays fixed run in the tuned
+ * execution mode; a level inside an interpolation interval or the ramp is
+ * launched alone.  The adjoint returns SC_ERR_UNSUPPORTED while a series
+ * is set.  Errors: SC_ERR_ARG for n_targets outside
+ * [0, SC_SERIES_MAX_TARGETS], a null array with n_targets > 0, a
+ * non-finite or negative speed factor, a non-finite direction,
+ * steps_per_target outside [1, 2^40] or interp_steps outside
+ * [0, steps_per_target].                                                 */
+#define SC_SERIES_MAX_TARGETS 100000
+int sc_lbm_set_inflow_series(sc_lbm_t h, int n_targets, const double* speed, const double* dir_deg,
+                             long long steps_per_target, long long interp_steps);
+
+/* Host-only: the factor (a, b, m_) above at time level `level` >= 0 for a
+ * ramp of ramp_steps levels and a series (n_targets = 0: none) into
+ * factor[3].  Needs no handle and no GPU.  SC_ERR_ARG as above, or for
+ * ramp_steps < 0, level < 0 or a null factor.                            */
+int sc_lbm_inflow_factor(int ramp_steps, int n_targets, const double* speed, const double* dir_deg,
+                         long long steps_per_target, long long interp_steps, long long level, double* factor);
+
 /* Device bytes the adjoint needs for this domain, step count, checkpoint
  * count (0 = ceil(sqrt(n_steps))) and probe count (1..256).                */
 int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_snapshots,
@@ -364,7 +443,8 @@ int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_sna
  * grad_out: host double[2]; u_probe_out: host double [n_probes][3] or NULL.
  * Leaves the handle's populations untouched; synchronises.
  * SC_ERR_UNSUPPORTED when c_smag > 0, collision is not SC_COLL_BGK (the
- * adjoint covers BGK) or profile is not SC_PROFILE_POWER.                  */
+ * adjoint covers BGK), profile is not SC_PROFILE_POWER, an inflow series is
+ * set or the domain is circular (disk_radius > 0).                         */
 int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int n_probes,
                    const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
                    double* loss_out, double* grad_out, double* u_probe_out);

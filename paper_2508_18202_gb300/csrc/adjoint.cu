@@ -48,15 +48,16 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
   N.bout = nullptr;
   N.uinf = A.uin;
   N.uind = nullptr;
+  const Wind<float> w1{1.f, 0.f, r1};  // steady inflow: the ramp alone
   if (!(lw & kLinkSlow)) {
     float ux, uy, uz;
-    wall_velocity<float>(N, lw, z, ux, uy, uz);
+    wall_velocity<float>(N, lw, z, w1, ux, uy, uz);
     fast_push<float>(dst + c, lw, (int)pc, D.nx, D.nx * D.ny, ux, uy, uz, r1, g);
     return;
   }
   const ListedRef L = listed_ref(D, listed_index(D, c));
   float ux = 0.f, uy = 0.f, uz = 0.f;
-  if (L.word(kWordPushMove)) inflow_velocity<float>(N, z, ux, uy, uz);
+  if (L.word(kWordPushMove)) inflow_velocity<float>(N, z, w1, ux, uy, uz);
   listed_push<float>(L, dst, ux, uy, uz, r1, g);
 }
 

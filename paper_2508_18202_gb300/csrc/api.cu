@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <new>
 #include <string>
@@ -41,8 +42,9 @@ struct DomLayout {
   size_t avg = 0;  // time-averaged |u| accumulators [nq][ncell] (FP64), when configured
 };
 struct Layout {
-  size_t hdr = 0, ramp_f = 0, ramp_d = 0, probes = 0;
+  size_t hdr = 0, probes = 0;
   size_t st_mean = 0, st_std = 0, st_coef = 0, st_prof = 0, st_pnodes = 0;
+  size_t q_phi = 0, q_cells = 0, q_k = 0;  // gPC quantile scratch (gpc_degree >= 0)
   DomLayout dom[kMaxDomains];
   size_t total = 0;
 };
@@ -110,6 +112,14 @@ int validate(const sc_lbm_config* c, std::string& why) {
       }
     }
     if (D.quad_level < 1) { why = "quad_level must be >= 1"; return SC_ERR_ARG; }
+    if (!(D.disk_radius >= 0.0) || !std::isfinite(D.disk_radius)) {
+      why = "disk_radius must be finite and >= 0";
+      return SC_ERR_ARG;
+    }
+    if (D.disk_radius > 0.0 && D.bc[1] == SC_BC_OUTFLOW) {
+      why = "a circular domain (disk_radius > 0) takes no OUTFLOW face";
+      return SC_ERR_UNSUPPORTED;
+    }
   }
   return SC_OK;
 }
@@ -147,8 +157,6 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     return o;
   };
   L.hdr = take(sizeof(Header));
-  L.ramp_f = take(sizeof(float) * (size_t)(c->ramp_steps + 1));
-  L.ramp_d = take(sizeof(double) * (size_t)(c->ramp_steps + 1));
   L.probes = take(sizeof(int32_t) * 2 * kMaxProbes);
   const size_t sb = storage_bytes(c->precision);
   const int P = c->gpc_degree >= 0 ? hn_gpc_size(c->n_inputs, c->gpc_degree) : 0;
@@ -197,6 +205,11 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
   L.st_coef = take(sizeof(double) * (size_t)max_cell * P);
   L.st_prof = take(sizeof(double) * 4 * (size_t)kMaxProbes * max_nz);
   L.st_pnodes = take(sizeof(float) * (size_t)kMaxProbes * max_nq * max_nz);
+  if (P > 0) {
+    L.q_phi = take(sizeof(double) * (size_t)SC_QUANTILE_MAX_SAMPLES * P);
+    L.q_cells = take(sizeof(int32_t) * (size_t)SC_QUANTILE_MAX_CELLS);
+    L.q_k = take(sizeof(int32_t) * (size_t)SC_QUANTILE_MAX_Q);
+  }
   L.total = off;
   return SC_OK;
 }
@@ -298,6 +311,11 @@ struct sc_lbm_s {
   std::string err;
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
+  Wind<float> graph_wind{};                   // the inflow factor the graph was captured with
+  // time-varying inflow (empty: steady): speed factors, continuous
+  // direction offsets (degrees), levels per target, interpolation levels
+  std::vector<double> series_speed, series_dir;
+  long long series_per = 1, series_interp = 0;
   int persist_grid = 0;
   int never_arrive = 0;
   long long spin_limit = kSpinLimit;
@@ -378,7 +396,43 @@ int reset_state(sc_lbm_t h) {
   return SC_OK;
 }
 
-float ramp_f(const sc_lbm_t h, long long m) { return (float)hn_ramp(h->cfg.ramp_steps, m); }
+// Inflow factor of ramp r, speed factor s and direction offset d (degrees).
+// No offset gives exactly (1, 0, r s), the steady form.
+Wind<double> wind_of(double r, double s, double d) {
+  const double rad = d * (M_PI / 180.0);
+  return Wind<double>{cos(rad), sin(rad), r * s};
+}
+
+// Inflow factor of time level m: start-up ramp times the series' speed
+// factor, turned by its direction offset.
+Wind<double> wind_at(const sc_lbm_t h, long long m) {
+  double s = 1.0, d = 0.0;
+  if (!h->series_speed.empty())
+    hn_series_at((int)h->series_speed.size(), h->series_speed.data(), h->series_dir.data(), h->series_per,
+                 h->series_interp, m, &s, &d);
+  return wind_of(hn_ramp(h->cfg.ramp_steps, m), s, d);
+}
+
+Wind<float> to_float(const Wind<double>& w) { return Wind<float>{(float)w.cos_d, (float)w.sin_d, (float)w.scale}; }
+
+// Factors of a launch that advances level lvl: pulls at lvl, pushes at lvl + 1.
+void set_winds(const sc_lbm_t h, StepParams& P, long long lvl) {
+  P.wpd = wind_at(h, lvl);
+  P.wqd = wind_at(h, lvl + 1);
+  P.wp = to_float(P.wpd);
+  P.wq = to_float(P.wqd);
+}
+
+// The same factor at both ends (steps inside a stretch of constant inflow).
+void set_winds(StepParams& P, const Wind<double>& w) {
+  P.wpd = P.wqd = w;
+  P.wp = P.wq = to_float(w);
+}
+
+// First level after m at which the inflow factor may change.
+long long next_change(const sc_lbm_t h, long long m) {
+  return hn_wind_next_change(h->cfg.ramp_steps, (int)h->series_speed.size(), h->series_per, h->series_interp, m);
+}
 
 // n steps with one launch each, starting at time level `start`
 int run_launches(sc_lbm_t h, long long start, int n) {
@@ -386,8 +440,7 @@ int run_launches(sc_lbm_t h, long long start, int n) {
     const long long lvl = start + s;
     const int parity = (int)(lvl & 1);
     StepParams P = h->P;
-    P.r_pull = ramp_f(h, lvl);
-    P.r_push = ramp_f(h, lvl + 1);
+    set_winds(h, P, lvl);
     int rc = h->cfg.collision == SC_COLL_RR ? rr::launch_aa_step(P, h->cfg.precision, h->stream, parity)
                                             : launch_aa_step(P, h->cfg.precision, h->stream, parity);
     if (rc) return cuda_fail(h, (cudaError_t)rc, "aa_step launch");
@@ -397,32 +450,32 @@ int run_launches(sc_lbm_t h, long long start, int n) {
 }
 
 // Replays of a captured graph of G steps (even/odd pairs, G even) starting
-// at an even time level.
-// The graph is captured once with the ramp complete (r = 1 on every level),
-// so levels inside the start-up ramp are launched one by one.
-int run_graph(sc_lbm_t h, int n) {
+// at an even time level, over levels [t, t + n) of constant inflow factor w.
+// The graph holds w in its launch parameters; it is captured again when a
+// stretch with another factor comes.
+int run_graph(sc_lbm_t h, long long t, int n, const Wind<double>& w) {
   const int G = h->tune.graph_steps + (h->tune.graph_steps & 1);
-  if (!h->stream) return run_launches(h, h->steps, n);  // capture needs a non-default stream
-  long long t = h->steps;
-  const long long ramp_done = h->cfg.ramp_steps;  // r(m) = 1 for every m >= ramp_steps
-  long long head = 0;
-  if (t < ramp_done) head = std::min<long long>(n, ramp_done - t);
-  if (((t + head) & 1) && head < n) ++head;
-  if (head > 0) {
-    int rc = run_launches(h, t, (int)head);
+  if (!h->stream) return run_launches(h, t, n);  // capture needs a non-default stream
+  if ((t & 1) && n > 0) {
+    int rc = run_launches(h, t, 1);
     if (rc) return rc;
-    t += head;
-    n -= (int)head;
+    ++t;
+    --n;
   }
-  if (!h->graph || h->graph_len != G) {
+  const int reps = n / G;
+  if (reps == 0) return run_launches(h, t, n);
+  const Wind<float> wf = to_float(w);
+  const bool same = h->graph_wind.cos_d == wf.cos_d && h->graph_wind.sin_d == wf.sin_d &&
+                    h->graph_wind.scale == wf.scale;
+  if (!h->graph || h->graph_len != G || !same) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
+    h->graph_len = 0;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
     StepParams P = h->P;
-    P.r_pull = 1.0f;
-    P.r_push = 1.0f;
+    set_winds(P, w);
     for (int s = 0; s < G && !rc; ++s)
       rc = h->cfg.collision == SC_COLL_RR ? rr::launch_aa_step(P, h->cfg.precision, h->stream, s & 1)
                                           : launch_aa_step(P, h->cfg.precision, h->stream, s & 1);
@@ -436,8 +489,8 @@ int run_graph(sc_lbm_t h, int n) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     h->graph_len = G;
+    h->graph_wind = wf;
   }
-  const int reps = n / G;
   for (int r = 0; r < reps; ++r) {
     CK(cudaGraphLaunch(h->graph, h->stream));
     h->launches += G + (h->P.tma ? G / 2 : 0);  // TMA odd levels launch two kernels
@@ -445,7 +498,8 @@ int run_graph(sc_lbm_t h, int n) {
   return run_launches(h, t + (long long)reps * G, n - reps * G);
 }
 
-int run_persistent(sc_lbm_t h, int n) {
+// Persistent launches over levels [t, t + n) of constant inflow factor w.
+int run_persistent(sc_lbm_t h, long long t, int n, const Wind<double>& w) {
   if (!h->persist_grid) {
     int grid = 0;
     int rc = h->cfg.collision == SC_COLL_RR ? rr::aa_persistent_max_grid(h->P, h->cfg.precision, &grid)
@@ -457,8 +511,9 @@ int run_persistent(sc_lbm_t h, int n) {
   for (int done = 0; done < n;) {
     const int k = std::min(chunk, n - done);
     StepParams P = h->P;
+    set_winds(P, w);
     P.n_steps = k;
-    P.n_host = (unsigned long long)(h->steps + done);
+    P.n_host = (unsigned long long)(t + done);
     P.never_arrive = h->never_arrive;
     P.spin_limit = h->spin_limit;
     CK(cudaMemsetAsync(&h->hdr()->bar_count, 0, sizeof(unsigned int), h->stream));
@@ -479,6 +534,7 @@ int run_plain(sc_lbm_t h, int n) {
       P.plain_domain = d;
       P.plain_node = j;
       for (int s = 0; s < n; ++s) {
+        set_winds(h, P, h->steps + s);
         int rc = h->cfg.collision == SC_COLL_RR
                      ? rr::launch_plain_step(P, (unsigned long long)(h->steps + s), h->stream)
                      : launch_plain_step(P, (unsigned long long)(h->steps + s), h->stream);
@@ -489,13 +545,38 @@ int run_plain(sc_lbm_t h, int n) {
   return SC_OK;
 }
 
+// AA steps from level h->steps: stretches over which the inflow factor is
+// constant go to the tuned execution mode (graph replays, persistent
+// launches or plain launches); a step whose two factors differ (start-up
+// ramp, a move between series targets) is launched alone with both.
+int run_aa(sc_lbm_t h, int n) {
+  long long t = h->steps;
+  while (n > 0) {
+    const long long e = next_change(h, t);  // W(m) = W(t) for m in [t, e)
+    const long long c = std::min<long long>(n, e - 1 - t);  // steps t .. t + c - 1 see W(t) at both ends
+    int rc;
+    if (c <= 0) {
+      rc = run_launches(h, t, 1);
+      t += 1;
+      n -= 1;
+    } else {
+      const Wind<double> w = wind_at(h, t);
+      if (h->tune.exec_mode == SC_EXEC_GRAPH) rc = run_graph(h, t, (int)c, w);
+      else if (h->tune.exec_mode == SC_EXEC_PERSISTENT) rc = run_persistent(h, t, (int)c, w);
+      else rc = run_launches(h, t, (int)c);
+      t += c;
+      n -= (int)c;
+    }
+    if (rc) return rc;
+  }
+  return SC_OK;
+}
+
 int do_steps(sc_lbm_t h, int n) {
   if (n <= 0) return SC_OK;
   int rc;
   if (h->cfg.precision == SC_P_FP64_PLAIN) rc = run_plain(h, n);
-  else if (h->tune.exec_mode == SC_EXEC_GRAPH) rc = run_graph(h, n);
-  else if (h->tune.exec_mode == SC_EXEC_PERSISTENT) rc = run_persistent(h, n);
-  else rc = run_launches(h, h->steps, n);
+  else rc = run_aa(h, n);
   if (rc == SC_OK) h->steps += n;
   return rc;
 }
@@ -509,10 +590,12 @@ int read_err(sc_lbm_t h, unsigned* bits) {
   return SC_OK;
 }
 
-// Kernel parameters with the host's time level (observables need its parity).
+// Kernel parameters with the host's time level (observables need its parity
+// and, at odd levels, its inflow factor).
 StepParams params_now(sc_lbm_t h) {
   StepParams P = h->P;
   P.n_host = (unsigned long long)h->steps;
+  set_winds(h, P, h->steps);
   return P;
 }
 
@@ -617,9 +700,6 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   P.smag18c2 = (float)(18.0 * c.c_smag * c.c_smag);
   P.smag18c2_d = 18.0 * c.c_smag * c.c_smag;
   P.csmag_on = c.c_smag > 0 ? 1 : 0;
-  P.ramp_steps = c.ramp_steps;
-  P.ramp_f = (const float*)(h->ws + L.ramp_f);
-  P.ramp_d = (const double*)(h->ws + L.ramp_d);
   Header* H = h->hdr();
   P.err = &H->err;
   P.bar_count = &H->bar_count;
@@ -636,12 +716,6 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   std::vector<std::vector<int32_t>> ltab_words(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
-  std::vector<float> rampf(c.ramp_steps + 1);
-  std::vector<double> rampd(c.ramp_steps + 1);
-  for (int m = 0; m <= c.ramp_steps; ++m) {
-    rampd[m] = hn_ramp(c.ramp_steps, m);
-    rampf[m] = (float)rampd[m];
-  }
   h->wsum.assign(c.n_domains, 0.0);
   h->nq.assign(c.n_domains, 0);
   for (int d = 0; d < c.n_domains; ++d) {
@@ -650,6 +724,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     if (flags_host && flags_host[d]) {
       flags[d].assign(flags_host[d], flags_host[d] + M.ncell);
       for (auto& v : flags[d]) v = v ? 1 : 0;
+      hn_mark_mantle(D, flags[d]);
     } else {
       rc = hn_geometry(D, flags[d]);
       if (rc) { delete h; return rc; }
@@ -735,8 +810,6 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     return cudaMemcpyAsync(h->ws + off, src, n, cudaMemcpyHostToDevice, h->stream);
   };
   cudaError_t e = cudaSuccess;
-  e = up(L.ramp_f, rampf.data(), sizeof(float) * rampf.size());
-  if (e == cudaSuccess) e = up(L.ramp_d, rampd.data(), sizeof(double) * rampd.size());
   for (int d = 0; d < c.n_domains && e == cudaSuccess; ++d) {
     const DomLayout& M = L.dom[d];
     e = up(M.flags, flags[d].data(), flags[d].size());
@@ -882,6 +955,45 @@ int sc_lbm_moments_from_sums(sc_lbm_t h, int domain, const double* d_s1, const d
   if (!(wsum > 0.0)) return fail(h, SC_ERR_ARG, "weight sum must be positive");
   int rc = launch_finalize_moments(d_s1, d_s2, wsum, d_mean, d_stdev, h->P.dom[domain].ncell, h->stream);
   if (rc) return cuda_fail(h, (cudaError_t)rc, "finalize launch");
+  ++h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_gpc_quantiles(sc_lbm_t h, int domain, const double* d_coef, int n_cells, const int32_t* cells,
+                         int n_samples, const double* samples, int n_q, const double* q, double* d_out) {
+  if (!h || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (h->gpcP == 0) return fail(h, SC_ERR_ARG, "gpc_degree < 0 in the configuration");
+  if (n_cells < 0 || n_cells > SC_QUANTILE_MAX_CELLS || n_samples < 1 || n_samples > SC_QUANTILE_MAX_SAMPLES ||
+      n_q < 1 || n_q > SC_QUANTILE_MAX_Q || !samples || !q || (n_cells > 0 && (!cells || !d_coef || !d_out)))
+    return fail(h, SC_ERR_ARG, "quantiles: bad counts or null arrays");
+  const DevDomain& D = h->P.dom[domain];
+  for (int i = 0; i < n_cells; ++i)
+    if (cells[i] < 0 || cells[i] >= D.ncell) return fail(h, SC_ERR_ARG, "quantiles: cell outside the domain");
+  std::vector<int32_t> kidx((size_t)n_q);
+  for (int i = 0; i < n_q; ++i) {
+    if (!(q[i] >= 0.0 && q[i] <= 1.0)) return fail(h, SC_ERR_ARG, "quantiles: probabilities must lie in [0, 1]");
+    const double k = std::ceil(q[i] * (double)n_samples);
+    kidx[(size_t)i] = (int32_t)std::min<double>(n_samples, std::max<double>(1.0, k));
+  }
+  const int d = h->cfg.n_inputs, P = h->gpcP;
+  std::vector<double> phi((size_t)n_samples * P);
+  for (int m = 0; m < n_samples; ++m) {
+    for (int t = 0; t < d; ++t)
+      if (!std::isfinite(samples[(size_t)m * d + t])) return fail(h, SC_ERR_ARG, "quantiles: non-finite sample");
+    hn_gpc_basis(d, h->cfg.gpc_degree, samples + (size_t)m * d, phi.data() + (size_t)m * P,
+                 h->cfg.quad_rule == SC_Q_GH);
+  }
+  if (n_cells == 0) return SC_OK;
+  std::vector<int32_t> cl(cells, cells + n_cells);
+  const Layout& L = h->L;
+  // pageable sources: each copy has taken its data when the call returns
+  CK(cudaMemcpyAsync(h->ws + L.q_phi, phi.data(), sizeof(double) * phi.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->ws + L.q_cells, cl.data(), sizeof(int32_t) * cl.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->ws + L.q_k, kidx.data(), sizeof(int32_t) * kidx.size(), cudaMemcpyHostToDevice, h->stream));
+  const int rc = launch_gpc_quantiles(d_coef, D.ncell, P, (const int32_t*)(h->ws + L.q_cells), n_cells,
+                                      (const double*)(h->ws + L.q_phi), n_samples,
+                                      (const int32_t*)(h->ws + L.q_k), n_q, d_out, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "quantile launch");
   ++h->launches;
   return SC_OK;
 }
@@ -1243,6 +1355,48 @@ int sc_lbm_set_inflow(sc_lbm_t h, double u_ref, double alpha, double angle_deg) 
   return SC_OK;
 }
 
+namespace {
+int check_series(int n, const double* speed, const double* dir_deg, long long per, long long interp) {
+  if (n < 0 || n > SC_SERIES_MAX_TARGETS) return SC_ERR_ARG;
+  if (n == 0) return SC_OK;
+  if (!speed || !dir_deg || per < 1 || per > (1LL << 40) || interp < 0 || interp > per) return SC_ERR_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(speed[k]) || speed[k] < 0.0 || !std::isfinite(dir_deg[k])) return SC_ERR_ARG;
+  return SC_OK;
+}
+}  // namespace
+
+int sc_lbm_set_inflow_series(sc_lbm_t h, int n_targets, const double* speed, const double* dir_deg,
+                             long long steps_per_target, long long interp_steps) {
+  if (!h) return SC_ERR_ARG;
+  if (check_series(n_targets, speed, dir_deg, steps_per_target, interp_steps))
+    return fail(h, SC_ERR_ARG, "inflow series: need 0 <= n_targets <= SC_SERIES_MAX_TARGETS, finite speed "
+                               "factors >= 0 and directions, 1 <= steps_per_target <= 2^40, "
+                               "0 <= interp_steps <= steps_per_target");
+  h->series_speed.assign(speed, speed + n_targets);
+  h->series_dir.assign((size_t)n_targets, 0.0);
+  hn_series_unwrap(n_targets, dir_deg, h->series_dir.data());
+  h->series_per = n_targets ? steps_per_target : 1;
+  h->series_interp = n_targets ? interp_steps : 0;
+  return SC_OK;
+}
+
+int sc_lbm_inflow_factor(int ramp_steps, int n_targets, const double* speed, const double* dir_deg,
+                         long long steps_per_target, long long interp_steps, long long level, double* factor) {
+  if (ramp_steps < 0 || level < 0 || !factor ||
+      check_series(n_targets, speed, dir_deg, steps_per_target, interp_steps))
+    return SC_ERR_ARG;
+  std::vector<double> un((size_t)n_targets);
+  hn_series_unwrap(n_targets, dir_deg, un.data());
+  double sp = 1.0, d = 0.0;
+  if (n_targets > 0) hn_series_at(n_targets, speed, un.data(), steps_per_target, interp_steps, level, &sp, &d);
+  const Wind<double> w = wind_of(hn_ramp(ramp_steps, level), sp, d);
+  factor[0] = w.scale * w.cos_d;
+  factor[1] = w.scale * w.sin_d;
+  factor[2] = w.scale;
+  return SC_OK;
+}
+
 // ------------------------------------------------------------ adjoint
 namespace {
 struct AdjLayout {
@@ -1298,6 +1452,10 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
     return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers BGK (c_smag = 0, SC_COLL_BGK)");
   if (h->cfg.profile != SC_PROFILE_POWER)
     return fail(h, SC_ERR_UNSUPPORTED, "the adjoint's parameters are those of the power-law profile");
+  if (!h->series_speed.empty())
+    return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers a steady inflow (no inflow series set)");
+  if (domain >= 0 && domain < (int)h->doms.size() && h->doms[domain].disk_radius > 0.0)
+    return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers box domains (disk_radius = 0)");
   AdjLayout L;
   int rc = adj_plan(h, domain, n_steps, n_snapshots, n_probes, L);
   if (rc) return fail(h, rc, "bad adjoint arguments");

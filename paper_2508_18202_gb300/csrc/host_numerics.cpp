@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "sclbm_internal.h"
@@ -327,6 +328,20 @@ int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi
   return SC_OK;
 }
 
+void hn_mark_mantle(const sc_domain_desc& D, std::vector<uint8_t>& flags) {
+  if (!(D.disk_radius > 0.0)) return;
+  const double r2 = D.disk_radius * D.disk_radius, cx = 0.5 * D.nx, cy = 0.5 * D.ny;
+  const size_t plane = (size_t)D.nx * D.ny;
+  for (int y = 0; y < D.ny; ++y) {
+    const double ey = (y + 0.5) - cy;
+    for (int x = 0; x < D.nx; ++x) {
+      const double ex = (x + 0.5) - cx;
+      if (ex * ex + ey * ey > r2)
+        for (int z = 0; z < D.nz; ++z) flags[(size_t)x + (size_t)D.nx * y + plane * z] = kFlagMantle;
+    }
+  }
+}
+
 int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags) {
   const long long n = (long long)D.nx * D.ny * D.nz;
   flags.assign((size_t)n, 0);
@@ -349,6 +364,7 @@ int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags) {
       const int32_t* B = D.boxes + 6 * b;
       box(B[0], B[1], B[2], B[3], B[4], B[5]);
     }
+    hn_mark_mantle(D, flags);
     return SC_OK;
   }
   Rng rng{D.geom_seed};
@@ -365,6 +381,7 @@ int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags) {
     const int y0 = rng.draw(ylo, yhi);
     box(x0, y0, 0, x0 + wx, y0 + wy, h);
   }
+  hn_mark_mantle(D, flags);
   return SC_OK;
 }
 
@@ -415,9 +432,10 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<Li
   const long long n = (long long)D.nx * D.ny * D.nz;
   link.assign((size_t)n, 0ull);
   const int dims[3] = {D.nx, D.ny, D.nz};
-  auto fluid_at = [&](const int* q) {
-    return flags[(size_t)q[0] + (size_t)D.nx * ((size_t)q[1] + (size_t)D.ny * q[2])] == 0;
+  auto flag_at = [&](const int* q) {
+    return flags[(size_t)q[0] + (size_t)D.nx * ((size_t)q[1] + (size_t)D.ny * q[2])];
   };
+  auto fluid_at = [&](const int* q) { return flag_at(q) == 0; };
   for (int z = 0; z < D.nz; ++z)
     for (int y = 0; y < D.ny; ++y)
       for (int x = 0; x < D.nx; ++x) {
@@ -445,8 +463,12 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<Li
           }
           int kind = kStream;
           if (nf == 0) {
-            if (!fluid_at(p)) kind = kBounce;
-            else if (wrapped) {
+            if (flag_at(p) == kFlagMantle) {
+              kind = kMoving;  // the circular mantle's velocity boundary
+              vel = true;
+            } else if (!fluid_at(p)) {
+              kind = kBounce;
+            } else if (wrapped) {
               kind = kBounce;  // placeholder: streaming across a periodic face
               complex_cell = true;
             }
@@ -470,6 +492,10 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<Li
               // free slip at a z face: in-plane source x - (c_x, c_y, 0)
               int s[3] = {xc[0] - ci[0], xc[1] - ci[1], xc[2]};
               kind = fluid_at(s) ? kSpecZ : kBounce;
+              if (flag_at(s) == kFlagMantle) {
+                kind = kMoving;
+                vel = true;
+              }
             } else {
               kind = kBounce;  // placeholder: outflow or free slip on an x/y face
               complex_cell = true;
@@ -593,6 +619,7 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
         if (c.n == 0) {
           const long long p = cidx(c.p);
           if (flags[p] == 0) src = (long long)h_opp(i) * pitch + p;
+          else if (flags[p] == kFlagMantle) L.pull_move |= 1u << i;
         } else if (c.n == 1) {
           const int kind = D.bc[c.f[0]];
           if (kind == SC_BC_VELOCITY) {
@@ -605,6 +632,7 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
             const long long sp = cidx(cs.p);
             if (kind == SC_BC_FREE_SLIP) {
               if (flags[sp] == 0) src = (long long)h_opp(h_refl(i, a)) * pitch + sp;
+              else if (flags[sp] == kFlagMantle) L.pull_move |= 1u << i;
             } else {  // OUTFLOW on +x
               L.bout_mask |= 1u << i;
               src = flags[sp] == 0 ? ((long long)cs.p[2] * D.ny + cs.p[1]) * 5 + h_kout(i)
@@ -637,6 +665,7 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
         if (c.n == 0) {
           const long long q = cidx(c.p);
           if (flags[q] == 0) dst = (long long)j * pitch + q;
+          else if (flags[q] == kFlagMantle) L.push_move |= 1u << j;
         } else if (c.n == 1) {
           const int kind = D.bc[c.f[0]];
           if (kind == SC_BC_VELOCITY) {
@@ -648,6 +677,7 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
             const HCross ct = h_classify(D, t[0], t[1], t[2]);
             const long long tp = cidx(ct.p);
             if (flags[tp] == 0) dst = (long long)h_refl(j, a) * pitch + tp;
+            else if (flags[tp] == kFlagMantle) L.push_move |= 1u << j;
           } else if (kind != SC_BC_BOUNCE_BACK) {
             dst = -1;  // OUTFLOW: leaves the domain
           }
@@ -714,6 +744,43 @@ double hn_ramp(int ramp_steps, long long m) {
   if (ramp_steps <= 0) return 1.0;
   const long long mm = m < ramp_steps ? m : ramp_steps;
   return 0.5 * (1.0 - cos(M_PI * (double)mm / (double)ramp_steps));
+}
+
+void hn_series_unwrap(int n, const double* dir_deg, double* unwrapped) {
+  if (n <= 0) return;
+  unwrapped[0] = dir_deg[0];
+  for (int k = 1; k < n; ++k) {
+    // the change in [-180, 180): fmod keeps the sign of its first argument
+    double turn = fmod(dir_deg[k] - dir_deg[k - 1] + 180.0, 360.0);
+    if (turn < 0.0) turn += 360.0;
+    unwrapped[k] = unwrapped[k - 1] + (turn - 180.0);
+  }
+}
+
+void hn_series_at(int n, const double* speed, const double* unwrapped, long long per, long long interp,
+                  long long m, double* s, double* d) {
+  const long long k = m / per;
+  if (k <= 0 || k >= n) {
+    const int t = k <= 0 ? 0 : n - 1;
+    *s = speed[t];
+    *d = unwrapped[t];
+    return;
+  }
+  const long long o = m - k * per;
+  const double lam = interp == 0 ? 1.0 : (double)std::min(o, interp) / (double)interp;
+  *s = speed[k - 1] + lam * (speed[k] - speed[k - 1]);
+  *d = unwrapped[k - 1] + lam * (unwrapped[k] - unwrapped[k - 1]);
+}
+
+long long hn_wind_next_change(int ramp_steps, int n, long long per, long long interp, long long m) {
+  if (m + 1 <= (long long)ramp_steps) return m + 1;  // r(m) rises up to level ramp_steps
+  if (n < 2) return LLONG_MAX;
+  // target k >= 1 changes the factor at levels k per + 1 .. k per + interp
+  // (at k per alone when interp = 0)
+  const long long k = m / per;
+  if (interp > 0 && k >= 1 && k <= n - 1 && m + 1 <= k * per + interp) return m + 1;
+  if (k + 1 <= n - 1) return (k + 1) * per + (interp > 0 ? 1 : 0);
+  return LLONG_MAX;
 }
 
 int hn_gpc_size(int d, int degree) {

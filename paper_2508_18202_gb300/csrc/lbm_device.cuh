@@ -352,7 +352,8 @@ __device__ __forceinline__ long long link_offset(const DevDomain& D, int i) {
 // offsets from the cell's own slot 0 (a node holds fewer than 2^31
 // populations).
 
-// 6 w_i (c_i . u) r, direction i known at compile time.
+// 6 w_i (c_i . u) r, direction i known at compile time; u is the wall
+// velocity turned to the arrival level's direction, r its scale.
 template <class T>
 __device__ __forceinline__ T wall_term(int i, T ux, T uy, T uz, T r) {
   return T(6) * W<T>(i) * (T(CX(i)) * ux + T(CY(i)) * uy + T(CZ(i)) * uz) * r;
@@ -466,41 +467,53 @@ __device__ __forceinline__ long long listed_index(const DevDomain& D, long long 
   return lo;
 }
 
-// Inflow velocity of layer z for the moving-wall term (zero when the cell has
-// no inflow link, so the table is not read).
+// Inflow factors of a launch in the compute type T: arrival level n (pulls)
+// and n + 1 (pushes).
+template <class T>
+__device__ __forceinline__ Wind<T> wind_pull(const StepParams& P) {
+  if constexpr (sizeof(T) == 8) return P.wpd;
+  else return P.wp;
+}
+template <class T>
+__device__ __forceinline__ Wind<T> wind_push(const StepParams& P) {
+  if constexpr (sizeof(T) == 8) return P.wqd;
+  else return P.wq;
+}
+
+// Inflow velocity of layer z of a node at the level of factor w: the table
+// row turned by the level's direction offset (the scale is applied by the
+// moving-wall term).
 template <class S>
-__device__ __forceinline__ void wall_velocity(const Node<S>& N, LinkWord lw, int z, typename Store<S>::C& ux,
+__device__ __forceinline__ void inflow_velocity(const Node<S>& N, int z, Wind<typename Store<S>::C> w,
+                                                typename Store<S>::C& ux, typename Store<S>::C& uy,
+                                                typename Store<S>::C& uz) {
+  using T = typename Store<S>::C;
+  T x, y, zz;
+  if constexpr (sizeof(T) == 8) {
+    x = T(N.uind[3 * z]);
+    y = T(N.uind[3 * z + 1]);
+    zz = T(N.uind[3 * z + 2]);
+  } else {
+    const float4 u = N.uinf[z];
+    x = T(u.x);
+    y = T(u.y);
+    zz = T(u.z);
+  }
+  ux = w.cos_d * x - w.sin_d * y;
+  uy = w.sin_d * x + w.cos_d * y;
+  uz = zz;
+}
+
+// The same for the moving-wall term of a bulk cell: zero when the cell has
+// no inflow link, so the table is not read.
+template <class S>
+__device__ __forceinline__ void wall_velocity(const Node<S>& N, LinkWord lw, int z,
+                                              Wind<typename Store<S>::C> w, typename Store<S>::C& ux,
                                               typename Store<S>::C& uy, typename Store<S>::C& uz) {
   using T = typename Store<S>::C;
   ux = uy = uz = T(0);
   if (!(lw & kLinkVel)) return;
-  if constexpr (sizeof(T) == 8) {
-    ux = T(N.uind[3 * z]);
-    uy = T(N.uind[3 * z + 1]);
-    uz = T(N.uind[3 * z + 2]);
-  } else {
-    const float4 u = N.uinf[z];
-    ux = T(u.x);
-    uy = T(u.y);
-    uz = T(u.z);
-  }
-}
-
-// Inflow velocity of layer z of a node, unconditionally.
-template <class S>
-__device__ __forceinline__ void inflow_velocity(const Node<S>& N, int z, typename Store<S>::C& ux,
-                                                typename Store<S>::C& uy, typename Store<S>::C& uz) {
-  using T = typename Store<S>::C;
-  if constexpr (sizeof(T) == 8) {
-    ux = T(N.uind[3 * z]);
-    uy = T(N.uind[3 * z + 1]);
-    uz = T(N.uind[3 * z + 2]);
-  } else {
-    const float4 u = N.uinf[z];
-    ux = T(u.x);
-    uy = T(u.y);
-    uz = T(u.z);
-  }
+  inflow_velocity<S>(N, z, w, ux, uy, uz);
 }
 
 // ------------------------------------------------------------ per-node views

@@ -187,7 +187,7 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
 // or lid link takes the link-kind form for all its cells, so neither
 // diverges.  The next cell's link word is loaded one cell ahead.
 template <class S, bool CG>
-__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R, float r, float r1) {
+__device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R) {
   using T = typename Store<S>::C;
   if (!R.valid) return;
   const DevDomain& D = P.dom[R.d];
@@ -219,10 +219,11 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef
       N.uinf = uinf;
       N.uind = uind;
       T ux, uy, uz;
-      wall_velocity<S>(N, lw, z, ux, uy, uz);
-      fast_pull<S, CG>(base, lw, pc, sy, sz, ux, uy, uz, T(r), g);
+      wall_velocity<S>(N, lw, z, wind_pull<T>(P), ux, uy, uz);
+      fast_pull<S, CG>(base, lw, pc, sy, sz, ux, uy, uz, wind_pull<T>(P).scale, g);
       collide_p<T, true>(P, g);
-      fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, T(r1), g);
+      wall_velocity<S>(N, lw, z, wind_push<T>(P), ux, uy, uz);
+      fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, wind_push<T>(P).scale, g);
     }
   }
 }
@@ -243,8 +244,7 @@ __device__ __forceinline__ int decode_bitem(const StepParams& P, long long item,
 // the compiled link rules (one round of table loads, one of population
 // loads).
 template <class S, bool CG>
-__device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long item, float r,
-                                                  float r1) {
+__device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long item) {
   using T = typename Store<S>::C;
   if (item >= P.total_bitems) return;
   int d = 0;
@@ -258,12 +258,14 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   // two rounds of memory latency (words, then populations and inflow)
   const ListedRef L = listed_ref(D, li);
   const Node<S> N = node_view<S>(D, node);
+  const int z = L.word(kWordZ);
   T ux, uy, uz;
-  inflow_velocity<S>(N, L.word(kWordZ), ux, uy, uz);
+  inflow_velocity<S>(N, z, wind_pull<T>(P), ux, uy, uz);
   T g[kQ];
-  listed_pull<S, CG>(L, N.g, N.bout, ux, uy, uz, T(r), g);
+  listed_pull<S, CG>(L, N.g, N.bout, ux, uy, uz, wind_pull<T>(P).scale, g);
   collide_p<T, true>(P, g);
-  listed_push<S>(L, N.g, ux, uy, uz, T(r1), g);
+  inflow_velocity<S>(N, z, wind_push<T>(P), ux, uy, uz);
+  listed_push<S>(L, N.g, ux, uy, uz, wind_push<T>(P).scale, g);
 }
 
 // Listed cells of the even level (local update; outlet cells save their
@@ -278,11 +280,6 @@ __device__ __forceinline__ void even_boundary_item(const StepParams& P, long lon
   const int z = (int)(idx / ((long long)D.nx * D.ny));
   const LinkWord lw = __ldg(D.link + idx);
   cell_even<S, CG>(P, D, node_view<S>(D, node), lw, y, z, idx);
-}
-
-__device__ __forceinline__ float ramp_at(const StepParams& P, unsigned long long m) {
-  const unsigned long long k = m < (unsigned long long)P.ramp_steps ? m : (unsigned long long)P.ramp_steps;
-  return P.ramp_f[k];
 }
 
 // Blocks of an even or odd launch that carry the listed (node, cell) items:
@@ -325,17 +322,17 @@ __global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constan
 // Odd time level in one launch: the listed blocks take the listed boundary
 // cells (one thread per (node, cell)), the rest the tiles of bulk cells.  The
 // two sets touch disjoint slots, so the long-latency boundary work overlaps
-// with the bulk stream.  The inflow ramp factors of the odd level n (pulls,
-// r(n)) and of level n + 1 (pushes) come with the launch.
+// with the bulk stream.  The inflow factors of the odd level n (pulls) and
+// of level n + 1 (pushes) come with the launch.
 template <class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_constant__ StepParams P) {
   unsigned k;
   if (block_role(P, &k)) {
     const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-    odd_boundary_item<S, false>(P, item, P.r_pull, P.r_push);
+    odd_boundary_item<S, false>(P, item);
     return;
   }
-  odd_bulk_tile<S, false>(P, block_tile(P, k), P.r_pull, P.r_push);
+  odd_bulk_tile<S, false>(P, block_tile(P, k));
 }
 
 // Odd time level, listed boundary cells alone (after the TMA odd kernel of the
@@ -343,7 +340,7 @@ __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_con
 template <class S>
 __global__ void __launch_bounds__(256) aa_odd_boundary_kernel(const __grid_constant__ StepParams P) {
   const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-  odd_boundary_item<S, false>(P, item, P.r_pull, P.r_push);
+  odd_boundary_item<S, false>(P, item);
 }
 
 // ------------------------------------------------------------ TMA-staged bulk kernels
@@ -610,7 +607,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) aa_odd_tma_kernel(const __grid
       const int pc = (int)D.pitch, sy = D.nx, sz = D.nx * D.ny;
       const int z = (int)(c / ((long long)sz));
       T ux, uy, uz;
-      wall_velocity<S>(N, lw, z, ux, uy, uz);
+      wall_velocity<S>(N, lw, z, wind_pull<T>(P), ux, uy, uz);
       // links that do not stream take their value from the own or the
       // in-plane slot in global memory
 #pragma unroll
@@ -619,11 +616,12 @@ __global__ void __launch_bounds__(kTmaThreads, 2) aa_odd_tma_kernel(const __grid
         if (kind == kStream) continue;
         const int off = kind == kSpecZ ? OPP(REFL(i, 2)) * pc - (CX(i) + CY(i) * sy) : i * pc;
         T v = Store<S>::ld(base + off);
-        if (kind == kMoving) v += wall_term<T>(i, ux, uy, uz, T(P.r_pull));
+        if (kind == kMoving) v += wall_term<T>(i, ux, uy, uz, wind_pull<T>(P).scale);
         g[i] = v;
       }
       collide_p<T, true>(P, g);
-      fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, T(P.r_push), g);
+      wall_velocity<S>(N, lw, z, wind_push<T>(P), ux, uy, uz);
+      fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, wind_push<T>(P).scale, g);
     }
   }
 }
@@ -685,14 +683,13 @@ __global__ void __launch_bounds__(256, 3) aa_persistent_kernel(const __grid_cons
         __syncthreads();  // the shared tile head is rewritten next iteration
       }
     } else {
-      const float r = ramp_at(P, n), r1 = ramp_at(P, n + 1);
       for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) {
-        odd_bulk_tile<S, true>(P, block_tile(P, (unsigned)t), r, r1);
+        odd_bulk_tile<S, true>(P, block_tile(P, (unsigned)t));
         __syncthreads();
       }
       // bulk and boundary cells touch disjoint slots: no barrier between them
       for (long long b = blockIdx.x; b < bblocks; b += gridDim.x)
-        odd_boundary_item<S, true>(P, b * threads + threadIdx.y * P.bx + threadIdx.x, r, r1);
+        odd_boundary_item<S, true>(P, b * threads + threadIdx.y * P.bx + threadIdx.x);
     }
     if (!grid_barrier(P, gen)) return;
     ++n;
@@ -726,8 +723,6 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
     N.bout = nullptr;
     N.uinf = nullptr;
     N.uind = D.uin_d + (long long)node * D.nz * 3;
-    const unsigned long long m1 = n + 1;
-    const double r1 = P.ramp_d[m1 < (unsigned long long)P.ramp_steps ? m1 : P.ramp_steps];
     for (int z = z0; z < z1; ++z) {
       const long long idx = cidx(D, x, y, z);
       const LinkWord lw = __ldg(D.link + idx);
@@ -737,8 +732,8 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
       for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
       collide_p<double, false>(P, g);
       double ux, uy, uz;
-      wall_velocity<double>(N, lw, z, ux, uy, uz);
-      fast_push<double>(dst + idx, lw, (int)pc, (int)sy, (int)sz, ux, uy, uz, r1, g);
+      wall_velocity<double>(N, lw, z, P.wqd, ux, uy, uz);
+      fast_push<double>(dst + idx, lw, (int)pc, (int)sy, (int)sz, ux, uy, uz, P.wqd.scale, g);
     }
     return;
   }
@@ -752,15 +747,13 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const __grid_constant__
   N.bout = nullptr;
   N.uinf = nullptr;
   N.uind = D.uin_d + (long long)node * D.nz * 3;
-  const unsigned long long m1 = n + 1;
-  const double r1 = P.ramp_d[m1 < (unsigned long long)P.ramp_steps ? m1 : P.ramp_steps];
   double g[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) g[i] = src[(long long)i * pc + idx];
   collide_p<double, false>(P, g);
   double ux = 0.0, uy = 0.0, uz = 0.0;
-  if (L.word(kWordPushMove)) inflow_velocity<double>(N, z, ux, uy, uz);
-  listed_push<double>(L, dst, ux, uy, uz, r1, g);
+  if (L.word(kWordPushMove)) inflow_velocity<double>(N, z, P.wqd, ux, uy, uz);
+  listed_push<double>(L, dst, ux, uy, uz, P.wqd.scale, g);
 }
 
 #ifndef SCLBM_RR_UNIT
@@ -801,15 +794,16 @@ __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain
 #pragma unroll
       for (int i = 0; i < kQ; ++i) g[i] = Store<S>::ld(N.g + (long long)i * D.pitch + idx);
     } else {
-      const T r = T(ramp_at(P, n));
+      // P.wp is the inflow factor of level n (the launch's n_host)
       T ux, uy, uz;
       if (lw & kLinkSlow) {
         const ListedRef L = listed_ref(D, listed_index(D, idx));
-        inflow_velocity<S>(N, z, ux, uy, uz);
-        listed_pull<S, false>(L, N.g, N.bout, ux, uy, uz, r, g);
+        inflow_velocity<S>(N, z, wind_pull<T>(P), ux, uy, uz);
+        listed_pull<S, false>(L, N.g, N.bout, ux, uy, uz, wind_pull<T>(P).scale, g);
       } else {
-        wall_velocity<S>(N, lw, z, ux, uy, uz);
-        fast_pull<S, false>(N.g + idx, lw, (int)D.pitch, D.nx, D.nx * D.ny, ux, uy, uz, r, g);
+        wall_velocity<S>(N, lw, z, wind_pull<T>(P), ux, uy, uz);
+        fast_pull<S, false>(N.g + idx, lw, (int)D.pitch, D.nx, D.nx * D.ny, ux, uy, uz, wind_pull<T>(P).scale,
+                            g);
       }
     }
 #pragma unroll

@@ -80,6 +80,20 @@ constexpr int kWordBoutMask = 2 * kQ + kOutletPops * kOutletCopies;
 constexpr int kWordPullMove = kWordBoutMask + 1, kWordPushMove = kWordBoutMask + 2;
 constexpr int kWordZ = kWordBoutMask + 3;
 
+// Inflow factor of one time level: the node's inflow table u(z) is turned
+// about z by the level's direction offset delta and scaled by r s, the
+// start-up ramp times the level's speed factor.  The moving-wall term takes
+// the turned velocity and multiplies by `scale` last (steady inflow:
+// cos_d = 1, sin_d = 0, scale = r).
+template <class T>
+struct Wind {
+  T cos_d, sin_d, scale;
+};
+
+// Cell flags of the host geometry: 0 fluid, 1 solid (buildings), kFlagMantle
+// beyond the mantle of a circular domain (links into it take the velocity rule).
+constexpr uint8_t kFlagMantle = 2;
+
 // Per-domain view handed to the kernels (plain pointers into the workspace).
 struct DevDomain {
   int nx, ny, nz, nodes;
@@ -112,11 +126,12 @@ struct StepParams {
   float smag18c2;             // 18 C_S^2
   double tau0_d, smag18c2_d;
   int csmag_on;
-  const float* ramp_f;        // [ramp_steps + 1]
-  const double* ramp_d;
-  int ramp_steps;
   unsigned long long n_host;  // time level of the state (observables, persistent start)
-  float r_pull, r_push;       // odd-level launches: ramp r(n) and r(n + 1)
+  // Inflow factors of the launch: wp at arrival level n (odd-level pulls,
+  // observables of level n), wq at level n + 1 (odd-level and FP64 pushes).
+  // A persistent launch runs only levels over which both stay fixed.
+  Wind<float> wp, wq;
+  Wind<double> wpd, wqd;
   unsigned int* err;          // latched error bits
   long long total_tiles;       // bulk tiles of all domains and nodes
   long long total_bitems;      // boundary (node, cell) items of all domains
@@ -139,6 +154,10 @@ struct StepParams {
 int hn_quadrature(int rule, int d, int level, const double* lo, const double* hi,
                   std::vector<double>& Z, std::vector<double>& w);
 int hn_geometry(const sc_domain_desc& D, std::vector<uint8_t>& flags);
+// Circular domain (disk_radius > 0): every column whose centre (x + 1/2,
+// y + 1/2) lies more than disk_radius from (nx / 2, ny / 2) becomes
+// kFlagMantle in all layers.
+void hn_mark_mantle(const sc_domain_desc& D, std::vector<uint8_t>& flags);
 int hn_probe_columns(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xy);
 int hn_probe_points(const sc_domain_desc& D, const uint8_t* flags, int n, int32_t* xyz);
 void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<LinkWord>& link);
@@ -151,6 +170,17 @@ void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double t
 int hn_gpc_size(int d, int degree);
 void hn_gpc_basis(int d, int degree, const double* s /*[d]*/, double* phi /*[P]*/, bool hermite = false);
 double hn_ramp(int ramp_steps, long long m);
+// Time-varying inflow (Sec. 2.2, Sec. 3): n targets of speed factor s_k and
+// direction offset d_k (degrees), target 0 from level 0, target k >= 1
+// reached over `interp` levels from level k * per on, the last one held.
+// hn_series_unwrap makes the directions continuous (each move along the
+// shorter arc, a half turn clockwise); hn_series_at takes those.
+void hn_series_unwrap(int n, const double* dir_deg, double* unwrapped);
+void hn_series_at(int n, const double* speed, const double* unwrapped, long long per, long long interp,
+                  long long m, double* s, double* d);
+// The first level after m at which the inflow factor (ramp r(m) over
+// ramp_steps levels times the series) may differ from its value at m.
+long long hn_wind_next_change(int ramp_steps, int n, long long per, long long interp, long long m);
 
 // ------------------------------------------------------------ kernel launchers
 // Implemented in lbm_kernels.cu.  All return cudaError_t as int.
@@ -196,6 +226,10 @@ int launch_finalize_moments(const double* s1, const double* s2, double wsum, dou
 int launch_scale(const double* in, double s, double* out, long long n, void* stream);
 // Q-criterion of a velocity field u[3][ncell] of a domain into q[ncell].
 int launch_qcriterion(const StepParams& P, int domain, const float* u, float* q, void* stream);
+// Confidence bounds from the gPC surrogate (quantiles.cu): per listed cell
+// the k-th smallest of sum_a coef[a][cell] phi[m][a] over the M samples.
+int launch_gpc_quantiles(const double* coef, long long ncell, int P, const int32_t* cells, int n_cells,
+                         const double* phi, int M, const int32_t* kidx, int nq, double* out, void* stream);
 int launch_check(const StepParams& P, int precision, unsigned long long* d_count, void* stream);
 
 // Adjoint of one node's time step (adjoint.cu).
@@ -210,7 +244,7 @@ struct AdjArgs {
   double* accum;          // [0] loss, [1] dJ/du_ref, [2] dJ/dalpha
 };
 int launch_adj_forward(const StepParams& P, const AdjArgs& A, const float* src, float* dst, float r1,
-                       void* stream);
+                       void* stream);  // r1: ramp r(n + 1) of the step's pushes
 int launch_adj_loss(const StepParams& P, const AdjArgs& A, const float* f, float* lam, void* stream);
 int launch_adj_step(const StepParams& P, const AdjArgs& A, const float* f, const float* lam_next, float* lam,
                     float r1, void* stream);

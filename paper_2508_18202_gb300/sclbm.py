@@ -19,6 +19,8 @@ SC_ERR_ARG, SC_ERR_WORKSPACE, SC_ERR_CUDA = -1, -2, -3
 SC_ERR_DIVERGED, SC_ERR_TIMEOUT, SC_ERR_UNSUPPORTED, SC_ERR_STATE = -4, -5, -6, -7
 SC_ERR_SCRATCH = -8
 SC_NOALLOC_MAX_NODES = 1024
+SC_SERIES_MAX_TARGETS = 100000
+SC_QUANTILE_MAX_SAMPLES, SC_QUANTILE_MAX_CELLS, SC_QUANTILE_MAX_Q = 8192, 65536, 16
 SC_BC_VELOCITY, SC_BC_OUTFLOW, SC_BC_BOUNCE_BACK, SC_BC_FREE_SLIP, SC_BC_PERIODIC = 0, 1, 2, 3, 4
 SC_IN_SPEED_REL, SC_IN_ALPHA, SC_IN_ANGLE_DEG = 0, 1, 2
 SC_Q_GL, SC_Q_CC_SMOLYAK, SC_Q_GH = 0, 1, 2
@@ -44,7 +46,8 @@ class sc_domain_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("geom_seed", C.c_uint64),
                 ("n_buildings", C.c_int), ("fp_min", C.c_int), ("fp_max", C.c_int),
                 ("h_min", C.c_int), ("h_max", C.c_int), ("boxes", C.POINTER(C.c_int32)),
-                ("n_boxes", C.c_int), ("bc", C.c_int * 6), ("quad_level", C.c_int)]
+                ("n_boxes", C.c_int), ("bc", C.c_int * 6), ("quad_level", C.c_int),
+                ("disk_radius", C.c_double)]
 
 
 class sc_lbm_config(C.Structure):
@@ -88,6 +91,7 @@ SIGNATURES = {
     "sc_lbm_average_moments": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int]),
     "sc_lbm_average_field": (C.c_int, [_H, C.c_int, C.c_int, _P]),
     "sc_lbm_qcriterion": (C.c_int, [_H, C.c_int, _P, _P]),
+    "sc_lbm_gpc_quantiles": (C.c_int, [_H, C.c_int, _P, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P]),
     "sc_lbm_populations": (C.c_int, [_H, C.c_int, C.c_int, _P]),
     "sc_lbm_autotune": (C.c_int, [_H, C.c_char_p]),
     "sc_lbm_set_tuning": (C.c_int, [_H, C.POINTER(sc_lbm_tuning)]),
@@ -100,6 +104,9 @@ SIGNATURES = {
     "sc_lbm_save": (C.c_int, [_H, _P, C.c_size_t]),
     "sc_lbm_load": (C.c_int, [_H, _P, C.c_size_t]),
     "sc_lbm_set_inflow": (C.c_int, [_H, C.c_double, C.c_double, C.c_double]),
+    "sc_lbm_set_inflow_series": (C.c_int, [_H, C.c_int, _P, _P, C.c_longlong, C.c_longlong]),
+    "sc_lbm_inflow_factor": (C.c_int, [C.c_int, C.c_int, _P, _P, C.c_longlong, C.c_longlong, C.c_longlong,
+                                       _P]),
     "sc_lbm_adjoint_workspace_size": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int,
                                                 C.POINTER(C.c_size_t)]),
     "sc_lbm_adjoint": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, _P, C.c_size_t,
@@ -172,6 +179,7 @@ class Config:
             for f in range(6):
                 D.bc[f] = int(d["bc"][f])
             D.quad_level = d["quad_level"]
+            D.disk_radius = float(d.get("disk_radius", 0.0))
         c = sc_lbm_config()
         c.n_domains = len(domains)
         c.domains = C.cast(self._doms, C.POINTER(sc_domain_desc))
@@ -385,6 +393,43 @@ def sc_lbm_set_inflow(h, u_ref, alpha, angle_deg=0.0):
     _call("sc_lbm_set_inflow", h, float(u_ref), float(alpha), float(angle_deg), handle=h)
 
 
+def sc_lbm_gpc_quantiles(h, domain, coef, cells, samples, q, out):
+    """q-quantiles of the gPC surrogate at the given cells: coef device
+    double [P][ncell], samples host [M][n_inputs] in the basis's standard
+    coordinates, out device double [n_q][n_cells]."""
+    cells = np.ascontiguousarray(np.asarray(cells, np.int32).reshape(-1))
+    samples = np.ascontiguousarray(np.asarray(samples, np.float64))
+    n_s = samples.shape[0]
+    q = np.ascontiguousarray(np.asarray(q, np.float64).reshape(-1))
+    _call("sc_lbm_gpc_quantiles", h, domain, _ptr(coef), cells.size, cells.ctypes.data if cells.size else None,
+          n_s, samples.ctypes.data, q.size, q.ctypes.data, _ptr(out), handle=h)
+
+
+def _series_arrays(speed, dir_deg):
+    sp = np.ascontiguousarray(speed, np.float64).reshape(-1)
+    dd = np.ascontiguousarray(dir_deg, np.float64).reshape(-1)
+    if sp.shape != dd.shape:
+        raise ValueError("speed and dir_deg need one entry per target")
+    return sp, dd
+
+
+def sc_lbm_set_inflow_series(h, speed, dir_deg, steps_per_target, interp_steps):
+    """Hourly targets of the inflow: speed factors relative to u_ref and
+    direction offsets in degrees (empty arrays: steady inflow again)."""
+    sp, dd = _series_arrays(speed, dir_deg)
+    _call("sc_lbm_set_inflow_series", h, int(sp.size), _ptr(sp) if sp.size else None,
+          _ptr(dd) if dd.size else None, int(steps_per_target), int(interp_steps), handle=h)
+
+
+def sc_lbm_inflow_factor(ramp_steps, speed, dir_deg, steps_per_target, interp_steps, level):
+    """(a, b, m) of time level `level` (host only)."""
+    sp, dd = _series_arrays(speed, dir_deg)
+    out = np.zeros(3)
+    _call("sc_lbm_inflow_factor", int(ramp_steps), int(sp.size), _ptr(sp) if sp.size else None,
+          _ptr(dd) if dd.size else None, int(steps_per_target), int(interp_steps), int(level), _ptr(out))
+    return out
+
+
 def sc_lbm_adjoint_workspace_size(h, domain, n_steps, n_snapshots, n_probes):
     n = C.c_size_t(0)
     _call("sc_lbm_adjoint_workspace_size", h, domain, n_steps, n_snapshots, n_probes, C.byref(n), handle=h)
@@ -474,6 +519,9 @@ class Ensemble:
     def step(self, n):
         sc_lbm_step(self.h, n)
 
+    def set_inflow_series(self, speed, dir_deg, steps_per_target, interp_steps):
+        sc_lbm_set_inflow_series(self.h, speed, dir_deg, steps_per_target, interp_steps)
+
     def moments(self, domain=0, probes=None, nodes_profiles=False, gpc=False, _reader=None):
         t = self.torch
         n = self.ncell(domain)
@@ -534,6 +582,18 @@ class Ensemble:
         sc_lbm_average_field(self.h, domain, node, q)
         self._hand_over(q)
         return q
+
+    def gpc_quantiles(self, domain, coef, cells, samples, q):
+        """Quantiles [n_q][n_cells] of the gPC surrogate of coefficients coef
+        (from moments(..., gpc=True)["coef"]) at the M input samples
+        (standard coordinates, [M][n_inputs])."""
+        d = self.cfg.c.n_inputs
+        samples = np.asarray(samples, np.float64).reshape(-1, d)
+        out = self._out(len(q), len(cells))
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        sc_lbm_gpc_quantiles(self.h, domain, coef, cells, samples, q, out)
+        self._hand_over(out)
+        return out
 
     def qcriterion(self, domain, u):
         """Q-criterion of a velocity field u[3][ncell] (device float)."""

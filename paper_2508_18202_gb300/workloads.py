@@ -102,7 +102,36 @@ URBAN_GH121 = dict(
     profile=PROFILE_LOG, z0=0.1, gpc_degree=5, n_columns=4,
 )
 
-ALL = [CHANNEL_CUBE, URBAN_LES, URBAN_BATCHED, URBAN_ADJOINT, URBAN_LARGE, URBAN_LES_RR, URBAN_GH121]
+# The paper's case (Sec. 3 and its table of parameters) on one GPU: a disk of
+# radius 270 cells (270 m at dx = 1 m) and height 40 whose mantle carries the
+# velocity boundary, two buildings at the centre (stand-ins for the Reutlingen
+# pair), bounce-back ground, free-slip sky; Ma = 0.0346 (u = 0.02) and
+# Re = 1.8e6 on the domain height; the 121-node Gauss-Hermite rule on the
+# speed factor and direction, logarithmic profile z0 = 0.1, recursive
+# regularized collision with C_S = 0.25, Hermite gPC of degree 5.
+DISK_BC = [VEL, VEL, VEL, VEL, BB, FS]
+URBAN_DISK_PAPER = dict(
+    name="urban_disk_540x540x40_gh121",
+    domains=[dict(nx=540, ny=540, nz=40, boxes=[[240, 248, 0, 266, 288, 26], [272, 236, 0, 300, 270, 33]],
+                  bc=DISK_BC, quad_level=11, disk_radius=270.0)],
+    tau0=tau_for_reynolds(0.02, 40, 1.8e6), c_smag=0.25, u_ref=0.02, alpha=0.25, angle_deg=0.0, H_ref=0.0,
+    inputs=[SPEED, ANGLE], lo=[0.0, 0.0], hi=[0.1, 6.0], quad_rule=GH, collision=RR, profile=PROFILE_LOG,
+    z0=0.1, ramp_steps=1000, precision=FP32_SHIFT, gpc_degree=5, steps=2000, n_columns=4,
+)
+
+# A small circular domain for parity tests: 48 x 48 x 14, radius 23, two blocks
+# near the axis, 3 x 3 Gauss-Hermite nodes (wind from 20 +- 6 degrees), log profile.
+DISK_SMALL = dict(
+    name="disk_small_48x48x14_gh9",
+    domains=[dict(nx=48, ny=48, nz=14, boxes=[[20, 18, 0, 26, 28, 8], [28, 20, 0, 32, 26, 10]], bc=DISK_BC,
+                  quad_level=3, disk_radius=23.0)],
+    tau0=0.56, c_smag=0.14, u_ref=0.05, alpha=0.25, angle_deg=0.0, H_ref=0.0,
+    inputs=[SPEED, ANGLE], lo=[0.0, 20.0], hi=[0.1, 6.0], quad_rule=GH, profile=PROFILE_LOG, z0=0.1,
+    ramp_steps=10, precision=FP32_SHIFT, gpc_degree=2, steps=100, n_columns=2,
+)
+
+ALL = [CHANNEL_CUBE, URBAN_LES, URBAN_BATCHED, URBAN_ADJOINT, URBAN_LARGE, URBAN_LES_RR, URBAN_GH121,
+       URBAN_DISK_PAPER, DISK_SMALL]
 
 
 def variant(workload, **over):

@@ -2,6 +2,7 @@
 include/*.h declares, and its host-only calls (quadrature, geometry, probes,
 validation) agree bit for bit with the oracle.  No GPU is touched."""
 import glob
+import math
 import os
 import re
 
@@ -93,7 +94,8 @@ def test_geometry_and_probes_bit_exact_with_oracle(O, wl):
     for d, D in enumerate(wl["domains"]):
         flags = S.sc_lbm_geometry(cfg, d)
         fo = O.geometry(D["nx"], D["ny"], D["nz"], D.get("seed", 0), D.get("n_buildings", 0),
-                        *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"))
+                        *D.get("fp", (1, 1)), *D.get("h", (1, 1)), boxes=D.get("boxes"),
+                        disk_radius=D.get("disk_radius", 0.0))
         assert flags.tobytes() == fo.tobytes()
         if D.get("boxes") is None:
             xy = S.sc_lbm_probe_columns(cfg, d, 4)
@@ -126,6 +128,9 @@ def test_workspace_size_scales_with_precision():
     (dict(domain_over=dict(bc=[W.OUT, W.VEL, W.VEL, W.VEL, W.BB, W.FS])), S.SC_ERR_UNSUPPORTED),
     (dict(domain_over=dict(bc=[W.PER, W.OUT, W.VEL, W.VEL, W.BB, W.FS])), S.SC_ERR_ARG),
     (dict(domain_over=dict(nx=0)), S.SC_ERR_ARG),
+    (dict(domain_over=dict(disk_radius=-1.0)), S.SC_ERR_ARG),
+    (dict(domain_over=dict(disk_radius=float("nan"))), S.SC_ERR_ARG),
+    (dict(domain_over=dict(disk_radius=60.0)), S.SC_ERR_UNSUPPORTED),   # URBAN_BC has an outflow face
 ])
 def test_invalid_configurations_rejected(bad, code):
     wl = W.variant(W.URBAN_LES, **bad)
@@ -150,3 +155,51 @@ def test_init_rejects_missing_workspace():
     assert rc == S.SC_ERR_WORKSPACE
     rc = S.lib().sc_lbm_init(cfg.ref, C.c_void_p(0x1000), 16, None, None, C.byref(h))
     assert rc == S.SC_ERR_WORKSPACE
+
+
+SERIES = ([1.0, 1.35, 0.6, 0.9], [350.0, 20.0, 200.0, -170.0])
+
+
+@pytest.mark.parametrize("ramp,per,interp", [(0, 10, 4), (7, 10, 4), (25, 10, 10), (3, 6, 0), (0, 1, 1)])
+def test_inflow_factor_matches_oracle_schedule(O, ramp, per, interp):
+    """The library's factor of every level (ramp, interpolation intervals,
+    shorter-arc turns, the hold after the last target) against the oracle's
+    schedule: (a, b, m) = r s (cos delta, sin delta, 1)."""
+    speed, dirs = SERIES
+    for m in list(range(0, 5 * per + ramp + 3)) + [10 ** 7]:
+        s, d = O.series_at(speed, dirs, per, interp, m)
+        r = O.ramp(ramp, m)
+        want = r * s * np.array([math.cos(math.radians(d)), math.sin(math.radians(d)), 1.0])
+        got = S.sc_lbm_inflow_factor(ramp, speed, dirs, per, interp, m)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-14, err_msg=str(m))
+
+
+def test_inflow_factor_without_series_is_the_ramp(O):
+    for m in (0, 1, 5, 9, 10, 1000):
+        np.testing.assert_array_equal(S.sc_lbm_inflow_factor(10, [], [], 1, 0, m),
+                                      [O.ramp(10, m), 0.0, O.ramp(10, m)])
+
+
+@pytest.mark.parametrize("args", [
+    dict(speed=[1.0, 1.0], dirs=[0.0, 0.0], per=10, interp=11),   # interval longer than a target
+    dict(speed=[1.0, 1.0], dirs=[0.0, 0.0], per=0, interp=0),
+    dict(speed=[1.0, 1.0], dirs=[0.0, 0.0], per=(1 << 40) + 1, interp=0),
+    dict(speed=[1.0, -0.1], dirs=[0.0, 0.0], per=10, interp=2),   # negative speed factor
+    dict(speed=[1.0, 1.0], dirs=[0.0, float("nan")], per=10, interp=2),
+    dict(speed=[1.0, float("inf")], dirs=[0.0, 0.0], per=10, interp=2),
+    dict(speed=[1.0], dirs=[0.0], per=10, interp=-1),
+    dict(speed=[1.0], dirs=[0.0], per=10, interp=2, level=-1),
+    dict(speed=[1.0], dirs=[0.0], per=10, interp=2, ramp=-1),
+])
+def test_inflow_series_rejects_invalid_arguments(args):
+    with pytest.raises(S.ScError) as ei:
+        S.sc_lbm_inflow_factor(args.get("ramp", 0), args["speed"], args["dirs"], args["per"], args["interp"],
+                               args.get("level", 0))
+    assert ei.value.code == S.SC_ERR_ARG
+
+
+def test_inflow_series_rejects_too_many_targets():
+    n = S.SC_SERIES_MAX_TARGETS + 1
+    with pytest.raises(S.ScError) as ei:
+        S.sc_lbm_inflow_factor(0, np.ones(n), np.zeros(n), 1, 0, 0)
+    assert ei.value.code == S.SC_ERR_ARG

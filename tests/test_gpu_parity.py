@@ -187,6 +187,212 @@ def test_gaussian_inputs_ensemble_statistics(O, cuda, precision, tol):
     ens.close()
 
 
+SERIES = ([1.0, 1.3, 0.8, 1.1], [10.0, -15.0, 30.0, 355.0], 24, 10)
+
+
+@pytest.mark.parametrize("precision,tol", [(W.FP64_PLAIN, 1e-12), (W.FP32_SHIFT, 1e-5)])
+@pytest.mark.parametrize("steps", [79, 120])
+def test_inflow_series_parity(O, cuda, precision, tol, steps):
+    """Hourly inflow targets (speed and direction, the last across 0 degrees)
+    joined by 10-level interpolation intervals, on the cube channel with the
+    paper's Gaussian inputs (3 x 3 Gauss-Hermite) and log profile: each node's
+    velocity against the oracle, which builds every level's profile from the
+    reference speed and direction of that level.  Level 79 lies inside an
+    interval (an odd level: the exported velocity uses its factor), level 120
+    after the last target.  FP64: populations, max abs error; FP32: velocity,
+    relative L2."""
+    wl = dict(W.CHANNEL_CUBE, precision=precision, inputs=[W.SPEED, W.ANGLE], lo=[0.0, 0.0],
+              hi=[0.1, 6.0], quad_rule=W.GH, profile=W.PROFILE_LOG, z0=0.1, ramp_steps=12,
+              domains=[dict(W.CHANNEL_CUBE["domains"][0], quad_level=3)])
+    ens = S.Ensemble(S.make_config(wl))
+    ens.set_inflow_series(*SERIES)
+    ens.step(steps)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    U, F = O.ensemble_series(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, steps, SERIES,
+                             z0=wl["z0"], keep_f=True)
+    fl = fluid_mask(flags)
+    for j in range(len(a)):
+        if precision == W.FP64_PLAIN:
+            err = np.max(np.abs(gpu_state(ens, 0, j)[:, fl] - F[j][:, fl]))
+            assert err <= tol, (j, err)
+        else:
+            ug = ens.velocity(0, j).cpu().numpy()
+            assert rel_l2(ug[:, fl], U[j][:, fl]) <= tol, j
+    # the steady inflow gives another flow
+    Us = O.ensemble(p, flags, Z[:1], wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, steps, keep_u=True,
+                    z0=wl["z0"])[1][0]
+    assert rel_l2(Us[:, fl], U[0][:, fl]) > 1e-2
+    ens.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(W.FP64_PLAIN, 1e-12), (W.FP32_SHIFT, 1e-5)])
+@pytest.mark.parametrize("collision,c_smag", [(W.BGK, 0.14), (W.RR, 0.25)])
+def test_circular_domain_parity(O, cuda, precision, tol, collision, c_smag):
+    """The paper's cylinder at small size: velocity mantle (links into the
+    columns beyond the radius take the moving-wall rule), two blocks near
+    the axis, 3 x 3 Gauss-Hermite nodes on speed and direction, log profile;
+    every node against the oracle after 60 steps (FP64: populations, max
+    abs error; FP32: velocity, relative L2)."""
+    wl = dict(W.DISK_SMALL, precision=precision, collision=collision, c_smag=c_smag)
+    steps = 60
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(steps)
+    p, flags = oracle_domain(O, wl)
+    assert (flags == 2).sum() > 0
+    Z, a = oracle_nodes(O, wl)
+    fl = fluid_mask(flags)
+    D = wl["domains"][0]
+    for j in range(len(a)):
+        xi, al, th = O.node_inflow_params(Z[j], wl["inputs"], wl["u_ref"], wl["alpha"], wl["angle_deg"])
+        uin = O.inflow_log(D["nz"], wl["u_ref"], xi, wl["z0"], D["nz"], th)
+        f = O.init_equilibrium(p, flags)
+        O.run(p, flags, uin, f, 0, steps)
+        if precision == W.FP64_PLAIN:
+            err = np.max(np.abs(gpu_state(ens, 0, j)[:, fl] - f[:, fl]))
+            assert err <= tol, (j, err)
+        else:
+            ug = ens.velocity(0, j).cpu().numpy()
+            assert rel_l2(ug[:, fl], O.macros(p, flags, f)[1][:, fl]) <= tol, j
+    ens.close()
+
+
+def test_circular_domain_with_series(O, cuda):
+    """The paper's full input pipeline at small size: cylinder, Gaussian
+    speed and direction on 3 x 3 Gauss-Hermite nodes, log profile, the
+    recursive regularized collision with C_S = 0.25 and an hourly series
+    whose direction swings by 60 degrees; FP32 velocity of every node
+    against the oracle, level 71 (inside an interpolation interval)."""
+    wl = dict(W.DISK_SMALL, collision=W.RR, c_smag=0.25)
+    series = ([1.0, 1.2, 0.9], [0.0, 60.0, 10.0], 25, 12)
+    steps = 71
+    ens = S.Ensemble(S.make_config(wl))
+    ens.set_inflow_series(*series)
+    ens.step(steps)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    U = O.ensemble_series(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], wl["angle_deg"], p.nz, steps,
+                          series, z0=wl["z0"])
+    fl = fluid_mask(flags)
+    for j in range(len(a)):
+        assert rel_l2(ens.velocity(0, j).cpu().numpy()[:, fl], U[j][:, fl]) <= 1e-5, j
+    ens.close()
+
+
+def test_paper_case_full_size(O, cuda):
+    """The paper's configuration at full size on one GPU (disk of radius 270
+    and height 40, 121 Gauss-Hermite nodes, regularized collision, C_S =
+    0.25, Re = 1.8e6; 107 GB of populations) in the launch configuration
+    bench.py times it in: the first and the last node after 100 steps against
+    the oracle (relative L2 of u <= 1e-3, the LES bound), and no non-finite or
+    non-positive density.  100 steps: earlier in the start-up ramp the
+    velocities are so small (1e-6) that FP32 rounding of the O(1) density
+    alone reaches 1e-3 of them."""
+    wl = W.URBAN_DISK_PAPER
+    ens = S.Ensemble(S.make_config(wl))      # the default launch configuration, as bench.py's leg
+    steps = 100
+    ens.step(steps)
+    assert S.sc_lbm_check(ens.h) == (S.SC_OK, 0)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    assert len(a) == 121
+    D = wl["domains"][0]
+    fl = fluid_mask(flags)
+    for j in (0, len(a) - 1):
+        xi, al, th = O.node_inflow_params(Z[j], wl["inputs"], wl["u_ref"], wl["alpha"], wl["angle_deg"])
+        uin = O.inflow_log(D["nz"], wl["u_ref"], xi, wl["z0"], D["nz"], th)
+        f = O.init_equilibrium(p, flags)
+        O.run(p, flags, uin, f, 0, steps)
+        uo = O.macros(p, flags, f)[1]
+        del f
+        ug = ens.velocity(0, j).cpu().numpy()
+        assert rel_l2(ug[:, fl], uo[:, fl]) <= 1e-3, j
+    ens.close()
+
+
+@pytest.mark.parametrize("family", ["legendre", "hermite"])
+def test_gpc_quantile_bounds(O, cuda, family):
+    """Confidence bounds of the profile behind the cube from the gPC
+    surrogate (2.5 / 50 / 97.5 %, 3000 samples): the GPU's quantiles against
+    the oracle's on the same coefficients (evaluation, sort and selection,
+    to rounding), and the whole chain against the oracle's own ensemble and
+    projection."""
+    rng = np.random.default_rng(5)
+    if family == "legendre":
+        wl = dict(W.CHANNEL_CUBE)
+        samples = rng.uniform(-1.0, 1.0, (3000, 1))
+        fam = O.LEGENDRE
+    else:
+        wl = dict(W.CHANNEL_CUBE, inputs=[W.SPEED, W.ANGLE], lo=[0.0, 0.0], hi=[0.1, 6.0], quad_rule=W.GH,
+                  profile=W.PROFILE_LOG, z0=0.1, gpc_degree=2,
+                  domains=[dict(W.CHANNEL_CUBE["domains"][0], quad_level=3)])
+        samples = rng.standard_normal((3000, 2))
+        fam = O.HERMITE
+    steps = 120
+    ens = S.Ensemble(S.make_config(wl))
+    ens.step(steps)
+    coef = ens.moments(0, gpc=True)["coef"]
+    D = wl["domains"][0]
+    x, y = wl["columns"][0]
+    cells = [x + D["nx"] * (y + D["ny"] * z) for z in range(D["nz"])]
+    q = [0.025, 0.5, 0.975]
+    got = ens.gpc_quantiles(0, coef, cells, samples, q).cpu().numpy()
+    d = len(wl["inputs"])
+    phi = O.gpc_basis_family(d, wl["gpc_degree"], fam, samples)
+    cg = coef.cpu().numpy()
+    np.testing.assert_allclose(got, O.gpc_quantiles(cg[:, cells], phi, q), rtol=0, atol=1e-14)
+    assert (got[0] <= got[1]).all() and (got[1] <= got[2]).all()
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    Qv = O.ensemble(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, steps, z0=wl.get("z0"))
+    s_nodes = O.legendre_s(Z, wl["lo"], wl["hi"]) if fam == O.LEGENDRE else O.normal_s(Z, wl["lo"], wl["hi"])
+    co = O.gpc_project(a, Qv, O.gpc_basis_family(d, wl["gpc_degree"], fam, s_nodes))
+    assert rel_l2(got, O.gpc_quantiles(co[:, cells], phi, q)) <= 1e-10
+    for bad in (dict(q=[1.5]), dict(cells=[D["nx"] * D["ny"] * D["nz"]]),
+                dict(samples=np.zeros((S.SC_QUANTILE_MAX_SAMPLES + 1, d)))):
+        args = dict(cells=cells, samples=samples, q=q)
+        args.update(bad)
+        with pytest.raises(S.ScError) as ei:
+            ens.gpc_quantiles(0, coef, args["cells"], args["samples"], args["q"])
+        assert ei.value.code == S.SC_ERR_ARG
+    ens.close()
+
+
+def test_inflow_series_modes_are_bitwise_identical(cuda):
+    """Under a series (ramp, three interpolation intervals, holds between)
+    the graph mode, which replays graphs captured per hold, matches plain
+    launches bit for bit; the persistent mode matches to rounding.  Removing
+    the series mid-run gives the steady inflow back in every mode."""
+    wl = ragged(BC_SETS["urban"])
+    series = ([1.0, 1.2, 0.9, 1.05], [0.0, 40.0, -30.0, 185.0], 12, 5)
+    got = {}
+    for mode in (S.SC_EXEC_LAUNCH, S.SC_EXEC_GRAPH, S.SC_EXEC_PERSISTENT):
+        ens = S.Ensemble(S.make_config(wl))
+        S.sc_lbm_set_tuning(ens.h, 64, 1, 1, exec_mode=mode, graph_steps=4, variant=0)
+        ens.set_inflow_series(*series)
+        ens.step(45)
+        ens.set_inflow_series([], [], 1, 0)
+        ens.step(8)
+        got[mode] = _states(ens)
+        ens.close()
+    for a, b in zip(got[S.SC_EXEC_LAUNCH], got[S.SC_EXEC_GRAPH]):
+        assert np.array_equal(a, b)
+    for a, b in zip(got[S.SC_EXEC_LAUNCH], got[S.SC_EXEC_PERSISTENT]):
+        assert np.max(np.abs(a - b)) < 1e-6
+
+
+def test_inflow_series_rejected_by_the_adjoint(cuda):
+    wl = dict(W.CHANNEL_CUBE, precision=W.FP32_SHIFT)
+    ens = S.Ensemble(S.make_config(wl))
+    ens.set_inflow_series([1.0, 1.1], [0.0, 5.0], 10, 2)
+    ws = torch.empty(S.sc_lbm_adjoint_workspace_size(ens.h, 0, 10, 0, 1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.ScError) as ei:
+        S.sc_lbm_adjoint(ens.h, 0, 0, np.array([[30, 12, 18]], np.int32), np.zeros((1, 3)), 10, 0,
+                         ws.data_ptr(), ws.numel())
+    assert ei.value.code == S.SC_ERR_UNSUPPORTED
+    ens.close()
+
+
 @pytest.mark.parametrize("precision,tol", [(W.FP64_PLAIN, 1e-11), (W.FP32_SHIFT, 1e-5)])
 def test_time_averaged_fields(O, cuda, precision, tol):
     """Time-averaged |u| per node (5 samples, 15 steps apart, after 150
@@ -432,8 +638,10 @@ def test_host_outputs_match_device_outputs(cuda):
 
 def test_bounded_barrier_wait_times_out_and_recovers(cuda):
     """A grid-barrier arrival that never comes: the wait gives up after its
-    poll limit, the call reports SC_ERR_TIMEOUT and the device stays usable."""
-    wl = ragged(BC_SETS["urban"])
+    poll limit, the call reports SC_ERR_TIMEOUT and the device stays usable.
+    No start-up ramp: levels inside it are launched one by one, outside the
+    persistent kernel."""
+    wl = ragged(BC_SETS["urban"], ramp=0)
     ens = S.Ensemble(S.make_config(wl))
     S.sc_lbm_set_tuning(ens.h, 64, 2, 1, exec_mode=S.SC_EXEC_PERSISTENT)
     S.sc_lbm_debug_barrier(ens.h, 1, 20000)
