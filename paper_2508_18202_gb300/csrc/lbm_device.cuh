@@ -480,6 +480,23 @@ __device__ __forceinline__ Wind<T> wind_push(const StepParams& P) {
   else return P.wq;
 }
 
+// Inflow table row of layer z of a node, as stored (the steady direction).
+template <class S>
+__device__ __forceinline__ void table_velocity(const Node<S>& N, int z, typename Store<S>::C& ux,
+                                               typename Store<S>::C& uy, typename Store<S>::C& uz) {
+  using T = typename Store<S>::C;
+  if constexpr (sizeof(T) == 8) {
+    ux = T(N.uind[3 * z]);
+    uy = T(N.uind[3 * z + 1]);
+    uz = T(N.uind[3 * z + 2]);
+  } else {
+    const float4 u = N.uinf[z];
+    ux = T(u.x);
+    uy = T(u.y);
+    uz = T(u.z);
+  }
+}
+
 // Inflow velocity of layer z of a node at the level of factor w: the table
 // row turned by the level's direction offset (the scale is applied by the
 // moving-wall term).
@@ -488,32 +505,24 @@ __device__ __forceinline__ void inflow_velocity(const Node<S>& N, int z, Wind<ty
                                                 typename Store<S>::C& ux, typename Store<S>::C& uy,
                                                 typename Store<S>::C& uz) {
   using T = typename Store<S>::C;
-  T x, y, zz;
-  if constexpr (sizeof(T) == 8) {
-    x = T(N.uind[3 * z]);
-    y = T(N.uind[3 * z + 1]);
-    zz = T(N.uind[3 * z + 2]);
-  } else {
-    const float4 u = N.uinf[z];
-    x = T(u.x);
-    y = T(u.y);
-    zz = T(u.z);
-  }
+  T x, y;
+  table_velocity<S>(N, z, x, y, uz);
   ux = w.cos_d * x - w.sin_d * y;
   uy = w.sin_d * x + w.cos_d * y;
-  uz = zz;
 }
 
 // The same for the moving-wall term of a bulk cell: zero when the cell has
-// no inflow link, so the table is not read.
-template <class S>
+// no inflow link, so the table is not read.  TURN = false reads the table
+// row alone (launches whose factors do not turn the inflow).
+template <class S, bool TURN = true>
 __device__ __forceinline__ void wall_velocity(const Node<S>& N, LinkWord lw, int z,
                                               Wind<typename Store<S>::C> w, typename Store<S>::C& ux,
                                               typename Store<S>::C& uy, typename Store<S>::C& uz) {
   using T = typename Store<S>::C;
   ux = uy = uz = T(0);
   if (!(lw & kLinkVel)) return;
-  inflow_velocity<S>(N, z, w, ux, uy, uz);
+  if constexpr (TURN) inflow_velocity<S>(N, z, w, ux, uy, uz);
+  else table_velocity<S>(N, z, ux, uy, uz);
 }
 
 // ------------------------------------------------------------ per-node views

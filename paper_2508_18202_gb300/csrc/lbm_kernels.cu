@@ -186,7 +186,11 @@ __device__ __forceinline__ void even_tile(const StepParams& P, const TileRef& R)
 // (or skipped) takes the plain streaming form; a warp with any wall, inflow
 // or lid link takes the link-kind form for all its cells, so neither
 // diverges.  The next cell's link word is loaded one cell ahead.
-template <class S, bool CG>
+// ROT: the launch's factors may turn the inflow (a series); without it the
+// table velocity is read once and only scaled, which keeps the 64-register
+// kernels free of the second velocity (the host sends launches that turn to
+// the kernels compiled with ROT).
+template <class S, bool CG, bool ROT>
 __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef& R) {
   using T = typename Store<S>::C;
   if (!R.valid) return;
@@ -219,10 +223,10 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef
       N.uinf = uinf;
       N.uind = uind;
       T ux, uy, uz;
-      wall_velocity<S>(N, lw, z, wind_pull<T>(P), ux, uy, uz);
+      wall_velocity<S, ROT>(N, lw, z, wind_pull<T>(P), ux, uy, uz);
       fast_pull<S, CG>(base, lw, pc, sy, sz, ux, uy, uz, wind_pull<T>(P).scale, g);
       collide_p<T, true>(P, g);
-      wall_velocity<S>(N, lw, z, wind_push<T>(P), ux, uy, uz);
+      if constexpr (ROT) wall_velocity<S>(N, lw, z, wind_push<T>(P), ux, uy, uz);
       fast_push<S>(base, lw, pc, sy, sz, ux, uy, uz, wind_push<T>(P).scale, g);
     }
   }
@@ -243,7 +247,7 @@ __device__ __forceinline__ int decode_bitem(const StepParams& P, long long item,
 // Listed cells of the odd level: one thread per (node, listed cell), from
 // the compiled link rules (one round of table loads, one of population
 // loads).
-template <class S, bool CG>
+template <class S, bool CG, bool ROT>
 __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long item) {
   using T = typename Store<S>::C;
   if (item >= P.total_bitems) return;
@@ -260,11 +264,12 @@ __device__ __forceinline__ void odd_boundary_item(const StepParams& P, long long
   const Node<S> N = node_view<S>(D, node);
   const int z = L.word(kWordZ);
   T ux, uy, uz;
-  inflow_velocity<S>(N, z, wind_pull<T>(P), ux, uy, uz);
+  if constexpr (ROT) inflow_velocity<S>(N, z, wind_pull<T>(P), ux, uy, uz);
+  else table_velocity<S>(N, z, ux, uy, uz);
   T g[kQ];
   listed_pull<S, CG>(L, N.g, N.bout, ux, uy, uz, wind_pull<T>(P).scale, g);
   collide_p<T, true>(P, g);
-  inflow_velocity<S>(N, z, wind_push<T>(P), ux, uy, uz);
+  if constexpr (ROT) inflow_velocity<S>(N, z, wind_push<T>(P), ux, uy, uz);
   listed_push<S>(L, N.g, ux, uy, uz, wind_push<T>(P).scale, g);
 }
 
@@ -307,7 +312,8 @@ __device__ __forceinline__ bool block_role(const StepParams& P, unsigned* index)
 // Even time level for every (domain, node, tile).  The even level carries no
 // boundary term, so its launches have no time-dependent parameter.
 // MINB: resident blocks of 256 threads the register budget is sized for
-// (4: at most 64 registers; 3: at most 85), chosen by the autotuner.
+// (4: at most 64 registers; 3: at most 85), chosen by the autotuner; the
+// odd kernel with MINB = 3 is also the one that turns the inflow.
 template <class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constant__ StepParams P) {
   unsigned k;
@@ -329,10 +335,10 @@ __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_con
   unsigned k;
   if (block_role(P, &k)) {
     const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-    odd_boundary_item<S, false>(P, item);
+    odd_boundary_item<S, false, MINB != 4>(P, item);
     return;
   }
-  odd_bulk_tile<S, false>(P, block_tile(P, k));
+  odd_bulk_tile<S, false, MINB != 4>(P, block_tile(P, k));
 }
 
 // Odd time level, listed boundary cells alone (after the TMA odd kernel of the
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_con
 template <class S>
 __global__ void __launch_bounds__(256) aa_odd_boundary_kernel(const __grid_constant__ StepParams P) {
   const long long item = blockIdx.x * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-  odd_boundary_item<S, false>(P, item);
+  odd_boundary_item<S, false, true>(P, item);
 }
 
 // ------------------------------------------------------------ TMA-staged bulk kernels
@@ -663,7 +669,9 @@ __device__ bool grid_barrier(const StepParams& P, unsigned int& gen) {
 
 // One cooperative launch advances n_steps; blocks stride over the work of
 // each level and meet at a grid barrier between time steps.
-template <class S>
+// ROT as for the odd tile: the host picks the form that turns the inflow
+// for chunks whose factors do.
+template <class S, bool ROT>
 __global__ void __launch_bounds__(256, 3) aa_persistent_kernel(const __grid_constant__ StepParams P) {
   __shared__ unsigned long long s_n;
   __shared__ unsigned int s_gen;
@@ -684,12 +692,12 @@ __global__ void __launch_bounds__(256, 3) aa_persistent_kernel(const __grid_cons
       }
     } else {
       for (long long t = blockIdx.x; t < P.total_tiles; t += gridDim.x) {
-        odd_bulk_tile<S, true>(P, block_tile(P, (unsigned)t));
+        odd_bulk_tile<S, true, ROT>(P, block_tile(P, (unsigned)t));
         __syncthreads();
       }
       // bulk and boundary cells touch disjoint slots: no barrier between them
       for (long long b = blockIdx.x; b < bblocks; b += gridDim.x)
-        odd_boundary_item<S, true>(P, b * threads + threadIdx.y * P.bx + threadIdx.x);
+        odd_boundary_item<S, true, ROT>(P, b * threads + threadIdx.y * P.bx + threadIdx.x);
     }
     if (!grid_barrier(P, gen)) return;
     ++n;
@@ -1154,6 +1162,12 @@ int tma_grid(int* grid) {
 #ifdef SCLBM_RR_UNIT
 namespace rr {
 #endif
+// Whether a launch's inflow factors turn the table velocity (a direction
+// offset at either level); only the kernels compiled with ROT apply a turn.
+inline bool turns_inflow(const StepParams& P) {
+  return !(P.wp.cos_d == 1.0f && P.wp.sin_d == 0.0f && P.wq.cos_d == 1.0f && P.wq.sin_d == 0.0f);
+}
+
 int launch_aa_step(const StepParams& P, int precision, void* stream, int parity) {
   dim3 block(P.bx, P.by);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1179,7 +1193,7 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
           aa_odd_tma_kernel<S><<<tgrid, kTmaThreads, odd_tma_smem<S>(), s>>>(P);
           const long long grid = (P.total_bitems + 255) / 256;
           aa_odd_boundary_kernel<S><<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(P);
-        } else if (P.odd85) {
+        } else if (P.odd85 || turns_inflow(P)) {
           aa_odd_bulk_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
         } else {
           aa_odd_bulk_kernel<S, 4><<<lgrid, block, 0, s>>>(P);
@@ -1198,7 +1212,15 @@ int aa_persistent_max_grid(const StepParams& P, int precision, int* grid) {
   int rc = dispatch(precision, [&](auto tag) -> int {
     using S = std::remove_pointer_t<decltype(tag)>;
     if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
-    else return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, aa_persistent_kernel<S>, threads, 0);
+    else {
+      // the grid serves both forms: the smaller of their occupancies
+      int a = 0, b = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, aa_persistent_kernel<S, false>, threads, 0);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, aa_persistent_kernel<S, true>, threads, 0);
+      per = std::min(a, b);
+      return (int)e;
+    }
   });
   *grid = sms * per;
   return rc;
@@ -1212,8 +1234,9 @@ int launch_aa_persistent(const StepParams& P, int precision, void* stream, int g
     if constexpr (std::is_same_v<S, double>) return (int)cudaErrorInvalidValue;
     else {
       void* args[] = {(void*)&P};
-      return (int)cudaLaunchCooperativeKernel((const void*)aa_persistent_kernel<S>, dim3(grid), block,
-                                              args, 0, s);
+      const void* fn = turns_inflow(P) ? (const void*)aa_persistent_kernel<S, true>
+                                       : (const void*)aa_persistent_kernel<S, false>;
+      return (int)cudaLaunchCooperativeKernel(fn, dim3(grid), block, args, 0, s);
     }
   });
 }
