@@ -210,12 +210,19 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef
     if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
     T g[kQ];
     if (interior) {
+      // The 19 neighbour offsets are loop-invariant; hoisted out of the z
+      // loop they would hold 19 registers and spill at the 64-register
+      // budget.  Hiding the strides from the optimiser per cell makes each
+      // offset one multiply-add at its load or store instead.
+      int pcv = pc, syv = sy, szv = sz;
+      asm volatile("" : "+r"(pcv), "+r"(syv), "+r"(szv));
 #pragma unroll
       for (int i = 0; i < kQ; ++i)
-        g[i] = LD<S, CG>(base + (OPP(i) * pc - (CX(i) + CY(i) * sy + CZ(i) * sz)));
+        g[i] = LD<S, CG>(base + (OPP(i) * pcv - (CX(i) + CY(i) * syv + CZ(i) * szv)));
       collide_p<T, true>(P, g);
+      asm volatile("" : "+r"(pcv), "+r"(syv), "+r"(szv));
 #pragma unroll
-      for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * pc + (CX(j) + CY(j) * sy + CZ(j) * sz)), g[j]);
+      for (int j = 0; j < kQ; ++j) Store<S>::st(base + (j * pcv + (CX(j) + CY(j) * syv + CZ(j) * szv)), g[j]);
     } else {
       Node<S> N;
       N.g = nullptr;
