@@ -424,6 +424,15 @@ int sc_lbm_set_inflow_series(sc_lbm_t h, int n_targets, const double* speed, con
 int sc_lbm_inflow_factor(int ramp_steps, int n_targets, const double* speed, const double* dir_deg,
                          long long steps_per_target, long long interp_steps, long long level, double* factor);
 
+/* Host-only: the first level after `level` at which the factor above may
+ * change (LLONG_MAX if it never does) into *next.  sc_lbm_step runs the
+ * levels [level, *next - 1) of a stretch in the tuned execution mode with
+ * that one factor; the level before a change is launched alone.  Same
+ * arguments and errors as sc_lbm_inflow_factor.                          */
+int sc_lbm_inflow_next_change(int ramp_steps, int n_targets, const double* speed, const double* dir_deg,
+                              long long steps_per_target, long long interp_steps, long long level,
+                              long long* next);
+
 /* Device bytes the adjoint needs for this domain, step count, checkpoint
  * count (0 = ceil(sqrt(n_steps))) and probe count (1..256).                */
 int sc_lbm_adjoint_workspace_size(sc_lbm_t h, int domain, int n_steps, int n_snapshots,

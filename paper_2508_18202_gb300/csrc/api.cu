@@ -1397,6 +1397,17 @@ int sc_lbm_inflow_factor(int ramp_steps, int n_targets, const double* speed, con
   return SC_OK;
 }
 
+int sc_lbm_inflow_next_change(int ramp_steps, int n_targets, const double* speed, const double* dir_deg,
+                              long long steps_per_target, long long interp_steps, long long level,
+                              long long* next) {
+  if (ramp_steps < 0 || level < 0 || !next ||
+      check_series(n_targets, speed, dir_deg, steps_per_target, interp_steps))
+    return SC_ERR_ARG;
+  *next = hn_wind_next_change(ramp_steps, n_targets, n_targets ? steps_per_target : 1,
+                              n_targets ? interp_steps : 0, level);
+  return SC_OK;
+}
+
 // ------------------------------------------------------------ adjoint
 namespace {
 struct AdjLayout {

@@ -107,6 +107,8 @@ SIGNATURES = {
     "sc_lbm_set_inflow_series": (C.c_int, [_H, C.c_int, _P, _P, C.c_longlong, C.c_longlong]),
     "sc_lbm_inflow_factor": (C.c_int, [C.c_int, C.c_int, _P, _P, C.c_longlong, C.c_longlong, C.c_longlong,
                                        _P]),
+    "sc_lbm_inflow_next_change": (C.c_int, [C.c_int, C.c_int, _P, _P, C.c_longlong, C.c_longlong,
+                                            C.c_longlong, C.POINTER(C.c_longlong)]),
     "sc_lbm_adjoint_workspace_size": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int,
                                                 C.POINTER(C.c_size_t)]),
     "sc_lbm_adjoint": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, _P, C.c_size_t,
@@ -428,6 +430,15 @@ def sc_lbm_inflow_factor(ramp_steps, speed, dir_deg, steps_per_target, interp_st
     _call("sc_lbm_inflow_factor", int(ramp_steps), int(sp.size), _ptr(sp) if sp.size else None,
           _ptr(dd) if dd.size else None, int(steps_per_target), int(interp_steps), int(level), _ptr(out))
     return out
+
+
+def sc_lbm_inflow_next_change(ramp_steps, speed, dir_deg, steps_per_target, interp_steps, level):
+    """First level after `level` at which the inflow factor may change (host only)."""
+    sp, dd = _series_arrays(speed, dir_deg)
+    out = C.c_longlong(0)
+    _call("sc_lbm_inflow_next_change", int(ramp_steps), int(sp.size), _ptr(sp) if sp.size else None,
+          _ptr(dd) if dd.size else None, int(steps_per_target), int(interp_steps), int(level), C.byref(out))
+    return out.value
 
 
 def sc_lbm_adjoint_workspace_size(h, domain, n_steps, n_snapshots, n_probes):

@@ -203,3 +203,31 @@ def test_inflow_series_rejects_too_many_targets():
     with pytest.raises(S.ScError) as ei:
         S.sc_lbm_inflow_factor(0, np.ones(n), np.zeros(n), 1, 0, 0)
     assert ei.value.code == S.SC_ERR_ARG
+
+
+@pytest.mark.parametrize("ramp,per,interp", [(0, 10, 4), (7, 10, 4), (25, 10, 10), (3, 6, 0), (0, 1, 1),
+                                             (12, 5, 5)])
+def test_inflow_stretches_never_miss_a_change(ramp, per, interp):
+    """The execution stretches of sc_lbm_step: from every level m the factor
+    stays exactly W(m) up to the reported next change, so graph replays and
+    persistent launches that bake W(m) into a stretch use the right inflow;
+    and the stretches are long where nothing changes (holds, after the
+    last target)."""
+    speed, dirs = SERIES
+    end = 5 * per + ramp + 3
+    for m in range(end):
+        nxt = S.sc_lbm_inflow_next_change(ramp, speed, dirs, per, interp, m)
+        assert nxt > m
+        w = S.sc_lbm_inflow_factor(ramp, speed, dirs, per, interp, m)
+        for k in range(m, min(nxt, end + per)):
+            assert np.array_equal(S.sc_lbm_inflow_factor(ramp, speed, dirs, per, interp, k), w), (m, k, nxt)
+    last = (len(speed) - 1) * per + max(interp, 0) + ramp
+    assert S.sc_lbm_inflow_next_change(ramp, speed, dirs, per, interp, last + 1) > 2 ** 62
+    if interp < per and ramp < per:
+        # inside the hold of target 1 the next change is the start of the move to target 2
+        m = per + interp + 1
+        assert S.sc_lbm_inflow_next_change(ramp, speed, dirs, per, interp, m) == 2 * per + (1 if interp else 0)
+    # without a series only the ramp changes the factor
+    assert S.sc_lbm_inflow_next_change(ramp, [], [], 1, 0, ramp) > 2 ** 62
+    if ramp:
+        assert S.sc_lbm_inflow_next_change(ramp, [], [], 1, 0, 0) == 1
