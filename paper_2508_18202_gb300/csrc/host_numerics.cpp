@@ -8,12 +8,36 @@
 
 #include <algorithm>
 #include <climits>
+#include <thread>
 #include <vector>
 
 #include "sclbm_internal.h"
 
 namespace sclbm {
 namespace {
+
+// Runs f(z0, z1) over [0, nz) split into contiguous layer ranges on up to
+// hardware_concurrency threads (one thread below 2^16 cells).  The ranges
+// write disjoint cells, so the result does not depend on the split.
+template <class F>
+void parallel_layers(int nz, long long plane, F&& f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  nt = std::min<unsigned>(nt, 32u);
+  nt = std::min<unsigned>(nt, (unsigned)std::max(1, nz));
+  if ((long long)nz * plane < (1LL << 16)) nt = 1;
+  if (nt <= 1) {
+    f(0, nz);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (unsigned t = 0; t < nt; ++t) {
+    const int z0 = (int)((long long)nz * t / nt), z1 = (int)((long long)nz * (t + 1) / nt);
+    pool.emplace_back([&f, z0, z1] { f(z0, z1); });
+  }
+  for (auto& th : pool) th.join();
+}
 
 // D3Q19 velocities (rest, axis pairs, face-diagonal pairs), Sec. 2.2 Fig. 1.
 const int kCx[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -436,13 +460,29 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<Li
     return flags[(size_t)q[0] + (size_t)D.nx * ((size_t)q[1] + (size_t)D.ny * q[2])];
   };
   auto fluid_at = [&](const int* q) { return flag_at(q) == 0; };
-  for (int z = 0; z < D.nz; ++z)
+  // neighbour offsets of the 18 moving directions
+  long long noff[kQ];
+  for (int i = 0; i < kQ; ++i)
+    noff[i] = (long long)kCx[i] + (long long)D.nx * ((long long)kCy[i] + (long long)D.ny * kCz[i]);
+  // layers [z0, z1): each cell's word depends on the flags alone
+  auto layers = [&](int z0, int z1) {
+  for (int z = z0; z < z1; ++z)
     for (int y = 0; y < D.ny; ++y)
       for (int x = 0; x < D.nx; ++x) {
         const size_t c = (size_t)x + (size_t)D.nx * ((size_t)y + (size_t)D.ny * z);
         if (flags[c]) {
           link[c] = kLinkSolid;
           continue;
+        }
+        // a fluid cell away from every face whose 18 neighbours are fluid
+        // streams on every link: word 0 (the common case, decided first)
+        if (x > 0 && x < D.nx - 1 && y > 0 && y < D.ny - 1 && z > 0 && z < D.nz - 1) {
+          bool all = true;
+          for (int i = 1; i < kQ && all; ++i) all = flags[(size_t)((long long)c - noff[i])] == 0;
+          if (all) {
+            link[c] = 0;
+            continue;
+          }
         }
         const int xc[3] = {x, y, z};
         LinkWord word = 0;
@@ -508,6 +548,8 @@ void hn_link_words(const sc_domain_desc& D, const uint8_t* flags, std::vector<Li
         if (x == D.nx - 1 && D.bc[1] == SC_BC_OUTFLOW) word |= kLinkOutlet;
         link[c] = word;
       }
+  };
+  parallel_layers(D.nz, (long long)D.nx * D.ny, layers);
 }
 
 // Fluid cells that need the general boundary path of the odd AA level: a
@@ -522,6 +564,7 @@ void hn_cell_classes(const std::vector<LinkWord>& link, std::vector<uint8_t>& cl
   cls.assign(link.size(), 0);
   for (size_t c = 0; c < link.size(); ++c) {
     const LinkWord w = link[c];
+    if (w == 0) continue;  // streams on every link: class 0
     uint8_t k = 0;
     if (w & kLinkSlow) k |= kClsSkip;
     for (int i = 0; i < kQ; ++i) {
