@@ -490,10 +490,11 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         # geometry flags, link words, class bytes; listed (outlet) cells with their
-        # 256-byte rule records; inflow tables; node weights x gPC basis; ramp tables
+        # 256-byte rule records; inflow tables; node weights x gPC basis (the ramp
+        # travels in the launch parameters)
         n_listed = int((flags.reshape(D["nz"], D["ny"], D["nx"])[:, :, -1] == 0).sum())
         h2d = (cells * (1 + 8 + 1) + n_listed * (4 + 256) + nodes * D["nz"] * (16 + 24)
-               + nodes * 8 * (1 + 6) + 2 * 8 * (wl["ramp_steps"] + 1))
+               + nodes * 8 * (1 + 6))
         d2h = 2 * 8 * cells + len(columns[0]) * D["nz"] * 4 * 8
         e2e = {"value": round(float(cells) * nodes * L * n_e2e * world / dt / 1e9, 4), "unit": "GLUPS",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
