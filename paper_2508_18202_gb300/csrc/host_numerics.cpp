@@ -34,7 +34,11 @@ void parallel_layers(int nz, long long plane, F&& f) {
   pool.reserve(nt);
   for (unsigned t = 0; t < nt; ++t) {
     const int z0 = (int)((long long)nz * t / nt), z1 = (int)((long long)nz * (t + 1) / nt);
-    pool.emplace_back([&f, z0, z1] { f(z0, z1); });
+    try {
+      pool.emplace_back([&f, z0, z1] { f(z0, z1); });
+    } catch (...) {
+      f(z0, z1);  // no thread to be had: this range runs on the calling thread
+    }
   }
   for (auto& th : pool) th.join();
 }
