@@ -16,9 +16,10 @@
 namespace sclbm {
 namespace {
 
-// Runs f(z0, z1) over [0, nz) split into contiguous layer ranges on up to
-// hardware_concurrency threads (one thread below 2^16 cells).  The ranges
-// write disjoint cells, so the result does not depend on the split.
+// Runs f(z0, z1) over [0, nz) split into contiguous ranges on up to
+// hardware_concurrency threads (one thread below 2^16 cells of work, an item
+// weighing `plane` cells).  The ranges write disjoint outputs, so the result
+// does not depend on the split.
 template <class F>
 void parallel_layers(int nz, long long plane, F&& f) {
   unsigned nt = std::thread::hardware_concurrency();
@@ -647,7 +648,9 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
   auto cidx = [&](const int* p) { return (long long)p[0] + (long long)D.nx * p[1] + plane * p[2]; };
   auto loff = [&](int i) { return (long long)kCx[i] + (long long)kCy[i] * D.nx + (long long)kCz[i] * plane; };
   tab.assign(cells.size(), ListedLinks{});
-  for (size_t k = 0; k < cells.size(); ++k) {
+  // records [k0, k1): each depends on the flags and link words alone
+  auto records = [&](int k0, int k1) {
+  for (size_t k = (size_t)k0; k < (size_t)k1; ++k) {
     const long long idx = cells[k];
     const int x = (int)(idx % D.nx), y = (int)((idx / D.nx) % D.ny), z = (int)(idx / plane);
     const int xyz[3] = {x, y, z};
@@ -770,6 +773,8 @@ void hn_listed_links(const sc_domain_desc& D, const uint8_t* flags, const std::v
       }
     }
   }
+  };
+  parallel_layers((int)cells.size(), 64, records);  // a record costs about 64 cells of link words
 }
 
 void hn_inflow(int nz, double u_ref, double xi, double alpha, double H, double theta_deg,
