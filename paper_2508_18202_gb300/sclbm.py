@@ -302,6 +302,59 @@ def shard_nodes(n_nodes, world, rank):
     return begin, base + (1 if rank < extra else 0)
 
 
+def run_in_waves(workload, n_steps, nodes_per_wave, domain=0, gpc=False, prepare=None):
+    """An ensemble whose nodes do not fit on the device at once, run in waves:
+    the collocation nodes are taken nodes_per_wave at a time, each wave a
+    handle over its node range (the runs are independent, Sec. 2.4 step 5)
+    that is stepped n_steps; its moment sums are added on the device and the
+    handle is released before the next wave is made, so one wave's workspace
+    is held at a time.  The last wave's handle finishes the sums.
+    Single-domain workloads.  prepare(ens), if given, is called on every
+    wave's ensemble before it steps (for instance to set an inflow series).
+    Returns dict(mean, std, coef (None without gpc), waves)."""
+    import torch
+    from math import comb
+    if len(workload["domains"]) != 1:
+        raise ValueError("waves run single-domain workloads")
+    if nodes_per_wave < 1:
+        raise ValueError("nodes_per_wave must be >= 1")
+    _, a_full = sc_lbm_quadrature(make_config(workload), 0)
+    n_total = len(a_full)
+    ranges = [(b, min(nodes_per_wave, n_total - b)) for b in range(0, n_total, nodes_per_wave)]
+    s1 = s2 = gs = None
+    wsum = 0.0
+    for i, (b, c) in enumerate(ranges):
+        ens = Ensemble(make_config(workload, node_begin=b, node_count=c))
+        try:
+            if prepare is not None:
+                prepare(ens)
+            ens.step(n_steps)
+            n = ens.ncell(domain)
+            if s1 is None:
+                s1 = torch.zeros(n, dtype=torch.float64, device=ens.device)
+                s2 = torch.zeros_like(s1)
+                if gpc:
+                    P = comb(ens.cfg.c.gpc_degree + ens.cfg.c.n_inputs, ens.cfg.c.n_inputs)
+                    gs = torch.zeros((P, n), dtype=torch.float64, device=ens.device)
+            a1, a2 = torch.empty_like(s1), torch.empty_like(s2)
+            ag = torch.empty_like(gs) if gs is not None else None
+            sc_lbm_moment_sums(ens.h, domain, a1, a2, ag)
+            ens.sync()
+            s1 += a1
+            s2 += a2
+            if gs is not None:
+                gs += ag
+            wsum += sc_lbm_weight_sum(ens.h, domain)
+            if i == len(ranges) - 1:
+                mean, std = torch.empty_like(s1), torch.empty_like(s1)
+                torch.cuda.current_stream(ens.device).synchronize()
+                sc_lbm_moments_from_sums(ens.h, domain, s1, s2, wsum, mean, std)
+                ens.sync()
+        finally:
+            ens.close()
+    return dict(mean=mean, std=std, coef=gs, waves=len(ranges))
+
+
 def sc_lbm_average_reset(h):
     _call("sc_lbm_average_reset", h, handle=h)
 

@@ -141,3 +141,30 @@ def test_shards_on_one_gpu_match_the_whole_ensemble():
     finally:
         dist.destroy_process_group()
     full.close()
+
+
+def test_waves_reject_bad_arguments():
+    with pytest.raises(ValueError):
+        S.run_in_waves(W.URBAN_BATCHED, 10, 4)          # several domains
+    with pytest.raises(ValueError):
+        S.run_in_waves(W.CHANNEL_CUBE, 10, 0)
+
+
+@pytest.mark.gpu
+def test_waves_match_the_whole_ensemble():
+    """An ensemble run in waves of two nodes (three waves over the 5-node
+    rule, one wave's workspace held at a time) gives the whole ensemble's
+    moments and gPC coefficients."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = dict(W.CHANNEL_CUBE, precision=W.FP32_SHIFT)
+    full = S.Ensemble(S.make_config(wl))
+    full.step(120)
+    ref = full.moments(0, gpc=True)
+    full.sync()
+    out = S.run_in_waves(wl, 120, 2, gpc=True)
+    assert out["waves"] == 3
+    assert torch.max(torch.abs(out["mean"] - ref["mean"])).item() < 1e-12
+    assert torch.max(torch.abs(out["std"] - ref["std"])).item() < 1e-9
+    assert torch.max(torch.abs(out["coef"] - ref["coef"])).item() < 1e-12
+    full.close()
