@@ -268,16 +268,26 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev,
  * solid cells 0.                                                            */
 int sc_lbm_velocity(sc_lbm_t h, int domain, int node, float* d_u);
 
-/* Sharded ensembles: the raw FP64 sums of the handle's nodes,
+/* Sharded ensembles and waves (the nodes are independent runs, Sec. 2.4
+ * step 5; the quadrature sums of Eq. quad_moments and Eq. coef_discrete add
+ * over node ranges): the raw FP64 sums of the handle's nodes,
  * d_s1 = sum_j a_j Q_j, d_s2 = sum_j a_j Q_j^2 (device double [ncell]) and,
- * if d_gpc_sums is not NULL, sum_j a_j Q_j Phi_alpha(Z_j) ([P][ncell]);
- * sc_lbm_weight_sum gives the handle's sum_j a_j (host).  After the shards'
- * sums and weight sums are added (an all-reduce), sc_lbm_moments_from_sums
- * writes mean = S1 / W and std = sqrt(max(S2 / W - mean^2, 0)) (Eq.
- * quad_moments) into d_mean, d_stdev (device double [ncell]).  The gPC
- * coefficients are the summed gPC sums themselves.  Asynchronous.          */
-int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, double* d_gpc_sums);
+ * if d_gpc_sums is not NULL, sum_j a_j Q_j Phi_alpha(Z_j) ([P][ncell]).
+ * accumulate = 0 overwrites the three arrays; accumulate = 1 adds this
+ * handle's nodes to the sums already in them, continuing each cell's FP64
+ * sum node by node, so ranges [0, k) then [k, n) reduced into the same
+ * arrays give the bits of one handle over [0, n).  Other values: SC_ERR_ARG.
+ * sc_lbm_weight_sum gives the handle's sum_j a_j (host);
+ * sc_lbm_rule_weight_sum (host-only, no handle) the sum over every node of
+ * the domain's rule, in node order.  After the shards' sums and weight sums
+ * are added (an all-reduce), sc_lbm_moments_from_sums writes mean = S1 / W
+ * and std = sqrt(max(S2 / W - mean^2, 0)) (Eq. quad_moments) into d_mean,
+ * d_stdev (device double [ncell]).  The gPC coefficients are the summed gPC
+ * sums themselves.  Asynchronous.                                          */
+int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, double* d_gpc_sums,
+                       int accumulate);
 int sc_lbm_weight_sum(sc_lbm_t h, int domain, double* wsum);
+int sc_lbm_rule_weight_sum(const sc_lbm_config* cfg, int domain, double* wsum);
 int sc_lbm_moments_from_sums(sc_lbm_t h, int domain, const double* d_s1, const double* d_s2, double wsum,
                              double* d_mean, double* d_stdev);
 
@@ -478,15 +488,19 @@ int sc_lbm_destroy(sc_lbm_t h);
  * Its scratch (the weight table on the device and a counter of non-finite
  * inputs) is a fixed file-scope device array of about 8 KB, held by every
  * GPU that loads the library until the process exits.  The first call on
- * each device (with that device current) looks up the array's address; make
- * that first call before any stream capture begins.  Every call shares the
- * array and it keeps the last call's contents (the counter is cleared at the
- * start of each call): calls whose device work overlaps (unordered streams,
- * several host threads) race on it.
+ * each device (with that device current) looks up the array's address and
+ * the device's SM count; make that first call before any stream capture
+ * begins.  Every call shares the array and it keeps the last call's contents
+ * (the counter is cleared at the start of each call): calls whose device
+ * work overlaps (unordered streams, several host threads) race on it.
  *
  * d_field: device double [n_nodes][n_cells], Q_j(c) of node j at cell c;
  * weights: host double [n_nodes], the quadrature weights a_j (their sum must
- * be positive); d_mean, d_stdev: device double [n_cells] outputs,
+ * be positive), copied to the scratch by cudaMemcpyAsync on `stream`: from
+ * pageable memory the runtime stages them before the call returns (the
+ * array may be reused at once); from pinned memory the copy reads the array
+ * when the stream reaches it (keep it unchanged until then);
+ * d_mean, d_stdev: device double [n_cells] outputs,
  *   mean = sum_j a_j Q_j / sum_j a_j,
  *   std  = sqrt(max(sum_j a_j Q_j^2 / sum_j a_j - mean^2, 0));
  * d_nonfinite: device unsigned long long or NULL, receives the count of

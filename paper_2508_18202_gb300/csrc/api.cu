@@ -893,6 +893,7 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   A.avg = h->avg_read;
   A.avg_scale = h->avg_samples > 0 ? 1.0 / (double)h->avg_samples : 0.0;
   A.raw = 0;
+  A.accumulate = 0;
   if (n_p > 0)
     CK(cudaMemcpyAsync(h->ws + L.probes, probe_xy, sizeof(int32_t) * 2 * n_p, cudaMemcpyHostToDevice,
                        h->stream));
@@ -917,8 +918,10 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   return err_status(h, bits);
 }
 
-int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, double* d_gpc_sums) {
+int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, double* d_gpc_sums,
+                       int accumulate) {
   if (!h || !d_s1 || !d_s2 || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  if (accumulate != 0 && accumulate != 1) return fail(h, SC_ERR_ARG, "accumulate must be 0 or 1");
   if (d_gpc_sums && h->gpcP == 0) return fail(h, SC_ERR_ARG, "gpc_degree < 0 in the configuration");
   MomentArgs A;
   A.domain = domain;
@@ -937,9 +940,22 @@ int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, doubl
   A.avg = nullptr;
   A.avg_scale = 0.0;
   A.raw = 1;
+  A.accumulate = accumulate;
   int rc = launch_moments(params_now(h), h->cfg.precision, A, h->stream);
   if (rc) return cuda_fail(h, (cudaError_t)rc, "moment sums launch");
   ++h->launches;
+  return SC_OK;
+}
+
+int sc_lbm_rule_weight_sum(const sc_lbm_config* cfg, int domain, double* wsum) {
+  std::string why;
+  if (!wsum || validate(cfg, why)) return SC_ERR_ARG;
+  if (domain < 0 || domain >= cfg->n_domains) return SC_ERR_ARG;
+  std::vector<double> w;
+  if (node_count(cfg, domain, nullptr, &w) < 1) return SC_ERR_ARG;
+  double ws = 0.0;  // node order, as a handle over the whole rule sums it
+  for (double v : w) ws += v;
+  *wsum = ws;
   return SC_OK;
 }
 

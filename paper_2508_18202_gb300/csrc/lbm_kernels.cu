@@ -789,8 +789,11 @@ __global__ void init_kernel(S* g, long long pitch, long long total) {
 }
 
 // ------------------------------------------------------------ observables
-// Populations f_i of time level n at a fluid cell (natural layout at even n,
-// pulled at odd n), unshifted, in the compute type.
+// Populations of time level n at a fluid cell (natural layout at even n,
+// pulled at odd n) in the compute type, as stored: the in-place precisions
+// give g_i = f_i - w_i (SHIFT), the FP64 plain path f_i.  The moments are
+// summed on these values (macro), so the shift's precision carries into the
+// observables; f_i itself is rebuilt only where it is exported.
 template <class S, bool SHIFT>
 __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain& D, int node,
                                             unsigned long long n, int x, int y, int z,
@@ -821,31 +824,62 @@ __device__ __forceinline__ void gather_pops(const StepParams& P, const DevDomain
                             g);
       }
     }
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) g[i] += W<T>(i);
   }
 }
 
-template <class T>
+// Density and velocity from the populations gather_pops gives (Sec. 2.2:
+// rho = sum_i f_i, rho u = sum_i c_i f_i).  SHIFT: g_i = f_i - w_i, so
+// rho = 1 + sum_i g_i and, as sum_i w_i c_i = 0, rho u = sum_i c_i g_i; both
+// sums run over the small deviations from rest, as in the collision.
+template <class T, bool SHIFT>
 __device__ __forceinline__ void macro(const T g[kQ], T& rho, T& ux, T& uy, T& uz) {
-  rho = T(0);
-  T jx = T(0), jy = T(0), jz = T(0);
+  T m0 = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    rho += g[i];
-    jx += T(CX(i)) * g[i];
-    jy += T(CY(i)) * g[i];
-    jz += T(CZ(i)) * g[i];
+    m0 += g[i];
+    if (CX(i)) jx += CX(i) > 0 ? g[i] : -g[i];
+    if (CY(i)) jy += CY(i) > 0 ? g[i] : -g[i];
+    if (CZ(i)) jz += CZ(i) > 0 ? g[i] : -g[i];
   }
+  rho = SHIFT ? T(1) + m0 : m0;
   ux = jx / rho;
   uy = jy / rho;
   uz = jz / rho;
 }
 
+// |u| in the compute type T from the velocity macro() gives: (ux^2 + uy^2) +
+// uz^2, each operation rounded once (no contraction) and the correctly
+// rounded square root, so a host reproduces it bit for bit from an exported
+// velocity.  The in-place precisions take it in FP32 (the velocity carries
+// FP32 rounding already; an FP64 square root costs the FP64 pipe a dozen
+// operations per node and cell), the FP64 plain path in FP64.
+template <class T>
+__device__ __forceinline__ T speed(T ux, T uy, T uz) {
+  if constexpr (sizeof(T) == 4)
+    return __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), __fmul_rn(uz, uz)));
+  else
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
+}
+
+// mean = S1 / W, std = sqrt(max(S2 / W - mean^2, 0)) (Eq. quad_moments; the
+// clamp guards negative sparse-grid weights), each operation rounded once so
+// that every kernel finishing sums gives the same bits for the same sums.
+__device__ __forceinline__ void finish_moments(double s1, double s2, double wsum, double& mean, double& sd) {
+  mean = __ddiv_rn(s1, wsum);
+  double var = __dsub_rn(__ddiv_rn(s2, wsum), __dmul_rn(mean, mean));
+  if (var < 0.0) var = 0.0;
+  sd = __dsqrt_rn(var);
+}
+
 // Ensemble statistics of |u| per cell (Eq. quad_moments) and the gPC
-// projection (Eq. coef_discrete), FP64 accumulation over the nodes.
-template <class S, bool SHIFT>
-__global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs A) {
+// projection (Eq. coef_discrete): one thread per cell runs over the nodes in
+// order and accumulates in FP64.  PM >= A.P is the compile-time size of the
+// coefficient array (so a small basis holds few registers).  raw: write the
+// sums S1, S2 (and the gPC sums); with accumulate the sums start from the
+// values in the output arrays, so node ranges reduced one after another
+// (waves) give the same bits as one reduction over all nodes.
+template <class S, bool SHIFT, int PM>
+__global__ void __launch_bounds__(256) moments_kernel(const __grid_constant__ StepParams P, MomentArgs A) {
   using T = typename Store<S>::C;
   const DevDomain& D = P.dom[A.domain];
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -856,10 +890,11 @@ __global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs 
     const int y = (int)((c / D.nx) % D.ny);
     const int z = (int)(c / ((long long)D.nx * D.ny));
     const LinkWord lw = __ldg(D.link + c);
-    double s1 = 0.0, s2 = 0.0;
-    double coef[kMaxGpcP];
+    const bool acc = A.raw && A.accumulate;
+    double s1 = acc ? A.mean[c] : 0.0, s2 = acc ? A.stdev[c] : 0.0;
+    double coef[PM > 0 ? PM : 1];
 #pragma unroll
-    for (int a = 0; a < kMaxGpcP; ++a) coef[a] = 0.0;
+    for (int a = 0; a < PM; ++a) coef[a] = (acc && a < A.P) ? A.coef[(long long)a * D.ncell + c] : 0.0;
     if (!(lw & kLinkSolid)) {
       for (int j = 0; j < A.nq; ++j) {
         double q;
@@ -870,31 +905,30 @@ __global__ void moments_kernel(const __grid_constant__ StepParams P, MomentArgs 
           T g[kQ];
           gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
           T rho, ux, uy, uz;
-          macro<T>(g, rho, ux, uy, uz);
+          macro<T, SHIFT>(g, rho, ux, uy, uz);
           if (!(rho > T(0)) || !isfinite(double(ux + uy + uz)) || !isfinite(double(rho))) bad = true;
-          q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+          q = double(speed<T>(ux, uy, uz));
         }
         const double* ab = A.ab + (long long)j * A.stride;
         const double aq = ab[0] * q;
         s1 += aq;
-        s2 += aq * q;
+        s2 = fma(aq, q, s2);
 #pragma unroll
-        for (int a = 0; a < kMaxGpcP; ++a)
-          if (a < A.P) coef[a] += ab[1 + a] * q;
+        for (int a = 0; a < PM; ++a)
+          if (a < A.P) coef[a] = fma(ab[1 + a], q, coef[a]);
       }
     }
     if (A.raw) {
       A.mean[c] = s1;
       A.stdev[c] = s2;
     } else {
-      const double mean = s1 / A.wsum;
-      double var = s2 / A.wsum - mean * mean;
-      if (var < 0.0) var = 0.0;
-      A.mean[c] = mean;
-      A.stdev[c] = sqrt(var);
+      finish_moments(s1, s2, A.wsum, A.mean[c], A.stdev[c]);
     }
-    if (A.coef)
-      for (int a = 0; a < A.P; ++a) A.coef[(long long)a * D.ncell + c] = coef[a];
+    if (A.coef) {
+#pragma unroll
+      for (int a = 0; a < PM; ++a)
+        if (a < A.P) A.coef[(long long)a * D.ncell + c] = coef[a];
+    }
   }
   const unsigned any = __ballot_sync(0xffffffffu, bad);
   if (any && (threadIdx.x & 31) == 0) atomicOr(P.err, kErrDiverged);
@@ -925,8 +959,8 @@ __global__ void profiles_kernel(const __grid_constant__ StepParams P, MomentArgs
         T g[kQ];
         gather_pops<S, SHIFT>(P, D, j, n, x, y, z, c, lw, g);
         T rho, ux, uy, uz;
-        macro<T>(g, rho, ux, uy, uz);
-        q = sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+        macro<T, SHIFT>(g, rho, ux, uy, uz);
+        q = double(speed<T>(ux, uy, uz));
       }
     }
     if (A.prof_nodes) A.prof_nodes[((long long)p * A.nq + j) * D.nz + z] = float(q);
@@ -940,10 +974,8 @@ __global__ void profiles_kernel(const __grid_constant__ StepParams P, MomentArgs
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
   if (lane == 0) {
-    const double mean = s1 / A.wsum;
-    double var = s2 / A.wsum - mean * mean;
-    if (var < 0.0) var = 0.0;
-    const double sd = sqrt(var);
+    double mean, sd;
+    finish_moments(s1, s2, A.wsum, mean, sd);
     double* out = A.prof + ((long long)p * D.nz + z) * 4;
     out[0] = mean;
     out[1] = sd;
@@ -974,10 +1006,10 @@ __global__ void export_kernel(const __grid_constant__ StepParams P, int domain, 
   gather_pops<S, SHIFT>(P, D, node, P.n_host, x, y, z, c, lw, g);
   if (f)
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) f[(long long)i * D.ncell + c] = double(g[i]);
+    for (int i = 0; i < kQ; ++i) f[(long long)i * D.ncell + c] = SHIFT ? double(g[i]) + W<double>(i) : double(g[i]);
   if (u) {
     T rho, ux, uy, uz;
-    macro<T>(g, rho, ux, uy, uz);
+    macro<T, SHIFT>(g, rho, ux, uy, uz);
     u[c] = float(ux);
     u[D.ncell + c] = float(uy);
     u[2 * D.ncell + c] = float(uz);
@@ -1004,8 +1036,8 @@ __global__ void average_add_kernel(const __grid_constant__ StepParams P, int dom
     T g[kQ];
     gather_pops<S, SHIFT>(P, D, j, P.n_host, x, y, z, c, lw, g);
     T rho, ux, uy, uz;
-    macro<T>(g, rho, ux, uy, uz);
-    avg[k] += sqrt(double(ux) * double(ux) + double(uy) * double(uy) + double(uz) * double(uz));
+    macro<T, SHIFT>(g, rho, ux, uy, uz);
+    avg[k] += double(speed<T>(ux, uy, uz));
   }
 }
 
@@ -1068,13 +1100,8 @@ __global__ void qcriterion_kernel(const __grid_constant__ StepParams P, int doma
 // kernel finishes them.
 __global__ void finalize_moments_kernel(const double* __restrict__ s1, const double* __restrict__ s2, double wsum,
                                         double* __restrict__ mean, double* __restrict__ stdev, long long n) {
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    const double m = s1[c] / wsum;
-    double var = s2[c] / wsum - m * m;
-    if (var < 0.0) var = 0.0;
-    mean[c] = m;
-    stdev[c] = sqrt(var);
-  }
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    finish_moments(s1[c], s2[c], wsum, mean[c], stdev[c]);
 }
 
 __global__ void scale_kernel(const double* __restrict__ in, double sc, double* __restrict__ out, long long n) {
@@ -1290,7 +1317,15 @@ int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void
     constexpr bool SH = !std::is_same_v<S, double>;
     const int blk = 256;
     if (A.mean) {
-      moments_kernel<S, SH><<<(unsigned)((D.ncell + blk - 1) / blk), blk, 0, s>>>(P, A);
+      const unsigned grid = (unsigned)((D.ncell + blk - 1) / blk);
+      if (A.P > kMaxGpcP) return (int)cudaErrorInvalidValue;
+      if (A.P == 0) moments_kernel<S, SH, 0><<<grid, blk, 0, s>>>(P, A);
+      else if (A.P <= 3) moments_kernel<S, SH, 3><<<grid, blk, 0, s>>>(P, A);
+      else if (A.P <= 6) moments_kernel<S, SH, 6><<<grid, blk, 0, s>>>(P, A);
+      else if (A.P <= 10) moments_kernel<S, SH, 10><<<grid, blk, 0, s>>>(P, A);
+      else if (A.P <= 15) moments_kernel<S, SH, 15><<<grid, blk, 0, s>>>(P, A);
+      else if (A.P <= 21) moments_kernel<S, SH, 21><<<grid, blk, 0, s>>>(P, A);
+      else moments_kernel<S, SH, kMaxGpcP><<<grid, blk, 0, s>>>(P, A);
       int rc = (int)cudaGetLastError();
       if (rc) return rc;
     }

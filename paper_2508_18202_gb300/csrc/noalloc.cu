@@ -15,16 +15,25 @@
 //
 // The scratch array is a static __device__ symbol: every GPU on which the
 // library's module is loaded holds it (kNoallocScratchBytes, about 8 KB)
-// until the process exits.  Its device address is looked up once per device,
-// by the first call made with that device current; that first call should be
-// made before any stream capture begins.  All calls share the array and it
-// keeps the last call's contents: the counter is cleared at the start of each
-// call, the weight table is overwritten.  Calls whose device work overlaps
-// (different streams without ordering, or several host threads) race on it.
+// until the process exits.  Its device address, and the device's SM count
+// that sizes the grid, are looked up once per device, by the first call made
+// with that device current; that first call should be made before any stream
+// capture begins.  All calls share the array and it keeps the last call's
+// contents: the counter is cleared at the start of each call, the weight
+// table is overwritten.  Calls whose device work overlaps (different streams
+// without ordering, or several host threads) race on it.
+//
+// The weights travel from the caller's host array into the scratch with a
+// cudaMemcpyAsync on the caller's stream.  From pageable memory the runtime
+// stages them before the call returns, so the array may be reused at once;
+// from pinned memory the copy reads the array when the stream reaches it, so
+// the array must stay unchanged until then.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <stdarg.h>
 
 #include <mutex>
 
@@ -44,23 +53,28 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
 
-void put_err(char* err, size_t err_len, const char* fmt, long long a, long long b) {
-  if (err && err_len) snprintf(err, err_len, fmt, a, b);
+// printf-style message into the caller's buffer (nothing when err is NULL).
+void put_err(char* err, size_t err_len, const char* fmt, ...) {
+  if (!err || !err_len) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(err, err_len, fmt, ap);
+  va_end(ap);
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
-int scratch_for_current_device(void** out, char* err, size_t err_len) {
+// Device address of the scratch array and the SM count of the current
+// device (looked up once per device, with that device current).
+int setup_for_current_device(void** out, int* sms, char* err, size_t err_len) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
-    put_err(err, err_len, "cudaGetDevice failed (%lld)%lld", (long long)e, 0);
+    put_err(err, err_len, "cudaGetDevice failed: %s", cudaGetErrorString(e));
     return SC_ERR_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) {
-    put_err(err, err_len, "device ordinal %lld beyond the %lld devices the scratch table covers", dev,
-            kMaxDevices);
+    put_err(err, err_len, "device ordinal %d beyond the %d devices the scratch table covers", dev, kMaxDevices);
     return SC_ERR_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> lock(g_setup_mu);
@@ -68,13 +82,22 @@ int scratch_for_current_device(void** out, char* err, size_t err_len) {
     void* p = nullptr;
     e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
-      put_err(err, err_len, "cudaGetSymbolAddress of the no-alloc scratch failed (%lld) on device %lld",
-              (long long)e, dev);
+      put_err(err, err_len, "cudaGetSymbolAddress of the no-alloc scratch failed on device %d: %s", dev,
+              cudaGetErrorString(e));
       return SC_ERR_CUDA;
     }
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n < 1) {
+      put_err(err, err_len, "cudaDeviceGetAttribute(MultiProcessorCount) failed on device %d: %s", dev,
+              cudaGetErrorString(e));
+      return SC_ERR_CUDA;
+    }
+    g_sm_count[dev] = n;
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
+  *sms = g_sm_count[dev];
   return SC_OK;
 }
 
@@ -114,26 +137,31 @@ extern "C" int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, l
                                            size_t err_len) {
   if (err && err_len) err[0] = '\0';
   if (n_nodes < 1 || n_cells < 0) {
-    put_err(err, err_len, "n_nodes = %lld and n_cells = %lld must be >= 1 and >= 0", n_nodes, n_cells);
+    put_err(err, err_len, "n_nodes = %d and n_cells = %lld must be >= 1 and >= 0", n_nodes, n_cells);
     return SC_ERR_ARG;
   }
   if (n_nodes > kNoallocMaxNodes) {
-    put_err(err, err_len, "n_nodes = %lld exceeds the no-alloc scratch maximum of %lld nodes", n_nodes,
+    put_err(err, err_len, "n_nodes = %d exceeds the no-alloc scratch maximum of %d nodes", n_nodes,
             kNoallocMaxNodes);
     return SC_ERR_SCRATCH;
   }
-  if (!weights || (n_cells > 0 && (!d_field || !d_mean || !d_stdev))) {
-    put_err(err, err_len, "null weights, field or output pointer%lld%lld", 0, 0);
+  if (!weights) {
+    put_err(err, err_len, "null weights");
     return SC_ERR_ARG;
   }
   double wsum = 0.0;
   for (int j = 0; j < n_nodes; ++j) wsum += weights[j];
   if (!(wsum > 0.0) || !isfinite(wsum)) {
-    put_err(err, err_len, "the weights must have a positive finite sum%lld%lld", 0, 0);
+    put_err(err, err_len, "the weights must have a positive finite sum");
+    return SC_ERR_ARG;
+  }
+  if (n_cells > 0 && (!d_field || !d_mean || !d_stdev)) {
+    put_err(err, err_len, "null field or output pointer");
     return SC_ERR_ARG;
   }
   void* base = nullptr;
-  int rc = scratch_for_current_device(&base, err, err_len);
+  int sms = 0;
+  int rc = setup_for_current_device(&base, &sms, err, err_len);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   double* d_w = (double*)base;
@@ -142,8 +170,9 @@ extern "C" int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, l
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_w, weights, sizeof(double) * (size_t)n_nodes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_cells > 0) {
+    // grid-stride loop: at most 8 resident blocks of 256 threads per SM
     long long blocks = (n_cells + 255) / 256;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (blocks > 8LL * sms) blocks = 8LL * sms;
     quad_moments_noalloc_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_field, n_cells, n_nodes, d_w, wsum,
                                                                  d_mean, d_stdev, d_count);
     e = cudaGetLastError();
@@ -151,7 +180,7 @@ extern "C" int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, l
   if (e == cudaSuccess && d_nonfinite)
     e = cudaMemcpyAsync(d_nonfinite, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) {
-    put_err(err, err_len, "CUDA error %lld in the no-alloc moment reduction%lld", (long long)e, 0);
+    put_err(err, err_len, "CUDA error in the no-alloc moment reduction: %s", cudaGetErrorString(e));
     return SC_ERR_CUDA;
   }
   return SC_OK;

@@ -213,6 +213,7 @@ struct MomentArgs {
   const double* avg;       // [nq][ncell] time-accumulated |u|, or null for the current |u|
   double avg_scale;        // 1 / samples
   int raw;                 // 1: write the sums S1, S2 (and gPC sums) into mean / stdev / coef
+  int accumulate;          // with raw: the sums start from the values already in mean / stdev / coef
 };
 int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void* stream);
 int launch_export(const StepParams& P, int precision, int domain, int node, double* d_f,

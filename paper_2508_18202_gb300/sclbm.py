@@ -82,8 +82,9 @@ SIGNATURES = {
     "sc_lbm_step": (C.c_int, [_H, C.c_int]),
     "sc_lbm_moments": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int, _P, _P, _P, C.c_int]),
     "sc_lbm_velocity": (C.c_int, [_H, C.c_int, C.c_int, _P]),
-    "sc_lbm_moment_sums": (C.c_int, [_H, C.c_int, _P, _P, _P]),
+    "sc_lbm_moment_sums": (C.c_int, [_H, C.c_int, _P, _P, _P, C.c_int]),
     "sc_lbm_weight_sum": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
+    "sc_lbm_rule_weight_sum": (C.c_int, [C.POINTER(sc_lbm_config), C.c_int, C.POINTER(C.c_double)]),
     "sc_lbm_moments_from_sums": (C.c_int, [_H, C.c_int, _P, _P, C.c_double, _P, _P]),
     "sc_lbm_average_reset": (C.c_int, [_H]),
     "sc_lbm_average_add": (C.c_int, [_H]),
@@ -276,13 +277,20 @@ def sc_lbm_velocity(h, domain, node, u):
     _call("sc_lbm_velocity", h, domain, node, _ptr(u), handle=h)
 
 
-def sc_lbm_moment_sums(h, domain, s1, s2, gpc_sums=None):
-    _call("sc_lbm_moment_sums", h, domain, _ptr(s1), _ptr(s2), _ptr(gpc_sums), handle=h)
+def sc_lbm_moment_sums(h, domain, s1, s2, gpc_sums=None, accumulate=False):
+    _call("sc_lbm_moment_sums", h, domain, _ptr(s1), _ptr(s2), _ptr(gpc_sums), int(bool(accumulate)),
+          handle=h)
 
 
 def sc_lbm_weight_sum(h, domain):
     w = C.c_double(0.0)
     _call("sc_lbm_weight_sum", h, domain, C.byref(w), handle=h)
+    return w.value
+
+
+def sc_lbm_rule_weight_sum(cfg, domain):
+    w = C.c_double(0.0)
+    _call("sc_lbm_rule_weight_sum", cfg.ref, domain, C.byref(w))
     return w.value
 
 
@@ -306,50 +314,47 @@ def run_in_waves(workload, n_steps, nodes_per_wave, domain=0, gpc=False, prepare
     """An ensemble whose nodes do not fit on the device at once, run in waves:
     the collocation nodes are taken nodes_per_wave at a time, each wave a
     handle over its node range (the runs are independent, Sec. 2.4 step 5)
-    that is stepped n_steps; its moment sums are added on the device and the
-    handle is released before the next wave is made, so one wave's workspace
-    is held at a time.  The last wave's handle finishes the sums.
-    Single-domain workloads.  prepare(ens), if given, is called on every
-    wave's ensemble before it steps (for instance to set an inflow series).
-    Returns dict(mean, std, coef (None without gpc), waves)."""
+    that is stepped n_steps and reduces its nodes into the same FP64 sum
+    arrays (sc_lbm_moment_sums: the first wave overwrites, the later ones
+    accumulate, so the sums carry the bits of one reduction over the whole
+    rule); each handle is released before the next is made, so one wave's
+    workspace is held at a time.  The last wave's handle finishes mean and
+    std with the rule's weight sum.  Single-domain workloads.  prepare(ens),
+    if given, is called on every wave's ensemble before it steps (for
+    instance to set an inflow series).  Returns dict(mean, std, coef (None
+    without gpc), waves)."""
     import torch
     from math import comb
     if len(workload["domains"]) != 1:
         raise ValueError("waves run single-domain workloads")
     if nodes_per_wave < 1:
         raise ValueError("nodes_per_wave must be >= 1")
-    _, a_full = sc_lbm_quadrature(make_config(workload), 0)
+    cfg = make_config(workload)
+    _, a_full = sc_lbm_quadrature(cfg, 0)
     n_total = len(a_full)
+    wsum = sc_lbm_rule_weight_sum(cfg, domain)
     ranges = [(b, min(nodes_per_wave, n_total - b)) for b in range(0, n_total, nodes_per_wave)]
-    s1 = s2 = gs = None
-    wsum = 0.0
+    s1 = s2 = gs = mean = std = None
     for i, (b, c) in enumerate(ranges):
         ens = Ensemble(make_config(workload, node_begin=b, node_count=c))
         try:
             if prepare is not None:
                 prepare(ens)
             ens.step(n_steps)
-            n = ens.ncell(domain)
             if s1 is None:
-                s1 = torch.zeros(n, dtype=torch.float64, device=ens.device)
-                s2 = torch.zeros_like(s1)
+                n = ens.ncell(domain)
+                s1, s2 = ens._out(n), ens._out(n)
                 if gpc:
-                    P = comb(ens.cfg.c.gpc_degree + ens.cfg.c.n_inputs, ens.cfg.c.n_inputs)
-                    gs = torch.zeros((P, n), dtype=torch.float64, device=ens.device)
-            a1, a2 = torch.empty_like(s1), torch.empty_like(s2)
-            ag = torch.empty_like(gs) if gs is not None else None
-            sc_lbm_moment_sums(ens.h, domain, a1, a2, ag)
-            ens.sync()
-            s1 += a1
-            s2 += a2
-            if gs is not None:
-                gs += ag
-            wsum += sc_lbm_weight_sum(ens.h, domain)
+                    gs = ens._out(comb(ens.cfg.c.gpc_degree + ens.cfg.c.n_inputs, ens.cfg.c.n_inputs), n)
+            else:
+                # the sums were written on the previous wave's stream
+                ens.stream.wait_stream(torch.cuda.current_stream(ens.device))
+            sc_lbm_moment_sums(ens.h, domain, s1, s2, gs, accumulate=i > 0)
             if i == len(ranges) - 1:
-                mean, std = torch.empty_like(s1), torch.empty_like(s1)
-                torch.cuda.current_stream(ens.device).synchronize()
+                mean, std = ens._out(s1.shape[0]), ens._out(s1.shape[0])
                 sc_lbm_moments_from_sums(ens.h, domain, s1, s2, wsum, mean, std)
-                ens.sync()
+            ens._hand_over(s1, s2, gs, mean, std)
+            ens.sync()
         finally:
             ens.close()
     return dict(mean=mean, std=std, coef=gs, waves=len(ranges))

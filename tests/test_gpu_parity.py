@@ -607,7 +607,10 @@ def test_ensemble_moments_match_exported_fields(O, cuda):
     cfg = S.make_config(wl)
     Z, a = S.sc_lbm_quadrature(cfg, 0)
     flags = S.sc_lbm_geometry(cfg, 0)
-    Qv = np.stack([np.sqrt((ens.velocity(0, j).double().cpu().numpy() ** 2).sum(0)) for j in range(len(a))])
+    # |u| as the library forms it from its FP32 velocity: (ux^2 + uy^2) + uz^2
+    # and the square root, each rounded once in FP32
+    us = [ens.velocity(0, j).cpu().numpy() for j in range(len(a))]
+    Qv = np.stack([np.sqrt((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]).astype(np.float64) for u in us])
     Qv[:, flags != 0] = 0.0
     mean, std, _ = O.moments_two_pass(a, Qv)
     cols = S.sc_lbm_probe_columns(cfg, 0, 4)

@@ -178,6 +178,52 @@ def test_profiles_band(O):
             assert abs(prof[p, z, 3] - (e + 1.959963984540054 * s)) < 1e-15
 
 
+def test_profiles_band_factor_is_the_normal_quantile(O):
+    """The 95% band half-width is Phi^-1(0.975) std: the factor the oracle
+    applies, recovered from its output, equals the standard normal quantile
+    computed here independently (statistics.NormalDist)."""
+    from statistics import NormalDist
+    z975 = NormalDist().inv_cdf(0.975)
+    a = np.array([0.5, 0.5])
+    Qv = np.array([[1.0], [3.0]])          # mean 2, std 1 exactly
+    prof, _ = O.profiles(a, Qv, 1, 1, 1, np.array([[0, 0]], np.int32))
+    assert prof[0, 0, 0] == 2.0 and prof[0, 0, 1] == 1.0
+    assert abs((prof[0, 0, 3] - prof[0, 0, 0]) - z975) < 1e-12
+    assert abs((prof[0, 0, 0] - prof[0, 0, 2]) - z975) < 1e-12
+
+
+def test_profiles_pick_the_probe_column(O):
+    """Hand-worked field: Q_0(x, y, z) = x + 10 y + 100 z, Q_1 = Q_0 + 4 with
+    weights (1/4, 3/4), so at every cell mean = Q_0 + 3 and
+    var = (1/4) 9 + (3/4) 1 = 3.  The profile of column (x, y) = (2, 1) on a
+    3 x 2 x 4 grid is then mean 2 + 10 + 3 + 100 z = 15 + 100 z and std
+    sqrt(3) in every layer; a transposed index (x <-> y) or a wrong layer
+    stride would give other numbers."""
+    nx, ny, nz = 3, 2, 4
+    x, y, z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    q0 = np.zeros(nx * ny * nz)
+    q0[(x + nx * (y + ny * z)).ravel()] = (x + 10 * y + 100 * z).ravel()
+    Qv = np.stack([q0, q0 + 4.0])
+    a = np.array([0.25, 0.75])
+    prof, pn = O.profiles(a, Qv, nx, ny, nz, np.array([[2, 1]], np.int32))
+    for k in range(nz):
+        assert prof[0, k, 0] == 15.0 + 100.0 * k
+        assert abs(prof[0, k, 1] - math.sqrt(3.0)) < 1e-14
+        assert pn[0, 0, k] == 12.0 + 100.0 * k and pn[0, 1, k] == 16.0 + 100.0 * k
+
+
+def test_node_inflow_params_maps_inputs_by_kind(O):
+    """A node's coordinates replace the speed error, exponent and angle by
+    input kind, in the order the configuration lists the inputs; the others
+    keep the nominal values."""
+    Zj = np.array([0.07, 0.31, -4.0])
+    kinds = [O.IN_SPEED_REL, O.IN_ALPHA, O.IN_ANGLE_DEG]
+    assert O.node_inflow_params(Zj, kinds, 0.05, 0.25, 10.0) == (0.07, 0.31, -4.0)
+    assert O.node_inflow_params(Zj, kinds[::-1], 0.05, 0.25, 10.0) == (-4.0, 0.31, 0.07)
+    assert O.node_inflow_params(Zj[:1], [O.IN_ALPHA], 0.05, 0.25, 10.0) == (0.0, 0.07, 10.0)
+    assert O.node_inflow_params(Zj[:0], [], 0.05, 0.25, 10.0) == (0.0, 0.25, 10.0)
+
+
 def test_gpc_closed_form_coefficients_1d(O):
     """s^2 = (1/3) Phi_0 + 2/(3 sqrt 5) Phi_2 for orthonormal Legendre Phi."""
     lo, hi = [-0.1], [0.1]
