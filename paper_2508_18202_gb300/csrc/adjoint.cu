@@ -182,8 +182,18 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
       const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
       const long long pc = D.pitch;
       float ls[kQ];
+      if (lw == 0) {
+        // every delivery streams: lambda*_k(x) = lambda^{n+1}_k(x + c_k)
+        const int sy = D.nx, sz = D.nx * D.ny;
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) ls[k] = lam_next[(long long)k * pc + c + (CX(k) + CY(k) * sy + CZ(k) * sz)];
+      } else {
+        float lg[kQ];
 #pragma unroll 1
-      for (int k = 0; k < kQ; ++k) ls[k] = gather_deliveries(D, lam_next, k, x, y, z, c, lw);
+        for (int k = 0; k < kQ; ++k) lg[k] = gather_deliveries(D, lam_next, k, x, y, z, c, lw);
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) ls[k] = lg[k];
+      }
       // forward state of this level
       float rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll

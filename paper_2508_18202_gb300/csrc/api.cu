@@ -310,6 +310,10 @@ struct sc_lbm_s {
   const double* avg_read = nullptr;           // set while the moments read the time average
   std::string err;
   cudaGraphExec_t graph = nullptr;
+  // the adjoint's sweeps captured as one graph, replayed while its
+  // arguments (domain, step and checkpoint counts, workspace) stay the same
+  cudaGraphExec_t adj_graph = nullptr;
+  std::vector<long long> adj_key;
   int graph_len = 0;
   Wind<float> graph_wind{};                   // the inflow factor the graph was captured with
   // time-varying inflow (empty: steady): speed factors, continuous
@@ -320,6 +324,7 @@ struct sc_lbm_s {
   int never_arrive = 0;
   long long spin_limit = kSpinLimit;
   int tma_ok = 0;  // every domain's rows meet the 16-byte alignment of bulk copies
+  int pair_ok = 0; // every domain has an even nx (pair forms)
   Header* hdr() const { return reinterpret_cast<Header*>(ws + L.hdr); }
 };
 
@@ -348,9 +353,13 @@ void apply_tiling(sc_lbm_t h) {
   P.bz = h->tune.slab_z;
   P.order = h->tune.tile_order;
   long long begin = 0, bbegin = 0, rbegin = 0;
+  // pair forms: two x-adjacent cells per thread (launch and graph modes)
+  P.pair = ((h->tune.variant == 4 || h->tune.variant == 5) && h->pair_ok &&
+            h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
+  const int tile_x = P.bx * (P.pair ? 2 : 1);
   for (int d = 0; d < P.n_domains; ++d) {
     DevDomain& D = P.dom[d];
-    D.tiles_x = (D.nx + P.bx - 1) / P.bx;
+    D.tiles_x = (D.nx + tile_x - 1) / tile_x;
     D.tiles_y = (D.ny + P.by - 1) / P.by;
     D.tiles_z = (D.nz + P.bz - 1) / P.bz;
     D.tiles_per_node = D.tiles_x * D.tiles_y * D.tiles_z;
@@ -366,8 +375,8 @@ void apply_tiling(sc_lbm_t h) {
   P.total_bitems = bbegin;
   P.total_runs = rbegin;
   P.tma = (h->tune.variant == 1 && h->tma_ok && h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
-  P.even85 = h->tune.variant == 2 ? 1 : 0;
-  P.odd85 = (h->tune.variant == 2 || h->tune.variant == 3) ? 1 : 0;
+  P.even85 = (h->tune.variant == 2 || h->tune.variant == 5) ? 1 : 0;
+  P.odd85 = (h->tune.variant == 2 || h->tune.variant == 3 || h->tune.variant == 5) ? 1 : 0;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -383,7 +392,7 @@ int check_tuning(const sc_lbm_tuning& t) {
   if (t.tile_order < 0 || t.tile_order > 1) return SC_ERR_ARG;
   if (t.exec_mode < SC_EXEC_LAUNCH || t.exec_mode > SC_EXEC_PERSISTENT) return SC_ERR_ARG;
   if (t.graph_steps < 1 || t.graph_steps > 100000) return SC_ERR_ARG;
-  if (t.variant < 0 || t.variant > 3) return SC_ERR_ARG;
+  if (t.variant < 0 || t.variant > 5) return SC_ERR_ARG;
   return SC_OK;
 }
 
@@ -796,6 +805,9 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   h->tma_ok = c.precision != SC_P_FP64_PLAIN;
   for (int d = 0; d < c.n_domains; ++d)
     if (c.domains[d].nx % (int)(16 / storage_bytes(c.precision)) != 0) h->tma_ok = 0;
+  h->pair_ok = c.precision != SC_P_FP64_PLAIN;
+  for (int d = 0; d < c.n_domains; ++d)
+    if (c.domains[d].nx % 2 != 0) h->pair_ok = 0;
   // default launch shape
   h->tune.variant = 0;
   h->tune.block_x = 64;
@@ -1125,21 +1137,6 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   }
   int maxnx = 0;
   for (int d = 0; d < h->P.n_domains; ++d) maxnx = std::max(maxnx, h->P.dom[d].nx);
-  std::vector<sc_lbm_tuning> cand;
-  const int bxs[] = {32, 64, 128, 256};
-  const int bys[] = {1, 2, 4, 8};
-  const int bzs[] = {1, 2, 4, 8};
-  for (int bx : bxs) {
-    if (bx > 32 && bx / 2 >= maxnx) continue;
-    for (int by : bys)
-      for (int bz : bzs) {
-        if (bx * by > 256 || bx * by < 64) continue;
-        for (int order = 0; order < 2; ++order)
-          for (int v : {0, 2, 3}) cand.push_back({bx, by, bz, order, SC_EXEC_LAUNCH, 50, v});
-      }
-  }
-  if (h->tma_ok)
-    for (int order = 0; order < 2; ++order) cand.push_back({128, 2, 1, order, SC_EXEC_LAUNCH, 50, 1});
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1161,18 +1158,62 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
     CK(cudaEventElapsedTime(ms, e0, e1));
     return SC_OK;
   };
-  for (const auto& t : cand) {
-    float ms = 0;
-    int rc = time_it(t, &ms);
-    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-    if (ms < best) { best = ms; best_t = t; }
+  struct Timed {
+    float ms;
+    sc_lbm_tuning t;
+  };
+  std::vector<Timed> timed;
+  auto try_all = [&](const std::vector<sc_lbm_tuning>& cand) -> int {
+    for (const auto& t : cand) {
+      float ms = 0;
+      int rc = time_it(t, &ms);
+      if (rc) return rc;
+      timed.push_back({ms, t});
+      if (ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+    return SC_OK;
+  };
+  // stage 1: block shape and z-slab, one-cell and pair forms, patch-major order
+  std::vector<sc_lbm_tuning> cand;
+  const int bxs[] = {32, 64, 128, 256};
+  const int bys[] = {1, 2, 4, 8};
+  const int bzs[] = {2, 4, 8, 16, 32};
+  for (int bx : bxs) {
+    for (int by : bys)
+      for (int bz : bzs) {
+        if (bx * by > 256 || bx * by < 64) continue;
+        if (bx > 32 && bx / 2 >= maxnx) continue;
+        cand.push_back({bx, by, bz, 1, SC_EXEC_LAUNCH, 50, 0});
+        if (h->pair_ok && bx < maxnx) cand.push_back({bx, by, bz, 1, SC_EXEC_LAUNCH, 50, 4});
+      }
   }
+  int rc = try_all(cand);
+  if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+  // stage 2: register budgets and tile order on the three fastest shapes
+  std::sort(timed.begin(), timed.end(), [](const Timed& a, const Timed& b) { return a.ms < b.ms; });
+  cand.clear();
+  for (size_t k = 0; k < timed.size() && k < 3; ++k) {
+    const sc_lbm_tuning t = timed[k].t;
+    const bool pair = t.variant == 4;
+    for (int order = 0; order < 2; ++order)
+      for (int v : pair ? std::vector<int>{4, 5} : std::vector<int>{0, 2, 3}) {
+        if (order == t.tile_order && v == t.variant) continue;
+        cand.push_back({t.block_x, t.block_y, t.slab_z, order, SC_EXEC_LAUNCH, 50, v});
+      }
+  }
+  if (h->tma_ok)
+    for (int order = 0; order < 2; ++order) cand.push_back({128, 2, 1, order, SC_EXEC_LAUNCH, 50, 1});
+  rc = try_all(cand);
+  if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
   // execution mode for the best shape
   for (int mode : {SC_EXEC_GRAPH, SC_EXEC_PERSISTENT}) {
     sc_lbm_tuning t = best_t;
     t.exec_mode = mode;
-    if (mode == SC_EXEC_PERSISTENT && t.variant == 1) {
-      t.variant = 0;  // the persistent form loads per thread
+    if (mode == SC_EXEC_PERSISTENT && t.variant != 0 && t.variant != 2 && t.variant != 3) {
+      t.variant = 0;  // the persistent form loads one cell per thread
       t.block_x = 64;
       t.block_y = 2;
     }
@@ -1183,7 +1224,7 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int rc = sc_lbm_set_tuning(h, &best_t);
+  rc = sc_lbm_set_tuning(h, &best_t);
   if (rc) return rc;
   rc = reset_state(h);
   if (rc) return rc;
@@ -1537,43 +1578,78 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
   const long long nstate = (long long)kQ * D.pitch;
   const StepParams& P = h->P;
   auto ck = [&](int r, const char* what) { return r ? cuda_fail(h, (cudaError_t)r, what) : SC_OK; };
-  // forward sweep with checkpoints every L steps, equilibrium start
-  if ((rc = ck(launch_fill_zero(fa, nstate, h->stream), "adjoint fill"))) return rc;
-  if ((rc = ck(launch_fill_zero(fb, nstate, h->stream), "adjoint fill"))) return rc;
-  float* cur = fa;
-  float* nxt = fb;
-  for (int n = 0; n < n_steps; ++n) {
-    if (n % L.L == 0)
-      CK(cudaMemcpyAsync(snap0 + (size_t)(n / L.L) * (L.state_bytes / sizeof(float)), cur,
-                         sizeof(float) * nstate, cudaMemcpyDeviceToDevice, h->stream));
-    if ((rc = ck(launch_adj_forward(P, A, cur, nxt, (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
-                 "adjoint forward")))
-      return rc;
-    std::swap(cur, nxt);
-  }
-  // loss and seed at level T
-  if ((rc = ck(launch_fill_zero(lamA, nstate, h->stream), "adjoint fill"))) return rc;
-  if ((rc = ck(launch_fill_zero(lamB, nstate, h->stream), "adjoint fill"))) return rc;
-  if ((rc = ck(launch_adj_loss(P, A, cur, lamA, h->stream), "adjoint loss"))) return rc;
-  float* lnext = lamA;
-  float* lcur = lamB;
+  // The device work of one gradient: forward sweep with checkpoints every L
+  // steps from the equilibrium start, loss and seed at level T, then per
+  // segment (last first) the recompute of its states and the reverse steps.
   const size_t sf = L.state_bytes / sizeof(float);
-  for (int sgm = L.K - 1; sgm >= 0; --sgm) {
-    const int n0 = sgm * L.L, n1 = std::min(n0 + L.L, n_steps);
-    CK(cudaMemcpyAsync(seg0, snap0 + (size_t)sgm * sf, sizeof(float) * nstate, cudaMemcpyDeviceToDevice,
-                       h->stream));
-    for (int n = n0; n < n1 - 1; ++n)
-      if ((rc = ck(launch_adj_forward(P, A, seg0 + (size_t)(n - n0) * sf, seg0 + (size_t)(n - n0 + 1) * sf,
-                                      (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
-                   "adjoint recompute")))
-        return rc;
-    for (int n = n1 - 1; n >= n0; --n) {
-      if ((rc = ck(launch_adj_step(P, A, seg0 + (size_t)(n - n0) * sf, lnext, lcur,
-                                   (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
-                   "adjoint step")))
-        return rc;
-      std::swap(lnext, lcur);
+  auto issue = [&]() -> int {
+    int r;
+    if ((r = ck(launch_fill_zero(fa, nstate, h->stream), "adjoint fill"))) return r;
+    if ((r = ck(launch_fill_zero(fb, nstate, h->stream), "adjoint fill"))) return r;
+    float* cur = fa;
+    float* nxt = fb;
+    for (int n = 0; n < n_steps; ++n) {
+      if (n % L.L == 0)
+        CK(cudaMemcpyAsync(snap0 + (size_t)(n / L.L) * sf, cur, sizeof(float) * nstate, cudaMemcpyDeviceToDevice,
+                           h->stream));
+      if ((r = ck(launch_adj_forward(P, A, cur, nxt, (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
+                  "adjoint forward")))
+        return r;
+      std::swap(cur, nxt);
     }
+    if ((r = ck(launch_fill_zero(lamA, nstate, h->stream), "adjoint fill"))) return r;
+    if ((r = ck(launch_fill_zero(lamB, nstate, h->stream), "adjoint fill"))) return r;
+    if ((r = ck(launch_adj_loss(P, A, cur, lamA, h->stream), "adjoint loss"))) return r;
+    float* lnext = lamA;
+    float* lcur = lamB;
+    for (int sgm = L.K - 1; sgm >= 0; --sgm) {
+      const int n0 = sgm * L.L, n1 = std::min(n0 + L.L, n_steps);
+      CK(cudaMemcpyAsync(seg0, snap0 + (size_t)sgm * sf, sizeof(float) * nstate, cudaMemcpyDeviceToDevice,
+                         h->stream));
+      for (int n = n0; n < n1 - 1; ++n)
+        if ((r = ck(launch_adj_forward(P, A, seg0 + (size_t)(n - n0) * sf, seg0 + (size_t)(n - n0 + 1) * sf,
+                                       (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
+                    "adjoint recompute")))
+          return r;
+      for (int n = n1 - 1; n >= n0; --n) {
+        if ((r = ck(launch_adj_step(P, A, seg0 + (size_t)(n - n0) * sf, lnext, lcur,
+                                    (float)hn_ramp(h->cfg.ramp_steps, n + 1), h->stream),
+                    "adjoint step")))
+          return r;
+        std::swap(lnext, lcur);
+      }
+    }
+    return SC_OK;
+  };
+  // Replays of one captured graph while the arguments that shape the sweep
+  // stay the same (the node's inflow tables, probes and targets are read
+  // from the workspace, uploaded above); the legacy default stream cannot
+  // be captured and runs the launches directly.
+  const std::vector<long long> key = {domain, n_steps, L.K, L.L, n_probes, (long long)(uintptr_t)d_ws,
+                                      (long long)bytes, h->cfg.ramp_steps};
+  if (h->stream) {
+    if (!h->adj_graph || h->adj_key != key) {
+      if (h->adj_graph) cudaGraphExecDestroy(h->adj_graph);
+      h->adj_graph = nullptr;
+      h->adj_key.clear();
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      rc = issue();
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture (adjoint)");
+      e = cudaGraphInstantiate(&h->adj_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate (adjoint)");
+      h->adj_key = key;
+    }
+    CK(cudaGraphLaunch(h->adj_graph, h->stream));
+  } else {
+    rc = issue();
+    if (rc) return rc;
   }
   h->launches += 2LL * n_steps + (n_steps - L.K) + 5;
   double acc[3];
@@ -1599,6 +1675,7 @@ int sc_lbm_destroy(sc_lbm_t h) {
   if (!h) return SC_ERR_ARG;
   cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->adj_graph) cudaGraphExecDestroy(h->adj_graph);
   delete h;
   return SC_OK;
 }

@@ -138,6 +138,7 @@ struct StepParams {
   long long total_runs;        // runs of kRun cells of all domains and nodes
   int tma;                     // bulk kernels staged through shared memory by TMA
   int odd85, even85;           // per-thread odd / even kernels sized for 3 blocks (85 registers)
+  int pair;                    // two x-adjacent cells per thread (tiles of 2 * bx cells in x)
   int bx, by, bz, order;
   // persistent mode
   unsigned int* bar_count;

@@ -65,17 +65,22 @@ def cuda():
 
 @pytest.mark.parametrize("collision", [W.BGK, W.RR], ids=["bgk", "rr"])
 @pytest.mark.parametrize("bcname", list(BC_SETS))
-@pytest.mark.parametrize("precision,tol,nx", [(W.FP32_SHIFT, 2e-6, 37), (W.FP32_SHIFT, 2e-6, 40),
-                                              (W.FP64_PLAIN, 1e-13, 37)])
-def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx, collision):
+@pytest.mark.parametrize("precision,tol,nx,variant", [(W.FP32_SHIFT, 2e-6, 37, 0), (W.FP32_SHIFT, 2e-6, 40, 1),
+                                                      (W.FP32_SHIFT, 2e-6, 38, 4), (W.FP32_SHIFT, 2e-6, 38, 5),
+                                                      (W.FP64_PLAIN, 1e-13, 37, 0)])
+def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx, variant, collision):
     """Populations after 1..6 and 31 steps (both AA parities) at every fluid
-    cell and node, max abs difference, for both collision forms.  nx = 40 runs
-    the TMA-staged kernels (partial last run of 256 cells), nx = 37 the
-    per-thread ones."""
+    cell and node, max abs difference, for both collision forms.  Variant 1
+    (nx = 40) runs the TMA-staged kernels (partial last run of 256 cells),
+    variants 4 and 5 (nx = 38) the two-cells-per-thread forms with both
+    register budgets (a partial last warp of pairs in x), variant 0 (nx = 37)
+    the one-cell ones."""
     wl = ragged(BC_SETS[bcname], precision=precision, nx=nx, collision=collision)
     ens = S.Ensemble(S.make_config(wl))
-    if nx == 40:
+    if variant == 1:
         S.sc_lbm_set_tuning(ens.h, 128, 2, 1, variant=1)
+    elif variant in (4, 5):
+        S.sc_lbm_set_tuning(ens.h, 32, 2, 3, variant=variant)
     p, flags = oracle_domain(O, wl)
     Z, a = oracle_nodes(O, wl)
     fl = fluid_mask(flags)
@@ -94,14 +99,15 @@ def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx, colli
     ens.close()
 
 
+@pytest.mark.parametrize("variant", [1, 4])
 @pytest.mark.parametrize("precision", [W.BF16_STORE, W.FP16_STORE])
-def test_reduced_storage_tracks_oracle(O, cuda, precision):
+def test_reduced_storage_tracks_oracle(O, cuda, precision, variant):
     """BF16 / FP16 storage of the shifted populations: error report against
     FP64 after 40 steps (bounded, not bit-level); nx = 40 runs the TMA-staged
-    kernels with 2-byte elements."""
+    kernels (variant 1) or the pair forms (variant 4) with 2-byte elements."""
     wl = ragged(BC_SETS["urban"], precision=precision, nx=40)
     ens = S.Ensemble(S.make_config(wl))
-    S.sc_lbm_set_tuning(ens.h, 128, 2, 1, variant=1)
+    S.sc_lbm_set_tuning(ens.h, 128 if variant == 1 else 32, 2, 1 if variant == 1 else 4, variant=variant)
     ens.step(40)
     p, flags, f = oracle_run_node(O, wl, 0, 1, 40)
     _, uo = O.macros(p, flags, f)
@@ -283,31 +289,64 @@ def test_paper_case_full_size(O, cuda):
     """The paper's configuration at full size on one GPU (disk of radius 270
     and height 40, 121 Gauss-Hermite nodes, regularized collision, C_S =
     0.25, Re = 1.8e6; 107 GB of populations) in the launch configuration
-    bench.py times it in: the first node (an extreme one of the rule) after
-    40 steps against the oracle (relative L2 of u <= 1e-3, the LES bound), and
-    no non-finite or non-positive density.  Early in the start-up ramp the
-    velocities are small (1e-5 at level 40, 1e-6 at level 20), and FP32
-    rounding of the O(1) density is what the comparison sees: 1.4e-3 of u at
-    level 20, a quarter of that at level 40."""
+    bench.py times it in: the first, middle and last nodes (the two extremes
+    of the rule and its centre) at levels 20 and 100 against the oracle
+    (relative L2 of u <= 1e-3, the LES bound), and no non-finite or
+    non-positive density.  The velocities are small early in the start-up
+    ramp (about 1e-6 at level 20); the observables are summed on the shifted
+    populations, so FP32 rounding of the O(1) density does not enter them."""
     wl = W.URBAN_DISK_PAPER
     ens = S.Ensemble(S.make_config(wl))      # the default launch configuration, as bench.py's leg
-    steps = 40
-    ens.step(steps)
-    assert S.sc_lbm_check(ens.h) == (S.SC_OK, 0)
     p, flags = oracle_domain(O, wl)
     Z, a = oracle_nodes(O, wl)
     assert len(a) == 121
     D = wl["domains"][0]
     fl = fluid_mask(flags)
-    for j in (0,):
+    nodes = (0, 60, 120)
+    fo = {j: O.init_equilibrium(p, flags) for j in nodes}
+    uins = {}
+    for j in nodes:
         xi, al, th = O.node_inflow_params(Z[j], wl["inputs"], wl["u_ref"], wl["alpha"], wl["angle_deg"])
-        uin = O.inflow_log(D["nz"], wl["u_ref"], xi, wl["z0"], D["nz"], th)
-        f = O.init_equilibrium(p, flags)
-        O.run(p, flags, uin, f, 0, steps)
-        uo = O.macros(p, flags, f)[1]
-        del f
-        ug = ens.velocity(0, j).cpu().numpy()
-        assert rel_l2(ug[:, fl], uo[:, fl]) <= 1e-3, j
+        uins[j] = O.inflow_log(D["nz"], wl["u_ref"], xi, wl["z0"], D["nz"], th)
+    done = 0
+    for level in (20, 100):
+        ens.step(level - done)
+        assert S.sc_lbm_check(ens.h) == (S.SC_OK, 0)
+        for j in nodes:
+            O.run(p, flags, uins[j], fo[j], done, level - done)
+            uo = O.macros(p, flags, fo[j])[1]
+            ug = ens.velocity(0, j).cpu().numpy()
+            err = rel_l2(ug[:, fl], uo[:, fl])
+            assert err <= 1e-3, (level, j, err)
+        done = level
+    ens.close()
+
+
+def test_les_full_size_ensemble_fields_100_steps(O, cuda):
+    """The 13-node urban LES ensemble at full size (256x128x64, BGK +
+    Smagorinsky) in the benchmark's launch shape: mean, std and the profile
+    bands of |u| after 100 steps against the oracle's own 13 runs and its
+    two-pass reduction (relative L2 over fluid cells <= 1e-3, the ensemble
+    bound)."""
+    wl = W.URBAN_LES
+    ens = S.Ensemble(S.make_config(wl))
+    S.sc_lbm_autotune(ens.h, None)
+    ens.step(100)
+    cfg = S.make_config(wl)
+    cols = S.sc_lbm_probe_columns(cfg, 0, wl["n_columns"])
+    out = ens.moments(0, probes=cols, gpc=True)
+    p, flags = oracle_domain(O, wl)
+    Z, a = oracle_nodes(O, wl)
+    Qv = O.ensemble(p, flags, Z, wl["inputs"], wl["u_ref"], wl["alpha"], 0.0, p.nz, 100)
+    mean, std, _ = O.moments_two_pass(a, Qv)
+    prof, _ = O.profiles(a, Qv, p.nx, p.ny, p.nz, cols)
+    fl = fluid_mask(flags)
+    assert rel_l2(out["mean"].cpu().numpy()[fl], mean[fl]) <= 1e-3
+    assert rel_l2(out["std"].cpu().numpy()[fl], std[fl]) <= 1e-3
+    assert rel_l2(out["prof"].cpu().numpy(), prof) <= 1e-3
+    coef = O.gpc_project(a, Qv, O.gpc_basis(2, wl["gpc_degree"], O.legendre_s(Z, wl["lo"], wl["hi"])))
+    cg = out["coef"].cpu().numpy()
+    assert rel_l2(cg[0][fl], coef[0][fl]) <= 1e-3
     ens.close()
 
 
@@ -489,19 +528,20 @@ def test_launch_shapes_and_modes_are_bitwise_identical(cuda, shape):
     TMA-staged) gives the same bits."""
     wl = ragged(BC_SETS["urban"], nx=40)
     want = {}
-    for variant in (0, 1, 2, 3):
+    variants = (0, 1, 2, 3, 4, 5)
+    for variant in variants:
         ref = S.Ensemble(S.make_config(wl))
         S.sc_lbm_set_tuning(ref.h, 64, 1, 1, variant=variant)
         ref.step(17)
         want[variant] = _states(ref)
         ref.close()
-    # the two kernel forms are compiled separately (rounding may differ in the
+    # the kernel forms are compiled separately (rounding may differ in the
     # last bit); within a form every shape and mode is bitwise identical
-    for v in (1, 2, 3):
+    for v in variants[1:]:
         for a, b in zip(want[0], want[v]):
             assert np.max(np.abs(a - b)) < 1e-6
     for mode in (S.SC_EXEC_LAUNCH, S.SC_EXEC_GRAPH, S.SC_EXEC_PERSISTENT):
-        for variant in (0, 1, 2, 3):
+        for variant in variants:
             ens = S.Ensemble(S.make_config(wl))
             S.sc_lbm_set_tuning(ens.h, *shape, exec_mode=mode, graph_steps=4, variant=variant)
             ens.step(17)
