@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--tuning", default="",
                     help="fixed launch shape block_x,block_y,slab_z,tile_order,exec_mode,graph_steps,variant "
                          "instead of the autotuner")
+    ap.add_argument("--leg", default="",
+                    help="run only this extra leg (plain, les, batched, rr, series, paper, adjoint) and print its "
+                         "result (profiling runs)")
     return ap.parse_args()
 
 
@@ -592,6 +595,32 @@ def leg_cpu(wl_head):
             "host": host_info()}
 
 
+def one_leg(args, S, W, torch, np):
+    """A single extra leg, alone (for profiling its kernels)."""
+    peak, _ = peaks()
+    cx = Ctx(S, W, torch, np, peak, None)
+    prec = {"fp32": W.FP32_SHIFT, "bf16": W.BF16_STORE, "fp16": W.FP16_STORE}[args.precision]
+    name = args.leg
+    if name == "plain":
+        r = leg_plain(cx, workload_for(args), float("nan"))
+    elif name == "les":
+        r = leg_ensemble(cx, "urban_les_256x128x64_cc3", 20, [(args.precision, prec)], 20, 10)
+    elif name == "batched":
+        r = leg_ensemble(cx, "urban_batched_3domains", 20, [(args.precision, prec)], 20, 10)
+    elif name == "rr":
+        r = leg_rr(cx)
+    elif name == "series":
+        r = leg_series(cx)
+    elif name == "paper":
+        r = leg_paper(cx)
+    elif name == "adjoint":
+        r = leg_adjoint(cx)
+    else:
+        raise SystemExit("unknown leg " + name)
+    print(json.dumps({"leg": name, "result": r}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -607,6 +636,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.leg:
+        return one_leg(args, S, W, torch, np)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     skip = set(s for s in args.skip.split(",") if s)

@@ -169,7 +169,7 @@ void equilibrium(const T& rho, const T u[3], T feq[Q]) {
 // that the lattice moments sum_i h_k(c_i) f_i reproduce A_k exactly.
 const double CS2 = 1.0 / 3.0;
 
-double hermite2(int i, int a, int b) {
+double hermite2_of(int i, int a, int b) {
   return (double)(comp(i, a) * comp(i, b)) - (a == b ? CS2 : 0.0);
 }
 
@@ -185,17 +185,39 @@ double hermite3(int i, int a, int b, int g) {
 // index triples (x,x,y)/(y,z,z), (x,z,z)/(x,y,y), (y,y,z)/(x,x,z).
 const int TRIP[3][2][3] = {{{0, 0, 1}, {1, 2, 2}}, {{0, 2, 2}, {0, 1, 1}}, {{1, 1, 2}, {0, 0, 2}}};
 
-double hermite3_comb(int i, int k) {
+double hermite3_comb_of(int i, int k) {
   const int (*t)[3] = TRIP[k % 3];
   const double s = k < 3 ? 1.0 : -1.0;
   return hermite3(i, t[0][0], t[0][1], t[0][2]) + s * hermite3(i, t[1][0], t[1][1], t[1][2]);
 }
 
-double hermite3_norm(int k) {
-  double n = 0.0;
-  for (int i = 0; i < Q; ++i) n += weight(i) * hermite3_comb(i, k) * hermite3_comb(i, k);
-  return n;
+// The values above depend only on the lattice: they are evaluated once, by
+// the same expressions, and looked up per cell.
+struct HermiteTables {
+  double h2[Q][3][3];
+  double h3[Q][6];
+  double n3[6];
+  HermiteTables() {
+    for (int i = 0; i < Q; ++i) {
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) h2[i][a][b] = hermite2_of(i, a, b);
+      for (int k = 0; k < 6; ++k) h3[i][k] = hermite3_comb_of(i, k);
+    }
+    for (int k = 0; k < 6; ++k) {
+      double n = 0.0;
+      for (int i = 0; i < Q; ++i) n += weight(i) * h3[i][k] * h3[i][k];
+      n3[k] = n;
+    }
+  }
+};
+const HermiteTables& hermite_tables() {
+  static const HermiteTables t;
+  return t;
 }
+
+double hermite2(int i, int a, int b) { return hermite_tables().h2[i][a][b]; }
+double hermite3_comb(int i, int k) { return hermite_tables().h3[i][k]; }
+double hermite3_norm(int k) { return hermite_tables().n3[k]; }
 
 // The combination k of a symmetric third-order tensor a[3][3][3].
 template <class T>

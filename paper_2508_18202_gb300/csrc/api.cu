@@ -39,6 +39,7 @@ struct DomLayout {
   size_t guard = 0;
   long long nb_max = 0;
   size_t flags = 0, link = 0, cls = 0, bcell = 0, ltab = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
+  size_t abf = 0;  // [nq][P] float pairs (hi, lo) of a_j Phi_alpha(Z_j): the compensated gPC sums
   size_t avg = 0;  // time-averaged |u| accumulators [nq][ncell] (FP64), when configured
 };
 struct Layout {
@@ -195,6 +196,7 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     if (c->precision == SC_P_FP64_PLAIN) M.g2 = take(sb * kQ * (size_t)M.pitch * M.nq);
     else M.bout = take(sizeof(float) * 5 * (size_t)D.nz * D.ny * M.nq);
     M.ab = take(sizeof(double) * (size_t)M.nq * (P + 1));
+    M.abf = take(2 * sizeof(float) * (size_t)M.nq * (P > 0 ? P : 1));
     if (c->time_average) M.avg = take(sizeof(double) * (size_t)M.nq * (size_t)M.ncell);
     max_cell = std::max(max_cell, M.ncell);
     max_nz = std::max(max_nz, D.nz);
@@ -725,6 +727,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   std::vector<std::vector<int32_t>> ltab_words(c.n_domains);
   std::vector<std::vector<float>> uinf(c.n_domains);
   std::vector<std::vector<double>> uind(c.n_domains), abt(c.n_domains);
+  std::vector<std::vector<float>> abft(c.n_domains);
   h->wsum.assign(c.n_domains, 0.0);
   h->nq.assign(c.n_domains, 0);
   for (int d = 0; d < c.n_domains; ++d) {
@@ -842,6 +845,19 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     if (e == cudaSuccess) e = up(M.uin_f, uinf[d].data(), sizeof(float) * uinf[d].size());
     if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
     if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());
+    if (e == cudaSuccess && h->gpcP > 0) {
+      // each a_j Phi_alpha(Z_j) as hi = fl32(v), lo = fl32(v - hi): 48 bits of it
+      std::vector<float>& f = abft[d];
+      f.assign((size_t)2 * M.nq * h->gpcP, 0.0f);
+      for (int j = 0; j < M.nq; ++j)
+        for (int a = 0; a < h->gpcP; ++a) {
+          const double v = abt[d][(size_t)j * (h->gpcP + 1) + 1 + a];
+          const float hi = (float)v;
+          f[2 * ((size_t)j * h->gpcP + a)] = hi;
+          f[2 * ((size_t)j * h->gpcP + a) + 1] = (float)(v - (double)hi);
+        }
+      e = up(M.abf, f.data(), sizeof(float) * f.size());
+    }
     if (e == cudaSuccess && M.avg)
       e = cudaMemsetAsync(h->ws + M.avg, 0, sizeof(double) * (size_t)M.nq * (size_t)M.ncell, h->stream);
     if (e == cudaSuccess && M.bout)
@@ -891,6 +907,7 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   MomentArgs A;
   A.domain = domain;
   A.ab = (const double*)(h->ws + L.dom[domain].ab);
+  A.abf = (const float2*)(h->ws + L.dom[domain].abf);
   A.nq = h->nq[domain];
   A.stride = h->gpcP + 1;
   A.P = gpc_coef ? h->gpcP : 0;
@@ -938,6 +955,7 @@ int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, doubl
   MomentArgs A;
   A.domain = domain;
   A.ab = (const double*)(h->ws + h->L.dom[domain].ab);
+  A.abf = (const float2*)(h->ws + h->L.dom[domain].abf);
   A.nq = h->nq[domain];
   A.stride = h->gpcP + 1;
   A.P = d_gpc_sums ? h->gpcP : 0;

@@ -1129,14 +1129,53 @@ __device__ __forceinline__ void finish_moments(double s1, double s2, double wsum
   sd = __dsqrt_rn(var);
 }
 
+// Compensated FP32 sum of products (the Dot2 scheme of Ogita, Rump & Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005): the running
+// sum is the unevaluated pair hi + lo.  Each term b q, with b = bh + bl a
+// double split into two floats and q a float, enters as the exact product
+// bh q = p + e (TwoProduct by FMA) plus the small bl q; TwoSum (Knuth) adds p
+// to hi exactly and the rounding errors gather in lo; a final Fast2Sum keeps
+// |lo| <= ulp(hi) / 2, so hi + lo is the float pair nearest the sum.  The
+// result carries about twice FP32's precision (relative error near
+// n 2^-48 of the sum of |terms| for n terms).
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_dot_add(DF& s, float2 b, float q) {
+  const float p = __fmul_rn(b.x, q);
+  const float e = __fmaf_rn(b.x, q, -p);
+  const float t = __fmul_rn(b.y, q);
+  const float sum = __fadd_rn(s.hi, p);
+  const float bb = __fsub_rn(sum, s.hi);
+  const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+  const float lo = __fadd_rn(s.lo, __fadd_rn(err, __fadd_rn(e, t)));
+  const float hi = __fadd_rn(sum, lo);
+  s.lo = __fsub_rn(lo, __fsub_rn(hi, sum));
+  s.hi = hi;
+}
+// The pair nearest a double (its value to 48 bits) and back.
+__device__ __forceinline__ DF df_from(double v) {
+  DF s;
+  s.hi = __double2float_rn(v);
+  s.lo = __double2float_rn(v - (double)s.hi);
+  return s;
+}
+__device__ __forceinline__ double df_value(DF s) { return (double)s.hi + (double)s.lo; }
+
 // Ensemble statistics of |u| per cell (Eq. quad_moments) and the gPC
 // projection (Eq. coef_discrete): one thread per cell runs over the nodes in
-// order and accumulates in FP64.  PM >= A.P is the compile-time size of the
-// coefficient array (so a small basis holds few registers).  raw: write the
-// sums S1, S2 (and the gPC sums); with accumulate the sums start from the
-// values in the output arrays, so node ranges reduced one after another
-// (waves) give the same bits as one reduction over all nodes.
-template <class S, bool SHIFT, int PM>
+// order.  S1 and S2 accumulate in FP64.  The gPC sums accumulate in FP64 on
+// the FP64 plain path and, on the in-place (FP32-arithmetic) paths, as
+// compensated FP32 pairs (df_dot_add), which keeps the FP64 pipe for S1 and
+// S2: |u| is a float there, so each product is exact to 48 bits.  PM >= A.P is
+// the compile-time size of the coefficient array (a small basis holds few
+// registers).  raw: write the sums S1, S2 (and the gPC sums); with accumulate
+// the sums start from the values in the output arrays, so node ranges reduced
+// one after another (waves, shards) continue one sum per cell: S1 and S2 then
+// carry the bits of one reduction over all nodes, the gPC pair sums agree
+// with it to their 48-bit rounding.
+// AVG: the per-node time averages (A.avg) instead of the current |u|.
+template <class S, bool SHIFT, int PM, bool AVG>
 __global__ void __launch_bounds__(256) moments_kernel(const __grid_constant__ StepParams P, MomentArgs A) {
   using T = typename Store<S>::C;
   const DevDomain& D = P.dom[A.domain];
@@ -1150,13 +1189,22 @@ __global__ void __launch_bounds__(256) moments_kernel(const __grid_constant__ St
     const LinkWord lw = __ldg(D.link + c);
     const bool acc = A.raw && A.accumulate;
     double s1 = acc ? A.mean[c] : 0.0, s2 = acc ? A.stdev[c] : 0.0;
+    // compensated pair sums where |u| is a float (the time averages are
+    // FP64 and take the FP64 sums)
+    constexpr bool PAIR = SHIFT && !AVG;
     double coef[PM > 0 ? PM : 1];
+    DF cf[PAIR && PM > 0 ? PM : 1];
 #pragma unroll
-    for (int a = 0; a < PM; ++a) coef[a] = (acc && a < A.P) ? A.coef[(long long)a * D.ncell + c] : 0.0;
+    for (int a = 0; a < PM; ++a) {
+      const double v = (acc && a < A.P) ? A.coef[(long long)a * D.ncell + c] : 0.0;
+      if constexpr (PAIR) cf[a] = df_from(v);
+      else coef[a] = v;
+    }
     if (!(lw & kLinkSolid)) {
       for (int j = 0; j < A.nq; ++j) {
         double q;
-        if (A.avg) {
+        float qf = 0.0f;
+        if constexpr (AVG) {
           q = A.avg[(long long)j * D.ncell + c] * A.avg_scale;
           if (!isfinite(q)) bad = true;
         } else {
@@ -1165,16 +1213,29 @@ __global__ void __launch_bounds__(256) moments_kernel(const __grid_constant__ St
           T rho, ux, uy, uz;
           macro<T, SHIFT>(g, rho, ux, uy, uz);
           if (!(rho > T(0)) || !isfinite(double(ux + uy + uz)) || !isfinite(double(rho))) bad = true;
-          q = double(speed<T>(ux, uy, uz));
+          const T sp = speed<T>(ux, uy, uz);
+          q = double(sp);
+          qf = float(sp);
         }
         const double* ab = A.ab + (long long)j * A.stride;
         const double aq = ab[0] * q;
         s1 += aq;
         s2 = fma(aq, q, s2);
+        if constexpr (PAIR) {
+          const float2* bf = A.abf + (long long)j * A.P;
 #pragma unroll
-        for (int a = 0; a < PM; ++a)
-          if (a < A.P) coef[a] = fma(ab[1 + a], q, coef[a]);
+          for (int a = 0; a < PM; ++a)
+            if (a < A.P) df_dot_add(cf[a], bf[a], qf);
+        } else {
+#pragma unroll
+          for (int a = 0; a < PM; ++a)
+            if (a < A.P) coef[a] = fma(ab[1 + a], q, coef[a]);
+        }
       }
+    }
+    if constexpr (PAIR) {
+#pragma unroll
+      for (int a = 0; a < PM; ++a) coef[a] = df_value(cf[a]);
     }
     if (A.raw) {
       A.mean[c] = s1;
@@ -1588,13 +1649,18 @@ int launch_moments(const StepParams& P, int precision, const MomentArgs& A, void
     if (A.mean) {
       const unsigned grid = (unsigned)((D.ncell + blk - 1) / blk);
       if (A.P > kMaxGpcP) return (int)cudaErrorInvalidValue;
-      if (A.P == 0) moments_kernel<S, SH, 0><<<grid, blk, 0, s>>>(P, A);
-      else if (A.P <= 3) moments_kernel<S, SH, 3><<<grid, blk, 0, s>>>(P, A);
-      else if (A.P <= 6) moments_kernel<S, SH, 6><<<grid, blk, 0, s>>>(P, A);
-      else if (A.P <= 10) moments_kernel<S, SH, 10><<<grid, blk, 0, s>>>(P, A);
-      else if (A.P <= 15) moments_kernel<S, SH, 15><<<grid, blk, 0, s>>>(P, A);
-      else if (A.P <= 21) moments_kernel<S, SH, 21><<<grid, blk, 0, s>>>(P, A);
-      else moments_kernel<S, SH, kMaxGpcP><<<grid, blk, 0, s>>>(P, A);
+      auto go = [&](auto avg) {
+        constexpr bool AV = decltype(avg)::value;
+        if (A.P == 0) moments_kernel<S, SH, 0, AV><<<grid, blk, 0, s>>>(P, A);
+        else if (A.P <= 3) moments_kernel<S, SH, 3, AV><<<grid, blk, 0, s>>>(P, A);
+        else if (A.P <= 6) moments_kernel<S, SH, 6, AV><<<grid, blk, 0, s>>>(P, A);
+        else if (A.P <= 10) moments_kernel<S, SH, 10, AV><<<grid, blk, 0, s>>>(P, A);
+        else if (A.P <= 15) moments_kernel<S, SH, 15, AV><<<grid, blk, 0, s>>>(P, A);
+        else if (A.P <= 21) moments_kernel<S, SH, 21, AV><<<grid, blk, 0, s>>>(P, A);
+        else moments_kernel<S, SH, kMaxGpcP, AV><<<grid, blk, 0, s>>>(P, A);
+      };
+      if (A.avg) go(std::true_type{});
+      else go(std::false_type{});
       int rc = (int)cudaGetLastError();
       if (rc) return rc;
     }

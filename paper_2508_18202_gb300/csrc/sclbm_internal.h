@@ -201,6 +201,7 @@ int launch_init_equilibrium(const StepParams& P, int precision, void* stream);
 struct MomentArgs {
   int domain;
   const double* ab;        // [nq][stride] : a_j then a_j * Phi_alpha(Z_j)
+  const float2* abf;       // [nq][P] : a_j * Phi_alpha(Z_j) as (hi, lo) floats, hi + lo to 48 bits
   int stride;              // row length of ab (basis size of the configuration + 1)
   int nq, P;               // P: coefficients to produce (0 = none)
   double wsum;

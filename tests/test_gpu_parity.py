@@ -659,6 +659,12 @@ def test_ensemble_moments_match_exported_fields(O, cuda):
     assert np.max(np.abs(out["std"].cpu().numpy() - std)) < 1e-9
     prof, _ = O.profiles(a, Qv, 256, 128, 64, cols)
     assert np.max(np.abs(out["prof"].cpu().numpy() - prof)) < 1e-9
+    # gPC sums: compensated FP32 pairs against the FP64 projection of the
+    # same fields, within 1e-12 of sum_j |a_j Phi_alpha(Z_j) Q_j| per cell
+    phi = O.gpc_basis(2, wl["gpc_degree"], O.legendre_s(Z, wl["lo"], wl["hi"]))
+    coef = O.gpc_project(a, Qv, phi)
+    bound = (np.abs(a[:, None] * phi)).T @ np.abs(Qv)
+    assert np.all(np.abs(out["coef"].cpu().numpy() - coef) <= 1e-12 * bound)
     ens.close()
 
 
