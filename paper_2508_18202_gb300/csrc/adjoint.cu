@@ -55,10 +55,19 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const __grid_constant_
     fast_push<float>(dst + c, lw, (int)pc, D.nx, D.nx * D.ny, ux, uy, uz, r1, g);
     return;
   }
-  const ListedRef L = listed_ref(D, listed_index(D, c));
+  const ListedRef L = listed_ref(D, A.lmap[c]);
   float ux = 0.f, uy = 0.f, uz = 0.f;
   if (L.word(kWordPushMove)) inflow_velocity<float>(N, z, w1, ux, uy, uz);
   listed_push<float>(L, dst, ux, uy, uz, r1, g);
+}
+
+// Listed cell c -> its index in the domain's listed-cell array (entries of
+// other cells are never read).
+__global__ void adj_listed_map_kernel(const __grid_constant__ StepParams P, int domain, int32_t* lmap) {
+  const DevDomain& D = P.dom[domain];
+  for (long long li = blockIdx.x * (long long)blockDim.x + threadIdx.x; li < D.nb;
+       li += (long long)gridDim.x * blockDim.x)
+    lmap[__ldg(D.bcell + li)] = (int32_t)li;
 }
 
 // Loss at the probes and the adjoint seed lambda^T = dJ/df^T
@@ -182,11 +191,18 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
       const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
       const long long pc = D.pitch;
       float ls[kQ];
-      if (lw == 0) {
-        // every delivery streams: lambda*_k(x) = lambda^{n+1}_k(x + c_k)
+      if (!(lw & kLinkSlow)) {
+        // each f*_k goes to the one slot the forward push writes (stream,
+        // bounce-back, moving wall, specular lid): lambda*_k is lambda^{n+1}
+        // there
         const int sy = D.nx, sz = D.nx * D.ny;
 #pragma unroll
-        for (int k = 0; k < kQ; ++k) ls[k] = lam_next[(long long)k * pc + c + (CX(k) + CY(k) * sy + CZ(k) * sz)];
+        for (int k = 0; k < kQ; ++k) {
+          const int kind = link_kind(lw, OPP(k));
+          const int stream = k * (int)pc + (CX(k) + CY(k) * sy + CZ(k) * sz);
+          const int spec = REFL(k, 2) * (int)pc + (CX(k) + CY(k) * sy);
+          ls[k] = lam_next[c + (kind == kStream ? stream : (kind == kSpecZ ? spec : OPP(k) * (int)pc))];
+        }
       } else {
         float lg[kQ];
 #pragma unroll 1
@@ -228,7 +244,8 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
         const float4 du0 = A.du[z], du1 = A.du[D.nz + z];
 #pragma unroll 1
         for (int i = 1; i < kQ; ++i) {
-          if (link_kind(lw, i) == kStream || !velocity_link(D, i, x, y, z)) continue;
+          if (link_kind(lw, i) == kStream) continue;
+          if (!(lw & kLinkSlow) ? link_kind(lw, i) != kMoving : !velocity_link(D, i, x, y, z)) continue;
           const double li = (double)lam_next[(long long)i * pc + c];
           const double pre = 6.0 * c_lat.wd[i] * (double)r1;
           const double d0 = c_lat.cx[i] * (double)du0.x + c_lat.cy[i] * (double)du0.y + c_lat.cz[i] * (double)du0.z;
@@ -275,6 +292,12 @@ int launch_adj_step(const StepParams& P, const AdjArgs& A, const float* f, const
                     float r1, void* stream) {
   const DevDomain& D = P.dom[A.domain];
   adj_step_kernel<<<blocks_for(D.ncell), 256, 0, (cudaStream_t)stream>>>(P, A, f, lam_next, lam, r1);
+  return (int)cudaGetLastError();
+}
+
+int launch_adj_listed_map(const StepParams& P, int domain, int32_t* lmap, void* stream) {
+  const long long nb = P.dom[domain].nb;
+  adj_listed_map_kernel<<<(unsigned)(nb > 0 ? (nb + 255) / 256 : 1), 256, 0, (cudaStream_t)stream>>>(P, domain, lmap);
   return (int)cudaGetLastError();
 }
 

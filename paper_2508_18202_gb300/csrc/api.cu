@@ -326,7 +326,6 @@ struct sc_lbm_s {
   int never_arrive = 0;
   long long spin_limit = kSpinLimit;
   int tma_ok = 0;  // every domain's rows meet the 16-byte alignment of bulk copies
-  int pair_ok = 0; // every domain has an even nx (pair forms)
   Header* hdr() const { return reinterpret_cast<Header*>(ws + L.hdr); }
 };
 
@@ -355,13 +354,9 @@ void apply_tiling(sc_lbm_t h) {
   P.bz = h->tune.slab_z;
   P.order = h->tune.tile_order;
   long long begin = 0, bbegin = 0, rbegin = 0;
-  // pair forms: two x-adjacent cells per thread (launch and graph modes)
-  P.pair = ((h->tune.variant == 4 || h->tune.variant == 5) && h->pair_ok &&
-            h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
-  const int tile_x = P.bx * (P.pair ? 2 : 1);
   for (int d = 0; d < P.n_domains; ++d) {
     DevDomain& D = P.dom[d];
-    D.tiles_x = (D.nx + tile_x - 1) / tile_x;
+    D.tiles_x = (D.nx + P.bx - 1) / P.bx;
     D.tiles_y = (D.ny + P.by - 1) / P.by;
     D.tiles_z = (D.nz + P.bz - 1) / P.bz;
     D.tiles_per_node = D.tiles_x * D.tiles_y * D.tiles_z;
@@ -377,8 +372,8 @@ void apply_tiling(sc_lbm_t h) {
   P.total_bitems = bbegin;
   P.total_runs = rbegin;
   P.tma = (h->tune.variant == 1 && h->tma_ok && h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
-  P.even85 = (h->tune.variant == 2 || h->tune.variant == 5) ? 1 : 0;
-  P.odd85 = (h->tune.variant == 2 || h->tune.variant == 3 || h->tune.variant == 5) ? 1 : 0;
+  P.even85 = h->tune.variant == 2 ? 1 : 0;
+  P.odd85 = (h->tune.variant == 2 || h->tune.variant == 3) ? 1 : 0;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -394,7 +389,7 @@ int check_tuning(const sc_lbm_tuning& t) {
   if (t.tile_order < 0 || t.tile_order > 1) return SC_ERR_ARG;
   if (t.exec_mode < SC_EXEC_LAUNCH || t.exec_mode > SC_EXEC_PERSISTENT) return SC_ERR_ARG;
   if (t.graph_steps < 1 || t.graph_steps > 100000) return SC_ERR_ARG;
-  if (t.variant < 0 || t.variant > 5) return SC_ERR_ARG;
+  if (t.variant < 0 || t.variant > 3) return SC_ERR_ARG;
   return SC_OK;
 }
 
@@ -808,9 +803,6 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
   h->tma_ok = c.precision != SC_P_FP64_PLAIN;
   for (int d = 0; d < c.n_domains; ++d)
     if (c.domains[d].nx % (int)(16 / storage_bytes(c.precision)) != 0) h->tma_ok = 0;
-  h->pair_ok = c.precision != SC_P_FP64_PLAIN;
-  for (int d = 0; d < c.n_domains; ++d)
-    if (c.domains[d].nx % 2 != 0) h->pair_ok = 0;
   // default launch shape
   h->tune.variant = 0;
   h->tune.block_x = 64;
@@ -1194,7 +1186,7 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
     }
     return SC_OK;
   };
-  // stage 1: block shape and z-slab, one-cell and pair forms, patch-major order
+  // stage 1: block shape and z-slab, patch-major order
   std::vector<sc_lbm_tuning> cand;
   const int bxs[] = {32, 64, 128, 256};
   const int bys[] = {1, 2, 4, 8};
@@ -1205,7 +1197,6 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
         if (bx * by > 256 || bx * by < 64) continue;
         if (bx > 32 && bx / 2 >= maxnx) continue;
         cand.push_back({bx, by, bz, 1, SC_EXEC_LAUNCH, 50, 0});
-        if (h->pair_ok && bx < maxnx) cand.push_back({bx, by, bz, 1, SC_EXEC_LAUNCH, 50, 4});
       }
   }
   int rc = try_all(cand);
@@ -1215,9 +1206,8 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   cand.clear();
   for (size_t k = 0; k < timed.size() && k < 3; ++k) {
     const sc_lbm_tuning t = timed[k].t;
-    const bool pair = t.variant == 4;
     for (int order = 0; order < 2; ++order)
-      for (int v : pair ? std::vector<int>{4, 5} : std::vector<int>{0, 2, 3}) {
+      for (int v : {0, 2, 3}) {
         if (order == t.tile_order && v == t.variant) continue;
         cand.push_back({t.block_x, t.block_y, t.slab_z, order, SC_EXEC_LAUNCH, 50, v});
       }
@@ -1230,7 +1220,7 @@ int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   for (int mode : {SC_EXEC_GRAPH, SC_EXEC_PERSISTENT}) {
     sc_lbm_tuning t = best_t;
     t.exec_mode = mode;
-    if (mode == SC_EXEC_PERSISTENT && t.variant != 0 && t.variant != 2 && t.variant != 3) {
+    if (mode == SC_EXEC_PERSISTENT && t.variant == 1) {
       t.variant = 0;  // the persistent form loads one cell per thread
       t.block_x = 64;
       t.block_y = 2;
@@ -1486,7 +1476,7 @@ int sc_lbm_inflow_next_change(int ramp_steps, int n_targets, const double* speed
 // ------------------------------------------------------------ adjoint
 namespace {
 struct AdjLayout {
-  size_t accum, probes, target, uprobe, uin, du, states, state_bytes, total;
+  size_t accum, probes, target, uprobe, uin, du, lmap, states, state_bytes, total;
   int K, L;
 };
 
@@ -1511,6 +1501,7 @@ int adj_plan(sc_lbm_t h, int domain, int n_steps, int n_snapshots, int n_probes,
   A.uprobe = take(3 * sizeof(double) * (size_t)n_probes);
   A.uin = take(16 * (size_t)D.nz);
   A.du = take(32 * (size_t)D.nz);
+  A.lmap = take(sizeof(int32_t) * (size_t)D.ncell);
   A.state_bytes = align_up(sizeof(float) * kQ * (size_t)D.pitch);
   A.states = off;
   A.K = K;
@@ -1586,6 +1577,7 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
   A.u_probe = (double*)(ws + L.uprobe);
   A.n_probes = n_probes;
   A.accum = (double*)(ws + L.accum);
+  A.lmap = (const int32_t*)(ws + L.lmap);
   auto state = [&](int k) { return (float*)(ws + L.states + L.state_bytes * (size_t)k); };
   float* snap0 = state(0);           // K checkpoints
   float* seg0 = state(L.K);          // L segment states
@@ -1602,6 +1594,7 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
   const size_t sf = L.state_bytes / sizeof(float);
   auto issue = [&]() -> int {
     int r;
+    if ((r = ck(launch_adj_listed_map(P, domain, (int32_t*)(ws + L.lmap), h->stream), "adjoint map"))) return r;
     if ((r = ck(launch_fill_zero(fa, nstate, h->stream), "adjoint fill"))) return r;
     if ((r = ck(launch_fill_zero(fb, nstate, h->stream), "adjoint fill"))) return r;
     float* cur = fa;

@@ -111,7 +111,7 @@ __device__ __forceinline__ TileHead decode_tile_head(const StepParams& P, unsign
   const unsigned tz = ct / txy, rem = ct - tz * txy;
   const unsigned ty = rem / tx;
   H.d = d;
-  H.x0 = (int)(rem - ty * tx) * P.bx * (P.pair ? 2 : 1);
+  H.x0 = (int)(rem - ty * tx) * P.bx;
   H.y0 = (int)ty * P.by;
   H.z0 = (int)tz * P.bz;
   return H;
@@ -127,7 +127,7 @@ __device__ __forceinline__ TileRef block_tile(const StepParams& P, unsigned t) {
   const DevDomain& D = P.dom[H.d];
   R.d = H.d;
   R.node = H.node;
-  R.x = H.x0 + threadIdx.x * (P.pair ? 2 : 1);
+  R.x = H.x0 + threadIdx.x;
   R.y = H.y0 + threadIdx.y;
   R.z0 = H.z0;
   R.z1 = min(H.z0 + P.bz, D.nz);
@@ -239,241 +239,6 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef
   }
 }
 
-// ------------------------------------------------------------ pair forms
-// Two x-adjacent cells (x even, x + 1) per thread: every population row is
-// read and written with one aligned two-element access (float2, or the
-// 32-bit bf16x2 / half2 word), so a warp covers 64 consecutive cells of a
-// row per access.  Needs nx even (pairs never straddle rows; the row pitch is
-// a multiple of 256 cells).  The arithmetic per cell is that of the one-cell
-// forms.
-template <class S>
-struct Pair;
-template <>
-struct Pair<float> {
-  static __device__ __forceinline__ void ld(const float* p, float& a, float& b) {
-    const float2 v = *reinterpret_cast<const float2*>(p);
-    a = v.x;
-    b = v.y;
-  }
-  static __device__ __forceinline__ void st(float* p, float a, float b) {
-    *reinterpret_cast<float2*>(p) = make_float2(a, b);
-  }
-};
-template <>
-struct Pair<__nv_bfloat16> {
-  static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float& a, float& b) {
-    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
-    a = __low2float(v);
-    b = __high2float(v);
-  }
-  static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
-  }
-};
-template <>
-struct Pair<__half> {
-  static __device__ __forceinline__ void ld(const __half* p, float& a, float& b) {
-    const __half2 v = *reinterpret_cast<const __half2*>(p);
-    a = __low2float(v);
-    b = __high2float(v);
-  }
-  static __device__ __forceinline__ void st(__half* p, float a, float b) {
-    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
-  }
-};
-
-// Store of the two elements of a pair position, each only where its flag is
-// set (a whole word when both are).
-template <class S>
-__device__ __forceinline__ void store2_masked(S* p, float a, bool va, float b, bool vb) {
-  if (va && vb) {
-    Pair<S>::st(p, a, b);
-  } else {
-    if (va) Store<S>::st(p, a);
-    if (vb) Store<S>::st(p + 1, b);
-  }
-}
-
-// Even level over the z-run of a pair tile: both cells bulk -> pair loads and
-// stores; one of them skipped (solid, or listed for the leading blocks) ->
-// the other cell alone, element-wise.  The next pair's class bytes are
-// loaded one cell ahead.
-template <class S, bool CG>
-__device__ __forceinline__ void even_pair_run(const StepParams& P, S* base, const uint8_t* cp, int pc, int plane,
-                                              int n) {
-  using T = typename Store<S>::C;
-  uint16_t next = __ldg(reinterpret_cast<const uint16_t*>(cp));
-  for (int k = 0; k < n; ++k, base += plane, cp += plane) {
-    const uint16_t cls = next;
-    if (k + 1 < n) next = __ldg(reinterpret_cast<const uint16_t*>(cp + plane));
-    const bool skip_a = cls & kClsSkip, skip_b = (cls >> 8) & kClsSkip;
-    if (skip_a && skip_b) continue;
-    if (!skip_a && !skip_b) {
-      T ga[kQ], gb[kQ];
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) Pair<S>::ld(base + i * pc, ga[i], gb[i]);
-      collide_p<T, true>(P, ga);
-      collide_p<T, true>(P, gb);
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) Pair<S>::st(base + OPP(i) * pc, ga[i], gb[i]);
-    } else {
-      S* b1 = skip_a ? base + 1 : base;
-      T g[kQ];
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) g[i] = LD<S, CG>(b1 + i * pc);
-      collide_p<T, true>(P, g);
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) Store<S>::st(b1 + OPP(i) * pc, g[i]);
-    }
-  }
-}
-
-template <class S, bool CG>
-__device__ __forceinline__ void even_pair_tile(const StepParams& P, const TileRef& R) {
-  if (!R.valid) return;
-  const DevDomain& D = P.dom[R.d];
-  const int plane = D.nx * D.ny;
-  const int idx0 = R.x + D.nx * (R.y + D.ny * R.z0);
-  even_pair_run<S, CG>(P, reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0, D.cls + idx0,
-                       (int)D.pitch, plane, R.z1 - R.z0);
-}
-
-// Bits j of the directions whose delivery f*_j streams to x + c_j (the kind
-// of link opp(j) at the receiving side is stream), all of them for an
-// all-streaming cell, none for a cell this kernel does not update.
-__device__ __forceinline__ uint32_t stream_push_mask(LinkWord lw, bool fast) {
-  if (!fast) return 0u;
-  if (lw == 0) return (1u << kQ) - 1u;
-  uint32_t m = 0u;
-#pragma unroll
-  for (int j = 0; j < kQ; ++j)
-    if (link_kind(lw, OPP(j)) == kStream) m |= 1u << j;
-  return m;
-}
-
-// Odd level over the z-run of a pair tile.  Every lane of the warp takes part
-// (lanes beyond nx stand in at an in-bounds position and update nothing),
-// because the x-shifted rows are assembled with warp shuffles: the pull of a
-// link with c_x = +1 for the pair (x, x + 1) reads the row word at x and
-// takes the element at x - 1 from the left lane (lane 0 loads it itself);
-// c_x = -1 reads x + 1 from the own word and x + 2 from the right lane
-// (lane 31 loads it).  Deliveries mirror this: the word at x of a row with
-// c_x = +1 holds the left lane's second cell and the own first cell, and the
-// edge lanes store their outermost element alone.  Stores are masked per
-// element, so solid and listed cells (and links that do not stream) keep
-// their slots.  A warp whose updated cells all stream (interior) skips the
-// link-kind code.
-template <class S, bool CG, bool ROT>
-__device__ __forceinline__ void odd_pair_tile(const StepParams& P, const TileRef& R) {
-  using T = typename Store<S>::C;
-  const DevDomain& D = P.dom[R.d];
-  const int lane = threadIdx.x & 31;
-  const bool valid = R.valid;
-  const int sy = D.nx, sz = D.nx * D.ny;
-  const int x0 = valid ? R.x : 0, y0 = valid ? R.y : 0;
-  const int idx0 = x0 + D.nx * (y0 + D.ny * R.z0);
-  const int pc = (int)D.pitch;
-  S* base = reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0;
-  const LinkWord* lp = D.link + idx0;
-  const float4* uinf = D.uin_f + (long long)R.node * D.nz;
-  const double* uind = D.uin_d + (long long)R.node * D.nz * 3;
-  const unsigned full = 0xffffffffu;
-  LinkWord na = valid ? __ldg(lp) : kLinkSolid, nb = valid ? __ldg(lp + 1) : kLinkSolid;
-  for (int z = R.z0; z < R.z1; ++z, base += sz, lp += sz) {
-    const LinkWord la = na, lb = nb;
-    if (z + 1 < R.z1 && valid) {
-      na = __ldg(lp + sz);
-      nb = __ldg(lp + sz + 1);
-    }
-    const bool fa = !(la & kLinkSlow), fb = !(lb & kLinkSlow);
-    if (!__any_sync(full, fa || fb)) continue;
-    const bool interior = __all_sync(full, (!fa || la == 0) && (!fb || lb == 0));
-    T ga[kQ], gb[kQ];
-    T ux = T(0), uy = T(0), uz = T(0);
-    Node<S> N;
-    N.g = nullptr;
-    N.bout = nullptr;
-    N.uinf = uinf;
-    N.uind = uind;
-    if (!interior) wall_velocity<S, ROT>(N, la | lb, z, wind_pull<T>(P), ux, uy, uz);
-    int pcv = pc, syv = sy, szv = sz;
-    asm volatile("" : "+r"(pcv), "+r"(syv), "+r"(szv));
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const S* row = base + (OPP(i) * pcv - (CY(i) * syv + CZ(i) * szv));
-      T wx, wy;
-      Pair<S>::ld(row, wx, wy);
-      T sa, sb;
-      if (CX(i) == 0) {
-        sa = wx;
-        sb = wy;
-      } else if (CX(i) == 1) {
-        T up = __shfl_up_sync(full, wy, 1);
-        if (lane == 0) up = LD<S, CG>(row - 1);
-        sa = up;
-        sb = wx;
-      } else {
-        T dn = __shfl_down_sync(full, wx, 1);
-        if (lane == 31) dn = LD<S, CG>(row + 2);
-        sa = wy;
-        sb = dn;
-      }
-      if (!interior) {
-        const int ka = link_kind(la, i), kb = link_kind(lb, i);
-        const int spec = OPP(REFL(i, 2)) * pc - (CX(i) + CY(i) * sy);
-        if (fa && ka != kStream) {
-          T v = LD<S, CG>(base + (ka == kSpecZ ? spec : i * pc));
-          if (ka == kMoving) v += wall_term<T>(i, ux, uy, uz, wind_pull<T>(P).scale);
-          sa = v;
-        }
-        if (fb && kb != kStream) {
-          T v = LD<S, CG>(base + 1 + (kb == kSpecZ ? spec : i * pc));
-          if (kb == kMoving) v += wall_term<T>(i, ux, uy, uz, wind_pull<T>(P).scale);
-          sb = v;
-        }
-      }
-      ga[i] = sa;
-      gb[i] = sb;
-    }
-    if (fa) collide_p<T, true>(P, ga);
-    if (fb) collide_p<T, true>(P, gb);
-    if constexpr (ROT) {
-      if (!interior) wall_velocity<S>(N, la | lb, z, wind_push<T>(P), ux, uy, uz);
-    }
-    const uint32_t ma = interior ? (fa ? (1u << kQ) - 1u : 0u) : stream_push_mask(la, fa);
-    const uint32_t mb = interior ? (fb ? (1u << kQ) - 1u : 0u) : stream_push_mask(lb, fb);
-    uint32_t mprev = __shfl_up_sync(full, mb, 1), mnext = __shfl_down_sync(full, ma, 1);
-    if (lane == 0) mprev = 0u;    // the left warp stores its own edge element
-    if (lane == 31) mnext = 0u;
-    asm volatile("" : "+r"(pcv), "+r"(syv), "+r"(szv));
-#pragma unroll
-    for (int j = 0; j < kQ; ++j) {
-      T va = ga[j], vb = gb[j];
-      if (!interior) {
-        const int ka = link_kind(la, OPP(j)), kb = link_kind(lb, OPP(j));
-        if (ka == kMoving) va += wall_term<T>(OPP(j), ux, uy, uz, wind_push<T>(P).scale);
-        if (kb == kMoving) vb += wall_term<T>(OPP(j), ux, uy, uz, wind_push<T>(P).scale);
-        const int spec = REFL(j, 2) * pc + (CX(j) + CY(j) * sy);
-        if (fa && ka != kStream) Store<S>::st(base + (ka == kSpecZ ? spec : OPP(j) * pc), va);
-        if (fb && kb != kStream) Store<S>::st(base + 1 + (kb == kSpecZ ? spec : OPP(j) * pc), vb);
-      }
-      const bool sa = (ma >> j) & 1u, sb = (mb >> j) & 1u;
-      S* drow = base + (j * pcv + (CY(j) * syv + CZ(j) * szv));
-      if (CX(j) == 0) {
-        store2_masked<S>(drow, va, sa, vb, sb);
-      } else if (CX(j) == 1) {
-        const T pv = __shfl_up_sync(full, vb, 1);
-        store2_masked<S>(drow, pv, (mprev >> j) & 1u, va, sa);
-        if (lane == 31 && sb) Store<S>::st(drow + 2, vb);
-      } else {
-        const T nv = __shfl_down_sync(full, va, 1);
-        store2_masked<S>(drow, vb, sb, nv, (mnext >> j) & 1u);
-        if (lane == 0 && sa) Store<S>::st(drow - 1, va);
-      }
-    }
-  }
-}
-
 // Listed (node, cell) items: item -> domain, node and cell index.
 __device__ __forceinline__ int decode_bitem(const StepParams& P, long long item, int* node, long long* idx) {
   int d = 0;
@@ -581,29 +346,6 @@ __global__ void __launch_bounds__(256, MINB) aa_odd_bulk_kernel(const __grid_con
     return;
   }
   odd_bulk_tile<S, false, MINB != 4>(P, block_tile(P, k));
-}
-
-// The same two levels in the pair form (tiles of 2 * block_x cells in x).
-template <class S, int MINB>
-__global__ void __launch_bounds__(256, MINB) aa_even_pair_kernel(const __grid_constant__ StepParams P) {
-  unsigned k;
-  if (block_role(P, &k)) {
-    const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-    even_boundary_item<S, false>(P, item);
-    return;
-  }
-  even_pair_tile<S, false>(P, block_tile(P, k));
-}
-
-template <class S, int MINB>
-__global__ void __launch_bounds__(256, MINB) aa_odd_pair_kernel(const __grid_constant__ StepParams P) {
-  unsigned k;
-  if (block_role(P, &k)) {
-    const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-    odd_boundary_item<S, false, MINB != 4>(P, item);
-    return;
-  }
-  odd_pair_tile<S, false, MINB != 4>(P, block_tile(P, k));
 }
 
 // Odd time level, listed boundary cells alone (after the TMA odd kernel of the
@@ -1537,17 +1279,6 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
       // listed items ride in blocks spread over the per-thread launches
       const long long threads = (long long)P.bx * P.by;
       const unsigned lgrid = (unsigned)(P.total_tiles + (P.total_bitems + threads - 1) / threads);
-      if (P.pair) {
-        if (parity == 0) {
-          if (P.even85) aa_even_pair_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
-          else aa_even_pair_kernel<S, 4><<<lgrid, block, 0, s>>>(P);
-        } else if (P.odd85 || turns_inflow(P)) {
-          aa_odd_pair_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
-        } else {
-          aa_odd_pair_kernel<S, 4><<<lgrid, block, 0, s>>>(P);
-        }
-        return (int)cudaGetLastError();
-      }
       if (parity == 0) {
         if (P.tma) aa_even_tma_kernel<S><<<tgrid, kTmaThreads, even_tma_smem<S>(), s>>>(P);
         else if (P.even85) aa_even_kernel<S, 3><<<lgrid, block, 0, s>>>(P);

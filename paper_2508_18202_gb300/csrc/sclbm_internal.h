@@ -138,7 +138,6 @@ struct StepParams {
   long long total_runs;        // runs of kRun cells of all domains and nodes
   int tma;                     // bulk kernels staged through shared memory by TMA
   int odd85, even85;           // per-thread odd / even kernels sized for 3 blocks (85 registers)
-  int pair;                    // two x-adjacent cells per thread (tiles of 2 * bx cells in x)
   int bx, by, bz, order;
   // persistent mode
   unsigned int* bar_count;
@@ -245,6 +244,7 @@ struct AdjArgs {
   double* u_probe;        // [n_probes][3]
   int n_probes;
   double* accum;          // [0] loss, [1] dJ/du_ref, [2] dJ/dalpha
+  const int32_t* lmap;    // [ncell]: listed cell -> index in the listed-cell array
 };
 int launch_adj_forward(const StepParams& P, const AdjArgs& A, const float* src, float* dst, float r1,
                        void* stream);  // r1: ramp r(n + 1) of the step's pushes
@@ -252,5 +252,6 @@ int launch_adj_loss(const StepParams& P, const AdjArgs& A, const float* f, float
 int launch_adj_step(const StepParams& P, const AdjArgs& A, const float* f, const float* lam_next, float* lam,
                     float r1, void* stream);
 int launch_fill_zero(float* p, long long n, void* stream);
+int launch_adj_listed_map(const StepParams& P, int domain, int32_t* lmap, void* stream);
 
 }  // namespace sclbm

@@ -66,21 +66,19 @@ def cuda():
 @pytest.mark.parametrize("collision", [W.BGK, W.RR], ids=["bgk", "rr"])
 @pytest.mark.parametrize("bcname", list(BC_SETS))
 @pytest.mark.parametrize("precision,tol,nx,variant", [(W.FP32_SHIFT, 2e-6, 37, 0), (W.FP32_SHIFT, 2e-6, 40, 1),
-                                                      (W.FP32_SHIFT, 2e-6, 38, 4), (W.FP32_SHIFT, 2e-6, 38, 5),
-                                                      (W.FP64_PLAIN, 1e-13, 37, 0)])
+                                                      (W.FP32_SHIFT, 2e-6, 38, 3), (W.FP64_PLAIN, 1e-13, 37, 0)])
 def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx, variant, collision):
     """Populations after 1..6 and 31 steps (both AA parities) at every fluid
     cell and node, max abs difference, for both collision forms.  Variant 1
     (nx = 40) runs the TMA-staged kernels (partial last run of 256 cells),
-    variants 4 and 5 (nx = 38) the two-cells-per-thread forms with both
-    register budgets (a partial last warp of pairs in x), variant 0 (nx = 37)
-    the one-cell ones."""
+    variant 3 (nx = 38) the per-thread odd kernel with the larger register
+    budget, variant 0 (nx = 37) the default per-thread ones."""
     wl = ragged(BC_SETS[bcname], precision=precision, nx=nx, collision=collision)
     ens = S.Ensemble(S.make_config(wl))
     if variant == 1:
         S.sc_lbm_set_tuning(ens.h, 128, 2, 1, variant=1)
-    elif variant in (4, 5):
-        S.sc_lbm_set_tuning(ens.h, 32, 2, 3, variant=variant)
+    elif variant == 3:
+        S.sc_lbm_set_tuning(ens.h, 32, 2, 3, variant=3)
     p, flags = oracle_domain(O, wl)
     Z, a = oracle_nodes(O, wl)
     fl = fluid_mask(flags)
@@ -99,12 +97,13 @@ def test_ragged_domain_all_boundaries(O, cuda, bcname, precision, tol, nx, varia
     ens.close()
 
 
-@pytest.mark.parametrize("variant", [1, 4])
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("precision", [W.BF16_STORE, W.FP16_STORE])
 def test_reduced_storage_tracks_oracle(O, cuda, precision, variant):
     """BF16 / FP16 storage of the shifted populations: error report against
     FP64 after 40 steps (bounded, not bit-level); nx = 40 runs the TMA-staged
-    kernels (variant 1) or the pair forms (variant 4) with 2-byte elements."""
+    kernels (variant 1) or the per-thread ones (variant 0) with 2-byte
+    elements."""
     wl = ragged(BC_SETS["urban"], precision=precision, nx=40)
     ens = S.Ensemble(S.make_config(wl))
     S.sc_lbm_set_tuning(ens.h, 128 if variant == 1 else 32, 2, 1 if variant == 1 else 4, variant=variant)
@@ -528,7 +527,7 @@ def test_launch_shapes_and_modes_are_bitwise_identical(cuda, shape):
     TMA-staged) gives the same bits."""
     wl = ragged(BC_SETS["urban"], nx=40)
     want = {}
-    variants = (0, 1, 2, 3, 4, 5)
+    variants = (0, 1, 2, 3)
     for variant in variants:
         ref = S.Ensemble(S.make_config(wl))
         S.sc_lbm_set_tuning(ref.h, 64, 1, 1, variant=variant)

@@ -1,0 +1,100 @@
+"""Precision contract of the storage modes (FP32 shifted, FP16 and BF16
+storage of the shifted populations with FP32 arithmetic): the ensemble
+statistics of a batched three-domain ensemble of uneven sizes and node
+counts (the shape of the batched workload, small enough for the oracle)
+against the FP64 oracle's own runs and reduction, per field.
+
+Fields: mean and std of |u| (Eq. quad_moments), the 95% profile band
+(mean, std, mean -/+ 1.96 std at two columns) and the gPC coefficients
+(Eq. coef_discrete), after 200 steps of BGK + Smagorinsky with a 20-step
+start-up ramp.
+
+Tolerances, in units of the storage format's unit roundoff u (FP16 2^-11,
+BF16 2^-9; the populations are rounded to the format at every store):
+  mean, band, gPC coefficient 0 (= mean):  relative L2 <= 2u,
+  std:                                     relative L2 <= 8u,
+  every gPC coefficient:                   ||c_k - c_k^oracle|| <= 2u ||c_0^oracle||,
+  element-wise:                            max |err| <= 16u max |field|.
+The std is the spread between nodes; rounding noise that differs from node
+to node enters it at full size while it averages out of the mean, hence the
+wider bound.  FP32 storage is held to 1e-5 throughout (its measured error
+is about 1e-6).  The mean of a one-node domain's std is zero; there the
+bound is absolute (1e-6 of the mean's scale).
+"""
+import numpy as np
+import pytest
+
+from helpers import oracle_domain, oracle_nodes, rel_l2
+from paper_2508_18202_gb300 import sclbm as S
+from paper_2508_18202_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DOMS = [dict(nx=40, ny=18, nz=12, seed=1, n_buildings=2, fp=(4, 6), h=(3, 7), bc=W.URBAN_BC, quad_level=2),
+        dict(nx=32, ny=23, nz=14, seed=2, n_buildings=3, fp=(3, 5), h=(3, 9), bc=W.URBAN_BC, quad_level=3),
+        dict(nx=52, ny=12, nz=10, seed=3, n_buildings=1, fp=(3, 4), h=(2, 4), bc=W.URBAN_BC, quad_level=1)]
+WL = dict(W.URBAN_BATCHED, domains=DOMS, ramp_steps=20, tau0=0.56, c_smag=0.14)
+STEPS = 200
+UNIT = {W.FP32_SHIFT: None, W.FP16_STORE: 2.0 ** -11, W.BF16_STORE: 2.0 ** -9}
+
+
+def tolerances(prec):
+    u = UNIT[prec]
+    if u is None:
+        return dict(mean=1e-5, band=1e-5, std=1e-5, coef=1e-5, elem=1e-5)
+    return dict(mean=2 * u, band=2 * u, std=8 * u, coef=2 * u, elem=16 * u)
+
+
+@pytest.fixture(scope="module")
+def oracle_fields(O):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    out = []
+    cfg = S.make_config(WL)
+    for d in range(len(DOMS)):
+        p, flags = oracle_domain(O, WL, d)
+        Z, a = oracle_nodes(O, WL, d)
+        cols = S.sc_lbm_probe_columns(cfg, d, 2)
+        Qv = O.ensemble(p, flags, Z, WL["inputs"], WL["u_ref"], WL["alpha"], 0.0, p.nz, STEPS)
+        mean, std, _ = O.moments_two_pass(a, Qv)
+        prof, _ = O.profiles(a, Qv, p.nx, p.ny, p.nz, cols)
+        coef = O.gpc_project(a, Qv, O.gpc_basis(2, WL["gpc_degree"], O.legendre_s(Z, WL["lo"], WL["hi"])))
+        out.append(dict(mean=mean, std=std, prof=prof, coef=coef, fl=flags == 0, cols=cols, nq=len(a)))
+    return out
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["per_thread", "tma"])
+@pytest.mark.parametrize("prec", [W.FP32_SHIFT, W.FP16_STORE, W.BF16_STORE], ids=["fp32", "fp16", "bf16"])
+def test_storage_precision_contract(oracle_fields, prec, variant):
+    tol = tolerances(prec)
+    ens = S.Ensemble(S.make_config(dict(WL, precision=prec)))
+    S.sc_lbm_set_tuning(ens.h, 128 if variant == 1 else 32, 2, 1 if variant == 1 else 4, variant=variant)
+    ens.step(STEPS)
+    report = []
+    for d, ref in enumerate(oracle_fields):
+        out = ens.moments(d, probes=ref["cols"], gpc=True)
+        g = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+        fl = ref["fl"]
+        e_mean = rel_l2(g["mean"][fl], ref["mean"][fl])
+        e_band = rel_l2(g["prof"], ref["prof"])
+        scale = np.max(np.abs(ref["mean"][fl]))
+        if ref["nq"] > 1:
+            e_std = rel_l2(g["std"][fl], ref["std"][fl])
+            assert e_std <= tol["std"], (d, "std", e_std)
+        else:
+            e_std = float(np.max(np.abs(g["std"][fl])) / scale)
+            assert e_std <= 1e-6, (d, "std of one node", e_std)
+        c0 = np.linalg.norm(ref["coef"][0][fl])
+        e_coef = max(float(np.linalg.norm(g["coef"][k][fl] - ref["coef"][k][fl]) / c0)
+                     for k in range(ref["coef"].shape[0]))
+        e_elem = max(float(np.max(np.abs(g[f][fl] - ref[f][fl]))) for f in ("mean", "std")) / scale
+        report.append((d, e_mean, e_std, e_band, e_coef, e_elem))
+        assert e_mean <= tol["mean"], (d, "mean", e_mean)
+        assert e_band <= tol["band"], (d, "band", e_band)
+        assert rel_l2(g["coef"][0][fl], ref["coef"][0][fl]) <= tol["mean"], (d, "coef0")
+        assert e_coef <= tol["coef"], (d, "coef", e_coef)
+        assert e_elem <= tol["elem"], (d, "elementwise", e_elem)
+    print("precision %d variant %d: " % (prec, variant) +
+          "; ".join("d%d mean %.2e std %.2e band %.2e coef %.2e elem %.2e" % r for r in report))
+    ens.close()
