@@ -92,10 +92,16 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the stream-collide kernels' code (comments and whitespace
+    removed, so that a recorded traffic figure follows the code only)."""
+    import re
     h = hashlib.sha256()
     for f in ("lbm_kernels.cu", "lbm_device.cuh", "sclbm_internal.h"):
-        with open(os.path.join(ROOT, "paper_2508_18202_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2508_18202_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

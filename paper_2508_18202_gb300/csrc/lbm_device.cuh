@@ -124,6 +124,27 @@ __device__ __forceinline__ typename Store<S>::C LD(const S* p) {
   else return Store<S>::ld(p);
 }
 
+// Loads of the geometry (link words, class bytes) that every node of a launch
+// reads again: an L2 evict-last policy keeps them resident while the
+// populations stream through (measured: +1.5% on both AA levels of the
+// 13-node LES ensemble, where the 16.8 MB of link words otherwise left L2
+// between nodes).
+__device__ __forceinline__ uint64_t keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(keep_policy()));
+  return v;
+}
+__device__ __forceinline__ uint8_t ld_keep(const uint8_t* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(keep_policy()));
+  return (uint8_t)v;
+}
+
 // ------------------------------------------------------------ collision
 // Correctly rounded reciprocal (the same value as 1 / x in IEEE arithmetic).
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }

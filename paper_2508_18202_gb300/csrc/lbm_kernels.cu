@@ -18,11 +18,16 @@
 // x + c_i.  Every slot is then read and written by exactly one thread per
 // step, so one array suffices (152 B per fluid cell update in FP32).
 //
-// Links whose source is solid or lies across a bounce-back face use the own
-// slot instead of the neighbour's (an address select in the bulk kernels).
-// Cells with any other boundary link (inflow, outflow, free slip, periodic)
-// are listed on the host and updated by a compact general kernel that
-// applies the per-link rules of the pull formulation:
+// Every fluid cell carries a 64-bit link word whose 2-bit kind per direction
+// selects the rule of link i in the bulk kernels: stream from the neighbour,
+// bounce-back into the own slot (solid source, wall face), the moving-wall
+// rule of an inflow face or the circular mantle (own slot plus the wall
+// term), or specular reflection at a free-slip z face (the in-plane
+// neighbour's slot).  Cells with any other link (outflow, free slip on an x
+// or y face, periodic wraps) are listed on the host, their rules compiled
+// into per-cell offset records, and updated by the listed blocks of the same
+// launch.  Together the kinds and the records realise the per-link rules of
+// the pull formulation:
 //   source inside and solid            -> bounce-back
 //   one face crossed: BOUNCE_BACK      -> bounce-back
 //                     VELOCITY         -> bounce-back + 6 w_i (c_i . u_in(z)) r(t)
@@ -146,10 +151,10 @@ template <class S, bool CG>
 __device__ __forceinline__ void even_run(const StepParams& P, S* base, const uint8_t* cp, int pc, int plane,
                                          int n) {
   using T = typename Store<S>::C;
-  uint8_t next = __ldg(cp);
+  uint8_t next = ld_keep(cp);
   for (int k = 0; k < n; ++k, base += plane, cp += plane) {
     const uint8_t cls = next;
-    if (k + 1 < n) next = __ldg(cp + plane);
+    if (k + 1 < n) next = ld_keep(cp + plane);
     if (cls & kClsSkip) continue;
     T g[kQ];
 #pragma unroll
@@ -202,10 +207,10 @@ __device__ __forceinline__ void odd_bulk_tile(const StepParams& P, const TileRef
   const LinkWord* lp = D.link + idx0;
   const float4* uinf = D.uin_f + (long long)R.node * D.nz;
   const double* uind = D.uin_d + (long long)R.node * D.nz * 3;
-  LinkWord next = __ldg(lp);
+  LinkWord next = ld_keep(lp);
   for (int z = R.z0; z < R.z1; ++z, base += sz, lp += sz) {
     const LinkWord lw = next;
-    if (z + 1 < R.z1) next = __ldg(lp + sz);
+    if (z + 1 < R.z1) next = ld_keep(lp + sz);
     const bool interior = __all_sync(__activemask(), lw == 0 || (lw & kLinkSlow));
     if (lw & kLinkSlow) continue;   // solid, outlet or general-boundary cell
     T g[kQ];

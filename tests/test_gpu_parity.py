@@ -637,10 +637,13 @@ def test_other_full_size_workloads_single_step(O, cuda, name):
     ens.close()
 
 
-def test_ensemble_moments_match_exported_fields(O, cuda):
+@pytest.mark.parametrize("gpc_degree", [2, 3, 5], ids=["P6", "P10", "P21"])
+def test_ensemble_moments_match_exported_fields(O, cuda, gpc_degree):
     """Property at full size: the on-device FP64 reduction equals the oracle's
-    two-pass moments of the per-node |u| fields the GPU exports."""
-    wl = W.URBAN_LES
+    two-pass moments of the per-node |u| fields the GPU exports, and the gPC
+    sums (compensated FP32 pairs, bases of 6, 10 and 21 terms) equal the FP64
+    projection of the same fields."""
+    wl = dict(W.URBAN_LES, gpc_degree=gpc_degree)
     ens = S.Ensemble(S.make_config(wl))
     ens.step(60)
     cfg = S.make_config(wl)
