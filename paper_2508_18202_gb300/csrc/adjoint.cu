@@ -102,81 +102,6 @@ __global__ void adj_loss_kernel(const __grid_constant__ StepParams P, AdjArgs A,
   }
 }
 
-// lambda*_k(x): the sum of lambda^{n+1} over every slot that the forward
-// step delivers f*_k(x) to (the transpose of the push rules).
-__device__ float gather_deliveries(const DevDomain& D, const float* lam, int k, int x, int y, int z,
-                                   long long c, LinkWord lw) {
-  const long long pc = D.pitch;
-  const int cx = c_lat.cx[k], cy = c_lat.cy[k], cz = c_lat.cz[k], ok = c_lat.opp[k];
-  float s = 0.0f;
-  if (link_kind(lw, ok) == kStream) {
-    s = lam[(long long)k * pc + c + link_offset(D, k)];
-  } else {
-    const Cross q = classify(D, x + cx, y + cy, z + cz);
-    const float own = lam[(long long)ok * pc + c];
-    if (q.n == 0) {
-      const long long t = cidx(D, q.p[0], q.p[1], q.p[2]);
-      s = D.flags[t] == 0 ? lam[(long long)k * pc + t] : own;
-    } else if (q.n == 1) {
-      const int kind = D.bc[q.f[0]];
-      if (kind == SC_BC_BOUNCE_BACK || kind == SC_BC_VELOCITY) {
-        s = own;
-      } else if (kind == SC_BC_FREE_SLIP) {
-        const int a = q.f[0] >> 1;
-        int t[3] = {x + cx, y + cy, z + cz};
-        t[a] = a == 0 ? x : (a == 1 ? y : z);
-        const Cross ct = classify(D, t[0], t[1], t[2]);
-        const long long tp = cidx(D, ct.p[0], ct.p[1], ct.p[2]);
-        s = D.flags[tp] == 0 ? lam[(long long)c_lat.refl[k][a] * pc + tp] : own;
-      }
-      // OUTFLOW: the population leaves the domain
-    } else {
-      const int k0 = D.bc[q.f[0]], k1 = D.bc[q.f[1]];
-      if (k0 == SC_BC_BOUNCE_BACK || k1 == SC_BC_BOUNCE_BACK || k0 == SC_BC_VELOCITY ||
-          k1 == SC_BC_VELOCITY || (k0 == SC_BC_FREE_SLIP && k1 == SC_BC_FREE_SLIP))
-        s = own;
-    }
-  }
-  if ((lw & kLinkOutlet) && cx == -1) {
-    // (1) transverse neighbour on the outlet plane
-    {
-      const Cross q = classify(D, x, y + cy, z + cz);
-      if (q.n == 0) {
-        const long long t = cidx(D, q.p[0], q.p[1], q.p[2]);
-        if (D.flags[t] == 0) s += lam[(long long)k * pc + t];
-      }
-    }
-    // (2) own link k whose transverse source is solid
-    {
-      const Cross q = classify(D, x, y - cy, z - cz);
-      if (q.n == 0 && D.flags[cidx(D, q.p[0], q.p[1], q.p[2])] != 0) s += lam[(long long)k * pc + c];
-    }
-    // (3) outflow + free-slip edge
-    for (int a = 1; a < 3; ++a) {
-      const int ca = a == 1 ? cy : cz;
-      if (ca == 0) continue;
-      const int face = 2 * a + (ca > 0 ? 1 : 0);
-      const int pos = (a == 1 ? y : z) + ca;
-      const int lim = a == 1 ? D.ny : D.nz;
-      if (D.bc[face] == SC_BC_FREE_SLIP && (pos < 0 || pos >= lim))
-        s += lam[(long long)c_lat.refl[k][a] * pc + c];
-    }
-  }
-  return s;
-}
-
-// True when the pull rule of link i at the cell carries the moving-wall term.
-__device__ __forceinline__ bool velocity_link(const DevDomain& D, int i, int x, int y, int z) {
-  const Cross q = classify(D, x - c_lat.cx[i], y - c_lat.cy[i], z - c_lat.cz[i]);
-  if (q.n == 1) return D.bc[q.f[0]] == SC_BC_VELOCITY;
-  if (q.n == 2) {
-    const int k0 = D.bc[q.f[0]], k1 = D.bc[q.f[1]];
-    return k0 != SC_BC_BOUNCE_BACK && k1 != SC_BC_BOUNCE_BACK &&
-           (k0 == SC_BC_VELOCITY || k1 == SC_BC_VELOCITY);
-  }
-  return false;
-}
-
 // One reverse step: lambda^n from lambda^{n+1} and the forward state f^n;
 // accumulates the inflow-parameter gradient of level n + 1 (ramp r1).
 __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ StepParams P, AdjArgs A,
@@ -188,13 +113,19 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
   if (c < D.ncell) {
     const LinkWord lw = __ldg(D.link + c);
     if (!(lw & kLinkSolid)) {
-      const int x = (int)(c % D.nx), y = (int)((c / D.nx) % D.ny), z = (int)(c / ((long long)D.nx * D.ny));
+      const int z = (int)(c / ((long long)D.nx * D.ny));
       const long long pc = D.pitch;
       float ls[kQ];
+      // lambda*_k(x) = the sum of lambda^{n+1} over the slots the forward
+      // step delivers f*_k(x) to (the transpose of the push rules), and the
+      // moving-wall terms' share of dJ/dtheta: sum over the slots that receive
+      // a term 6 w_i (c_i . u_in(z)) r(n + 1) of lambda^{n+1} there times the
+      // term's derivative (summed per cell in FP32, over cells in FP64)
+      float g0 = 0.0f, g1 = 0.0f;
+      const float4 du0 = A.du[z], du1 = A.du[D.nz + z];
       if (!(lw & kLinkSlow)) {
         // each f*_k goes to the one slot the forward push writes (stream,
-        // bounce-back, moving wall, specular lid): lambda*_k is lambda^{n+1}
-        // there
+        // bounce-back, moving wall, specular lid)
         const int sy = D.nx, sz = D.nx * D.ny;
 #pragma unroll
         for (int k = 0; k < kQ; ++k) {
@@ -202,14 +133,49 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
           const int stream = k * (int)pc + (CX(k) + CY(k) * sy + CZ(k) * sz);
           const int spec = REFL(k, 2) * (int)pc + (CX(k) + CY(k) * sy);
           ls[k] = lam_next[c + (kind == kStream ? stream : (kind == kSpecZ ? spec : OPP(k) * (int)pc))];
+          if (kind == kMoving) {  // lands in the own slot i = opp(k) with the term of link i
+            const int i = OPP(k);
+            const float pre = 6.0f * W<float>(i) * r1 * ls[k];
+            g0 += pre * (CX(i) * du0.x + CY(i) * du0.y + CZ(i) * du0.z);
+            g1 += pre * (CX(i) * du1.x + CY(i) * du1.y + CZ(i) * du1.z);
+          }
         }
       } else {
-        float lg[kQ];
-#pragma unroll 1
-        for (int k = 0; k < kQ; ++k) lg[k] = gather_deliveries(D, lam_next, k, x, y, z, c, lw);
+        // listed cell: the deliveries of its compiled record; an outlet copy
+        // stored to a slot the cell's own primary delivery also wrote
+        // replaces it (listed_push writes the copies last)
+        const ListedRef L = listed_ref(D, A.lmap[c]);
+        constexpr int kCopies = kOutletPops * kOutletCopies;
+        int32_t ex[kCopies];
 #pragma unroll
-        for (int k = 0; k < kQ; ++k) ls[k] = lg[k];
+        for (int e = 0; e < kCopies; ++e) ex[e] = L.word(kWordExtra + e);
+        const uint32_t mm = (uint32_t)L.word(kWordPushMove);
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) {
+          const int d = L.word(kWordDst + k);
+          bool replaced = false;
+#pragma unroll
+          for (int e = 0; e < kCopies; ++e) replaced |= ex[e] == d;
+          const float v = (d >= 0 && !replaced) ? lam_next[d] : 0.0f;
+          ls[k] = v;
+          if ((mm >> k) & 1u) {
+            const int i = OPP(k);
+            const float pre = 6.0f * W<float>(i) * r1 * v;
+            g0 += pre * (CX(i) * du0.x + CY(i) * du0.y + CZ(i) * du0.z);
+            g1 += pre * (CX(i) * du1.x + CY(i) * du1.y + CZ(i) * du1.z);
+          }
+        }
+        constexpr int kPops[kOutletPops] = {2, 8, 10, 12, 14};
+#pragma unroll
+        for (int e = 0; e < kOutletPops; ++e)
+#pragma unroll
+          for (int m = 0; m < kOutletCopies; ++m) {
+            const int d = ex[e * kOutletCopies + m];
+            if (d >= 0) ls[kPops[e]] += lam_next[d];
+          }
       }
+      gr0 = (double)g0;
+      gr1 = (double)g1;
       // forward state of this level
       float rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
@@ -239,23 +205,10 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const __grid_constant__ S
 #pragma unroll
       for (int m = 0; m < kQ; ++m)
         lam[(long long)m * pc + c] = (1.0f - om) * ls[m] + om * (al + CX(m) * bx + CY(m) * by + CZ(m) * bz);
-      // inflow links of this cell at level n + 1
-      if (lw & kLinkVel) {
-        const float4 du0 = A.du[z], du1 = A.du[D.nz + z];
-#pragma unroll 1
-        for (int i = 1; i < kQ; ++i) {
-          if (link_kind(lw, i) == kStream) continue;
-          if (!(lw & kLinkSlow) ? link_kind(lw, i) != kMoving : !velocity_link(D, i, x, y, z)) continue;
-          const double li = (double)lam_next[(long long)i * pc + c];
-          const double pre = 6.0 * c_lat.wd[i] * (double)r1;
-          const double d0 = c_lat.cx[i] * (double)du0.x + c_lat.cy[i] * (double)du0.y + c_lat.cz[i] * (double)du0.z;
-          const double d1 = c_lat.cx[i] * (double)du1.x + c_lat.cy[i] * (double)du1.y + c_lat.cz[i] * (double)du1.z;
-          gr0 += li * pre * d0;
-          gr1 += li * pre * d1;
-        }
-      }
     }
   }
+  // warps without a moving-wall contribution skip the FP64 reduction
+  if (!__any_sync(0xffffffffu, gr0 != 0.0 || gr1 != 0.0)) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     gr0 += __shfl_xor_sync(0xffffffffu, gr0, o);

@@ -318,37 +318,6 @@ __device__ __forceinline__ void collide_p(const StepParams& P, T g[kQ]) {
 }
 
 // ------------------------------------------------------------ boundary helpers
-struct Cross {
-  int n;        // faces crossed (0, 1, 2)
-  int f[2];     // face ids
-  int p[3];     // position with periodic axes wrapped
-};
-
-__device__ __forceinline__ Cross classify(const DevDomain& D, int px, int py, int pz) {
-  Cross c;
-  c.n = 0;
-  c.f[0] = c.f[1] = -1;
-  int p[3] = {px, py, pz};
-  const int n[3] = {D.nx, D.ny, D.nz};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (D.bc[2 * a] == SC_BC_PERIODIC) {
-      if (p[a] < 0) p[a] += n[a];
-      else if (p[a] >= n[a]) p[a] -= n[a];
-    } else if (p[a] < 0) {
-      c.f[c.n < 2 ? c.n : 1] = 2 * a;
-      ++c.n;
-    } else if (p[a] >= n[a]) {
-      c.f[c.n < 2 ? c.n : 1] = 2 * a + 1;
-      ++c.n;
-    }
-  }
-  c.p[0] = p[0];
-  c.p[1] = p[1];
-  c.p[2] = p[2];
-  return c;
-}
-
 __device__ __forceinline__ long long cidx(const DevDomain& D, int x, int y, int z) {
   return (long long)x + (long long)D.nx * ((long long)y + (long long)D.ny * z);
 }
@@ -362,9 +331,6 @@ struct Node {
   const double* uind;  // [nz][3]
 };
 
-__device__ __forceinline__ long long link_offset(const DevDomain& D, int i) {
-  return (long long)c_lat.cx[i] + (long long)c_lat.cy[i] * D.nx + (long long)c_lat.cz[i] * D.nx * D.ny;
-}
 
 // ------------------------------------------------------------ fast link rules
 // Links of kind kStream, kBounce, kMoving and kSpecZ resolve to an address
