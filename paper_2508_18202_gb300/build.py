@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
     if failed:
         raise RuntimeError("libsclbm build failed:\n" + "\n".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    link = [nvcc, GENCODE, "-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-lpthread"]
+    link = [nvcc, GENCODE, "-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-lpthread", "-ldl"]
     subprocess.run(link, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sclbm_internal.h"
 
 using namespace sclbm;
@@ -331,6 +333,13 @@ struct sc_lbm_s {
 
 namespace {
 
+// NVTX range for the duration of a scope (named in profiler timelines; a
+// no-op when no tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 int fail(sc_lbm_t h, int rc, const std::string& why) {
   if (h) h->err = why;
   return rc;
@@ -498,6 +507,7 @@ int run_graph(sc_lbm_t h, long long t, int n, const Wind<double>& w) {
     h->graph_wind = wf;
   }
   for (int r = 0; r < reps; ++r) {
+    Range rg("graph replay");
     CK(cudaGraphLaunch(h->graph, h->stream));
     h->launches += G + (h->P.tma ? G / 2 : 0);  // TMA odd levels launch two kernels
   }
@@ -677,6 +687,7 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
                 const uint8_t* const* flags_host, sc_lbm_t* out) {
   if (!out) return SC_ERR_ARG;
   *out = nullptr;
+  Range range("sc_lbm_init");
   Layout L;
   std::string why;
   int rc = plan(cfg, L, why);
@@ -881,12 +892,14 @@ int sc_lbm_reset(sc_lbm_t h) {
 
 int sc_lbm_step(sc_lbm_t h, int n_steps) {
   if (!h || n_steps < 0) return SC_ERR_ARG;
+  Range r("sc_lbm_step");
   return do_steps(h, n_steps);
 }
 
 int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const int32_t* probe_xy,
                    int n_p, double* prof, float* prof_nodes, double* gpc_coef, int out_host) {
   if (!h || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
+  Range r("sc_lbm_moments");
   if (n_p < 0 || n_p > kMaxProbes || (n_p > 0 && (!probe_xy || !prof))) return SC_ERR_ARG;
   if ((mean == nullptr) != (stdev == nullptr)) return SC_ERR_ARG;
   if (gpc_coef && h->gpcP == 0) return fail(h, SC_ERR_ARG, "gpc_degree < 0 in the configuration");
@@ -943,6 +956,7 @@ int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, doubl
                        int accumulate) {
   if (!h || !d_s1 || !d_s2 || domain < 0 || domain >= h->P.n_domains) return SC_ERR_ARG;
   if (accumulate != 0 && accumulate != 1) return fail(h, SC_ERR_ARG, "accumulate must be 0 or 1");
+  Range r("sc_lbm_moment_sums");
   if (d_gpc_sums && h->gpcP == 0) return fail(h, SC_ERR_ARG, "gpc_degree < 0 in the configuration");
   MomentArgs A;
   A.domain = domain;
@@ -1132,6 +1146,7 @@ int sc_lbm_get_tuning(sc_lbm_t h, sc_lbm_tuning* t) {
 
 int sc_lbm_autotune(sc_lbm_t h, const char* cache_path) {
   if (!h) return SC_ERR_ARG;
+  Range range("sc_lbm_autotune");
   if (h->cfg.precision == SC_P_FP64_PLAIN) return SC_OK;  // the plain path is not tuned
   int dev = 0;
   cudaDeviceProp prop;
@@ -1525,6 +1540,7 @@ int sc_lbm_adjoint(sc_lbm_t h, int domain, int node, const int32_t* probes, int 
                    const double* u_target, int n_steps, int n_snapshots, void* d_ws, size_t bytes,
                    double* loss_out, double* grad_out, double* u_probe_out) {
   if (!h || !probes || !u_target || !loss_out || !grad_out) return SC_ERR_ARG;
+  Range range("sc_lbm_adjoint");
   if (h->cfg.c_smag != 0.0 || h->cfg.collision != SC_COLL_BGK)
     return fail(h, SC_ERR_UNSUPPORTED, "the adjoint covers BGK (c_smag = 0, SC_COLL_BGK)");
   if (h->cfg.profile != SC_PROFILE_POWER)

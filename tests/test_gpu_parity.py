@@ -316,6 +316,7 @@ def test_paper_case_full_size(O, cuda):
             uo = O.macros(p, flags, fo[j])[1]
             ug = ens.velocity(0, j).cpu().numpy()
             err = rel_l2(ug[:, fl], uo[:, fl])
+            print("paper case level %d node %d: relative L2 of u %.2e" % (level, j, err))
             assert err <= 1e-3, (level, j, err)
         done = level
     ens.close()
@@ -340,9 +341,10 @@ def test_les_full_size_ensemble_fields_100_steps(O, cuda):
     mean, std, _ = O.moments_two_pass(a, Qv)
     prof, _ = O.profiles(a, Qv, p.nx, p.ny, p.nz, cols)
     fl = fluid_mask(flags)
-    assert rel_l2(out["mean"].cpu().numpy()[fl], mean[fl]) <= 1e-3
-    assert rel_l2(out["std"].cpu().numpy()[fl], std[fl]) <= 1e-3
-    assert rel_l2(out["prof"].cpu().numpy(), prof) <= 1e-3
+    errs = (rel_l2(out["mean"].cpu().numpy()[fl], mean[fl]), rel_l2(out["std"].cpu().numpy()[fl], std[fl]),
+            rel_l2(out["prof"].cpu().numpy(), prof))
+    print("LES 13-node fields after 100 steps: mean %.2e std %.2e band %.2e" % errs)
+    assert errs[0] <= 1e-3 and errs[1] <= 1e-3 and errs[2] <= 1e-3, errs
     coef = O.gpc_project(a, Qv, O.gpc_basis(2, wl["gpc_degree"], O.legendre_s(Z, wl["lo"], wl["hi"])))
     cg = out["coef"].cpu().numpy()
     assert rel_l2(cg[0][fl], coef[0][fl]) <= 1e-3
