@@ -251,8 +251,11 @@ int sc_lbm_step(sc_lbm_t h, int n_steps);
  *   (Eq. quad_moments); d_mean, d_std: [nz*ny*nx] doubles, solid cells 0;
  *   gpc: d_gpc_coef [P][ncell] doubles, coef_alpha = sum_j a_j Q_j
  *   Phi_alpha(Z^(j)) for the orthonormal Legendre basis (Eq. coef_discrete,
- *   gamma = 1), P = C(gpc_degree + n_inputs, n_inputs), graded order; NULL
- *   skips it;
+ *   gamma = 1), P = C(gpc_degree + n_inputs, n_inputs) <= 28, graded order;
+ *   NULL skips it.  Q_j = |u| is formed in the path's arithmetic (FP32 for
+ *   the in-place precisions, FP64 for SC_P_FP64_PLAIN); the gPC sums run in
+ *   FP64 on the FP64 path and as compensated FP32 pairs (about 48 bits,
+ *   products exact) on the others;
  *   profiles at the n_p columns probe_xy (host int32 [n_p][2]):
  *   d_prof [n_p][nz][4] doubles = (mean, std, mean - 1.96 std,
  *   mean + 1.96 std) (95% band, Sec. 4) and optional d_prof_nodes
