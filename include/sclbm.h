@@ -488,21 +488,22 @@ int sc_lbm_destroy(sc_lbm_t h);
  * synchronise the device.  It calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *
- * Its scratch (the weight table on the device and a counter of non-finite
- * inputs) is a fixed file-scope device array of about 8 KB, held by every
- * GPU that loads the library until the process exits.  The first call on
- * each device (with that device current) looks up the array's address and
- * the device's SM count; make that first call before any stream capture
- * begins.  Every call shares the array and it keeps the last call's contents
- * (the counter is cleared at the start of each call): calls whose device
- * work overlaps (unordered streams, several host threads) race on it.
+ * The weights travel by value as a kernel parameter (8 KB).  The one piece
+ * of scratch, a counter of non-finite inputs, is a fixed file-scope device
+ * variable (8 bytes) held by every GPU that loads the library until the
+ * process exits.  The first call on each device (with that device current)
+ * looks up its address and the device's SM count and must not be made
+ * inside a stream capture; every later call issues only a memset, one
+ * kernel and, with d_nonfinite, a device-to-device copy on `stream`, so it
+ * may be captured into a CUDA graph (the graph keeps the weights it was
+ * captured with).  Every call shares the counter and clears it at its
+ * start: calls whose device work overlaps (unordered streams, several host
+ * threads) race on it.
  *
  * d_field: device double [n_nodes][n_cells], Q_j(c) of node j at cell c;
  * weights: host double [n_nodes], the quadrature weights a_j (their sum must
- * be positive), copied to the scratch by cudaMemcpyAsync on `stream`: from
- * pageable memory the runtime stages them before the call returns (the
- * array may be reused at once); from pinned memory the copy reads the array
- * when the stream reaches it (keep it unchanged until then);
+ * be positive and finite), read during the call only (the array may be
+ * reused as soon as the call returns);
  * d_mean, d_stdev: device double [n_cells] outputs,
  *   mean = sum_j a_j Q_j / sum_j a_j,
  *   std  = sqrt(max(sum_j a_j Q_j^2 / sum_j a_j - mean^2, 0));

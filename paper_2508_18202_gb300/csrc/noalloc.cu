@@ -9,25 +9,21 @@
 // the device's memory up front, where cudaMalloc fails or forces a cache
 // flush), and code on a latency-critical stream, where cudaMalloc / cudaFree
 // would synchronise the whole device.  Such a caller cannot size and hand
-// over a workspace either, so the two pieces of scratch the reduction needs
-// (the quadrature weight table on the device and a counter of non-finite
-// inputs) live in a fixed file-scope device array instead.
+// over a workspace either.
 //
-// The scratch array is a static __device__ symbol: every GPU on which the
-// library's module is loaded holds it (kNoallocScratchBytes, about 8 KB)
-// until the process exits.  Its device address, and the device's SM count
-// that sizes the grid, are looked up once per device, by the first call made
-// with that device current; that first call should be made before any stream
-// capture begins.  All calls share the array and it keeps the last call's
-// contents: the counter is cleared at the start of each call, the weight
-// table is overwritten.  Calls whose device work overlaps (different streams
-// without ordering, or several host threads) race on it.
-//
-// The weights travel from the caller's host array into the scratch with a
-// cudaMemcpyAsync on the caller's stream.  From pageable memory the runtime
-// stages them before the call returns, so the array may be reused at once;
-// from pinned memory the copy reads the array when the stream reaches it, so
-// the array must stay unchanged until then.
+// The quadrature weights travel by value, as an 8 KB __grid_constant__ kernel
+// parameter (the launch copies them, so the caller's host array may be reused
+// as soon as the call returns, and a captured launch keeps its own copy).  The
+// one piece of device scratch left, the counter of non-finite inputs, lives in
+// a fixed file-scope device array: a static __device__ symbol that every GPU
+// on which the library's module is loaded holds until the process exits.  Its
+// device address, and the device's SM count that sizes the grid, are looked
+// up once per device by the first call made with that device current; that
+// first call must not be inside a stream capture.  Later calls issue only a
+// memset, the kernel and (with d_nonfinite) a device-to-device copy, all of
+// which a stream capture records.  All calls share the counter (it is cleared
+// at the start of each call): calls whose device work overlaps (different
+// streams without ordering, several host threads) race on it.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -42,14 +38,16 @@
 namespace {
 
 constexpr int kNoallocMaxNodes = SC_NOALLOC_MAX_NODES;
-constexpr size_t kWeightBytes = sizeof(double) * kNoallocMaxNodes;
-constexpr size_t kCounterOffset = kWeightBytes;               // 256-byte aligned
-constexpr size_t kNoallocScratchBytes = kWeightBytes + 256;  // weights + counter
 constexpr int kMaxDevices = 64;
 
-// [0, kWeightBytes): the weights a_j (FP64); at kCounterOffset: the count of
-// non-finite field values (unsigned long long, cleared per call).
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+// The count of non-finite field values (cleared per call).
+static __device__ unsigned long long g_noalloc_nonfinite;
+
+// The weights a_j by value: 8 KB, inside the 32 KB kernel-parameter limit.
+struct QuadWeights {
+  double a[kNoallocMaxNodes];
+};
+static_assert(sizeof(QuadWeights) + 64 <= 32764, "kernel parameter space");
 
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
@@ -64,8 +62,7 @@ void put_err(char* err, size_t err_len, const char* fmt, ...) {
   va_end(ap);
 }
 
-// Device address of the scratch array and the SM count of the current
-// device (looked up once per device, with that device current).
+// Device address of the counter and the SM count of the current device (looked up once per device, with that device current).
 int setup_for_current_device(void** out, int* sms, char* err, size_t err_len) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -80,9 +77,9 @@ int setup_for_current_device(void** out, int* sms, char* err, size_t err_len) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_nonfinite);
     if (e != cudaSuccess || !p) {
-      put_err(err, err_len, "cudaGetSymbolAddress of the no-alloc scratch failed on device %d: %s", dev,
+      put_err(err, err_len, "cudaGetSymbolAddress of the no-alloc counter failed on device %d: %s", dev,
               cudaGetErrorString(e));
       return SC_ERR_CUDA;
     }
@@ -104,9 +101,10 @@ int setup_for_current_device(void** out, int* sms, char* err, size_t err_len) {
 // Per cell c: s1 = sum_j a_j Q_j(c), s2 = sum_j a_j Q_j(c)^2 (FP64, nodes in
 // order), mean = s1 / sum_j a_j, std = sqrt(max(s2 / sum_j a_j - mean^2, 0))
 // -- the same arithmetic as the handle path's moment reduction.  Non-finite
-// Q_j(c) are counted in the scratch counter.
+// Q_j(c) are counted in the counter.  Every lane of a warp reads the same
+// weight at the same time: a broadcast from the parameter bank.
 __global__ void __launch_bounds__(256) quad_moments_noalloc_kernel(
-    const double* __restrict__ field, long long n_cells, int n_nodes, const double* __restrict__ w,
+    const double* __restrict__ field, long long n_cells, int n_nodes, const __grid_constant__ QuadWeights w,
     double wsum, double* __restrict__ mean, double* __restrict__ stdev, unsigned long long* nonfinite) {
   unsigned bad = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -115,7 +113,7 @@ __global__ void __launch_bounds__(256) quad_moments_noalloc_kernel(
     for (int j = 0; j < n_nodes; ++j) {
       const double q = field[(long long)j * n_cells + c];
       if (!isfinite(q)) ++bad;
-      const double aq = w[j] * q;
+      const double aq = w.a[j] * q;
       s1 += aq;
       s2 += aq * q;
     }
@@ -141,7 +139,7 @@ extern "C" int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, l
     return SC_ERR_ARG;
   }
   if (n_nodes > kNoallocMaxNodes) {
-    put_err(err, err_len, "n_nodes = %d exceeds the no-alloc scratch maximum of %d nodes", n_nodes,
+    put_err(err, err_len, "n_nodes = %d exceeds the no-alloc maximum of %d nodes", n_nodes,
             kNoallocMaxNodes);
     return SC_ERR_SCRATCH;
   }
@@ -164,16 +162,16 @@ extern "C" int sc_lbm_quad_moments_noalloc(const double* d_field, int n_nodes, l
   int rc = setup_for_current_device(&base, &sms, err, err_len);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  double* d_w = (double*)base;
-  unsigned long long* d_count = (unsigned long long*)((unsigned char*)base + kCounterOffset);
+  unsigned long long* d_count = (unsigned long long*)base;
+  QuadWeights w;
+  memcpy(w.a, weights, sizeof(double) * (size_t)n_nodes);
+  memset(w.a + n_nodes, 0, sizeof(double) * (size_t)(kNoallocMaxNodes - n_nodes));
   cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_w, weights, sizeof(double) * (size_t)n_nodes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_cells > 0) {
     // grid-stride loop: at most 8 resident blocks of 256 threads per SM
     long long blocks = (n_cells + 255) / 256;
     if (blocks > 8LL * sms) blocks = 8LL * sms;
-    quad_moments_noalloc_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_field, n_cells, n_nodes, d_w, wsum,
+    quad_moments_noalloc_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_field, n_cells, n_nodes, w, wsum,
                                                                  d_mean, d_stdev, d_count);
     e = cudaGetLastError();
   }

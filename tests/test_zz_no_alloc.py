@@ -5,6 +5,8 @@ against the oracle's two-pass moments of the same per-node field, within the
 tolerances of the moment tests (mean 1e-12, std 1e-9 absolute).  The first
 call carries one non-finite value, which the counter reports and which only
 its own cell sees; the second call, on clean data, finds the counter cleared.
+A call captured into a CUDA graph is replayed on new field values after the
+host weight array was overwritten: the graph keeps the weights it captured.
 
 Named so that pytest collects it last; it passes alone in a fresh process and
 after the other tests."""
@@ -24,7 +26,7 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
     with pytest.raises(S.ScError) as ei:
         S.sc_lbm_quad_moments_noalloc(np.zeros((n, 4)), np.ones(n), None, None)
     assert ei.value.code == S.SC_ERR_SCRATCH
-    assert str(ei.value).endswith(": n_nodes = %d exceeds the no-alloc scratch maximum of %d nodes"
+    assert str(ei.value).endswith(": n_nodes = %d exceeds the no-alloc maximum of %d nodes"
                                   % (n, S.SC_NOALLOC_MAX_NODES))
     with pytest.raises(S.ScError) as ei:
         S.sc_lbm_quad_moments_noalloc(np.zeros((2, 4)), [1.0, -1.0], None, None)
@@ -88,3 +90,37 @@ def test_noalloc_matches_handle_moments_on_two_calls(O):
         assert np.max(np.abs(sg - s_o[keep])) < 1e-9
         del ref
     ens.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_call_replays_from_a_cuda_graph(O):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(11)
+    nq, nc = 9, 3 * 2048 + 37                     # several blocks and a ragged tail
+    a = rng.uniform(0.1, 1.0, nq)
+    a_captured = a.copy()
+    Q = torch.from_numpy(rng.normal(1.0, 0.3, (nq, nc))).cuda()
+    mean = torch.empty(nc, dtype=torch.float64, device="cuda")
+    std = torch.empty_like(mean)
+    nonfinite = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # the first call on the device looks up the counter: outside the capture
+    S.sc_lbm_quad_moments_noalloc(Q, a, mean, std, nonfinite, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sc_lbm_quad_moments_noalloc(Q, a, mean, std, nonfinite, torch.cuda.current_stream().cuda_stream)
+    a[:] = 1.0                                    # the graph must not read the host array again
+    for rep in range(2):
+        Qh = rng.normal(2.0 + rep, 0.5, (nq, nc))
+        keep = np.ones(nc, bool)
+        if rep == 1:
+            Qh[4, 777] = np.inf
+            keep[777] = False
+        Q.copy_(torch.from_numpy(Qh))
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(nonfinite.item()) == rep
+        m_o, s_o, _ = O.moments_two_pass(a_captured, Qh)
+        assert np.max(np.abs(mean.cpu().numpy()[keep] - m_o[keep])) < 1e-12
+        assert np.max(np.abs(std.cpu().numpy()[keep] - s_o[keep])) < 1e-9
