@@ -15,7 +15,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsclbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CUDA_UNITS = ["lbm_kernels.cu", "lbm_kernels_rr.cu", "adjoint.cu", "api.cu", "noalloc.cu", "quantiles.cu"]
+CUDA_UNITS = ["lbm_kernels.cu", "lbm_kernels_rr.cu", "observables.cu", "adjoint.cu", "api.cu", "noalloc.cu",
+              "quantiles.cu"]
 HOST_UNITS = ["host_numerics.cpp"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -41,7 +41,7 @@ struct DomLayout {
   size_t guard = 0;
   long long nb_max = 0;
   size_t flags = 0, link = 0, cls = 0, bcell = 0, ltab = 0, uin_f = 0, uin_d = 0, g = 0, g2 = 0, bout = 0, ab = 0;
-  size_t abf = 0;  // [nq][P] float pairs (hi, lo) of a_j Phi_alpha(Z_j): the compensated gPC sums
+  size_t abf = 0;  // [nq][gpc_pair_pad(P) / 2] float4 (hi_a, hi_a+1, lo_a, lo_a+1) of a_j Phi(Z_j)
   size_t avg = 0;  // time-averaged |u| accumulators [nq][ncell] (FP64), when configured
 };
 struct Layout {
@@ -198,7 +198,7 @@ int plan(const sc_lbm_config* c, Layout& L, std::string& why) {
     if (c->precision == SC_P_FP64_PLAIN) M.g2 = take(sb * kQ * (size_t)M.pitch * M.nq);
     else M.bout = take(sizeof(float) * 5 * (size_t)D.nz * D.ny * M.nq);
     M.ab = take(sizeof(double) * (size_t)M.nq * (P + 1));
-    M.abf = take(2 * sizeof(float) * (size_t)M.nq * (P > 0 ? P : 1));
+    M.abf = take(2 * sizeof(float) * (size_t)M.nq * (size_t)(P > 0 ? gpc_pair_pad(P) : 2));
     if (c->time_average) M.avg = take(sizeof(double) * (size_t)M.nq * (size_t)M.ncell);
     max_cell = std::max(max_cell, M.ncell);
     max_nz = std::max(max_nz, D.nz);
@@ -849,15 +849,19 @@ int sc_lbm_init(const sc_lbm_config* cfg, void* d_ws, size_t bytes, void* cuda_s
     if (e == cudaSuccess) e = up(M.uin_d, uind[d].data(), sizeof(double) * uind[d].size());
     if (e == cudaSuccess) e = up(M.ab, abt[d].data(), sizeof(double) * abt[d].size());
     if (e == cudaSuccess && h->gpcP > 0) {
-      // each a_j Phi_alpha(Z_j) as hi = fl32(v), lo = fl32(v - hi): 48 bits of it
+      // each a_j Phi_alpha(Z_j) as hi = fl32(v), lo = fl32(v - hi): 48 bits of
+      // it; terms a, a + 1 share a float4 (hi_a, hi_a+1, lo_a, lo_a+1), rows
+      // padded with zero terms to gpc_pair_pad(P)
+      const int Pp = gpc_pair_pad(h->gpcP);
       std::vector<float>& f = abft[d];
-      f.assign((size_t)2 * M.nq * h->gpcP, 0.0f);
+      f.assign((size_t)2 * M.nq * Pp, 0.0f);
       for (int j = 0; j < M.nq; ++j)
         for (int a = 0; a < h->gpcP; ++a) {
           const double v = abt[d][(size_t)j * (h->gpcP + 1) + 1 + a];
           const float hi = (float)v;
-          f[2 * ((size_t)j * h->gpcP + a)] = hi;
-          f[2 * ((size_t)j * h->gpcP + a) + 1] = (float)(v - (double)hi);
+          const size_t e = ((size_t)j * (Pp / 2) + a / 2) * 4 + (a & 1);
+          f[e] = hi;
+          f[e + 2] = (float)(v - (double)hi);
         }
       e = up(M.abf, f.data(), sizeof(float) * f.size());
     }
@@ -912,7 +916,7 @@ int sc_lbm_moments(sc_lbm_t h, int domain, double* mean, double* stdev, const in
   MomentArgs A;
   A.domain = domain;
   A.ab = (const double*)(h->ws + L.dom[domain].ab);
-  A.abf = (const float2*)(h->ws + L.dom[domain].abf);
+  A.abf = (const float4*)(h->ws + L.dom[domain].abf);
   A.nq = h->nq[domain];
   A.stride = h->gpcP + 1;
   A.P = gpc_coef ? h->gpcP : 0;
@@ -961,7 +965,7 @@ int sc_lbm_moment_sums(sc_lbm_t h, int domain, double* d_s1, double* d_s2, doubl
   MomentArgs A;
   A.domain = domain;
   A.ab = (const double*)(h->ws + h->L.dom[domain].ab);
-  A.abf = (const float2*)(h->ws + h->L.dom[domain].abf);
+  A.abf = (const float4*)(h->ws + h->L.dom[domain].abf);
   A.nq = h->nq[domain];
   A.stride = h->gpcP + 1;
   A.P = d_gpc_sums ? h->gpcP : 0;

@@ -536,5 +536,18 @@ __device__ __forceinline__ void save_outlet(const DevDomain& D, const Node<S>& N
   b[4] = float(g[14]);
 }
 
+// ------------------------------------------------------------ host dispatch
+// Calls f with a null pointer of the population storage type of a precision.
+template <class F>
+int dispatch(int precision, F&& f) {
+  switch (precision) {
+    case SC_P_FP32_SHIFT: return f((float*)nullptr);
+    case SC_P_BF16_STORE: return f((__nv_bfloat16*)nullptr);
+    case SC_P_FP16_STORE: return f((__half*)nullptr);
+    case SC_P_FP64_PLAIN: return f((double*)nullptr);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 }  // namespace sclbm

@@ -16,6 +16,15 @@ namespace sclbm {
 constexpr int kQ = 19;
 constexpr int kMaxDomains = SC_MAX_DOMAINS;
 constexpr int kMaxGpcP = 28;     // largest gPC basis the reduction kernel keeps in registers
+// The basis sizes the in-place precisions' reduction is compiled for: the gPC
+// basis size P padded up to an even size of at least 4 while P <= 12 (one
+// thread a cell sums two terms at a time), to a multiple of 4 above (two
+// threads a cell, each half the term pairs).  It is also the row length of
+// the pair table abf.
+constexpr int gpc_pair_pad(int P) {
+  return P <= 0 ? 0 : P <= 4 ? 4 : P <= 12 ? (P + 1) / 2 * 2 : (P + 3) / 4 * 4;
+}
+static_assert(kMaxGpcP % 4 == 0, "the pair table's rows split into two halves of term pairs");
 constexpr int kRun = 256;        // cells per run of the TMA-staged kernels; the row pitch is a multiple
 
 // Link word per cell (64 bits).  Bits 2i, 2i+1 give the kind of link i, the
@@ -200,7 +209,8 @@ int launch_init_equilibrium(const StepParams& P, int precision, void* stream);
 struct MomentArgs {
   int domain;
   const double* ab;        // [nq][stride] : a_j then a_j * Phi_alpha(Z_j)
-  const float2* abf;       // [nq][P] : a_j * Phi_alpha(Z_j) as (hi, lo) floats, hi + lo to 48 bits
+  const float4* abf;       // [nq][gpc_pair_pad(P) / 2] : a_j * Phi_alpha(Z_j) of terms (a, a + 1) as
+                           // (hi_a, hi_a+1, lo_a, lo_a+1) floats, hi + lo to 48 bits; zero pad terms
   int stride;              // row length of ab (basis size of the configuration + 1)
   int nq, P;               // P: coefficients to produce (0 = none)
   double wsum;
