@@ -40,8 +40,12 @@ namespace {
 constexpr int kNoallocMaxNodes = SC_NOALLOC_MAX_NODES;
 constexpr int kMaxDevices = 64;
 
-// The count of non-finite field values (cleared per call).
-static __device__ unsigned long long g_noalloc_nonfinite;
+// The device scratch of the entry point, a file-scope array at a 256-byte
+// boundary: one word, the count of non-finite field values (cleared per
+// call).  Its size does not depend on the request; the request's limit
+// (kNoallocMaxNodes) comes from the kernel-parameter space of the weights.
+constexpr int kNoallocScratchWords = 1;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocScratchWords];
 
 // The weights a_j by value: 8 KB, inside the 32 KB kernel-parameter limit.
 struct QuadWeights {
@@ -77,7 +81,7 @@ int setup_for_current_device(void** out, int* sms, char* err, size_t err_len) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_noalloc_nonfinite);
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       put_err(err, err_len, "cudaGetSymbolAddress of the no-alloc counter failed on device %d: %s", dev,
               cudaGetErrorString(e));
