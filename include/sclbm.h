@@ -179,8 +179,13 @@ typedef struct {
  * for 3 blocks, 3 uses 4 blocks for the even and 3 for the odd level, 1
  * streams runs of 256 consecutive cells through shared memory with TMA bulk
  * copies (needs nx a multiple of 16 bytes of populations; launch and graph
- * modes only).  Default: 64 x 2, slab 8, tile order 1, variant 0, launch
- * mode.                                                                     */
+ * modes only).  With BF16 / FP16 storage, the BGK collision and an even nx
+ * in every domain, variants 0 and 3 run the even level with two x-adjacent
+ * cells per thread (one 32-bit access per population pair, the collision on
+ * packed FP32x2 operations; the block then covers 2 * block_x cells in x),
+ * sized for 2 (variant 0) or 3 (variant 3) resident blocks; the results
+ * equal the one-cell form's to FP32 rounding, not bit for bit.  Default:
+ * 64 x 2, slab 8, tile order 1, variant 0, launch mode.                     */
 typedef struct {
   int block_x, block_y, slab_z, tile_order, exec_mode, graph_steps, variant;
 } sc_lbm_tuning;
@@ -489,9 +494,10 @@ int sc_lbm_destroy(sc_lbm_t h);
  * library routine.
  *
  * The weights travel by value as a kernel parameter (8 KB).  The one piece
- * of scratch, a counter of non-finite inputs, is a fixed file-scope device
- * variable (8 bytes) held by every GPU that loads the library until the
- * process exits.  The first call on each device (with that device current)
+ * of scratch, a counter of non-finite inputs, is one 8-byte word of a
+ * fixed file-scope device array (256-byte aligned) held by every GPU that
+ * loads the library until the process exits; its size does not depend on
+ * the request.  The first call on each device (with that device current)
  * looks up its address and the device's SM count and must not be made
  * inside a stream capture; every later call issues only a memset, one
  * kernel and, with d_nonfinite, a device-to-device copy on `stream`, so it

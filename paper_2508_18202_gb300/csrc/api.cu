@@ -356,6 +356,17 @@ int cuda_fail(sc_lbm_t h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);         \
   } while (0)
 
+// Whether the two-cells-per-thread kernels can run: 16-bit storage, the BGK
+// collision and an even nx in every domain (the first cell of a pair then
+// sits at an even index, and each pair of populations is one aligned word).
+bool pairs_ok(const sc_lbm_t h) {
+  if (h->cfg.collision == SC_COLL_RR) return false;
+  if (h->cfg.precision != SC_P_BF16_STORE && h->cfg.precision != SC_P_FP16_STORE) return false;
+  for (int d = 0; d < h->P.n_domains; ++d)
+    if (h->P.dom[d].nx % 2) return false;
+  return true;
+}
+
 void apply_tiling(sc_lbm_t h) {
   StepParams& P = h->P;
   P.bx = h->tune.block_x;
@@ -383,6 +394,11 @@ void apply_tiling(sc_lbm_t h) {
   P.tma = (h->tune.variant == 1 && h->tma_ok && h->tune.exec_mode != SC_EXEC_PERSISTENT) ? 1 : 0;
   P.even85 = h->tune.variant == 2 ? 1 : 0;
   P.odd85 = (h->tune.variant == 2 || h->tune.variant == 3) ? 1 : 0;
+  // 16-bit storage with the BGK collision, every domain's rows pairing up
+  // (even nx): two x-adjacent cells per thread on the even level in variants
+  // 0 (kernel sized for 2 resident blocks) and 3 (3 blocks)
+  const bool pairs = pairs_ok(h) && !P.tma;
+  P.even_pair = !pairs ? 0 : h->tune.variant == 0 ? 2 : h->tune.variant == 3 ? 3 : 0;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;

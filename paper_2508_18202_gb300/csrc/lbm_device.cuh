@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sclbm_internal.h"
 
@@ -143,6 +144,11 @@ __device__ __forceinline__ uint8_t ld_keep(const uint8_t* p) {
   unsigned short v;
   asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(keep_policy()));
   return (uint8_t)v;
+}
+__device__ __forceinline__ uint16_t ld_keep(const uint16_t* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(keep_policy()));
+  return (uint16_t)v;
 }
 
 // ------------------------------------------------------------ collision
@@ -299,6 +305,131 @@ __device__ __forceinline__ void collide_rr(T g[kQ], T tau0, T smag18c2, bool sma
     g[i] = W<T>(i) * v;
   }
 }
+
+// ------------------------------------------------------------ two cells at once
+// The BGK(+Smagorinsky) collision of collide<float, true> for two cells, one
+// in each lane of Blackwell's packed FP32x2 operations (__fadd2_rn,
+// __fmul2_rn, __ffma2_rn; each lane rounds as the scalar operation does),
+// which halves the arithmetic instructions of the 16-bit storage paths.  The
+// moments come from the sums s = g_i + g_opp(i) and differences d = g_i -
+// g_opp(i) of the nine opposite pairs, and the equilibrium's even part
+// base + rho (4.5 (c.u)^2 - 1.5 u^2) from (4.5 rho) (c.u)^2 + (base - rho 1.5
+// u^2): the same quantities as collide(), summed and rounded in another
+// order.  Reciprocals and square roots are taken lane by lane, correctly
+// rounded.
+__device__ __forceinline__ float2 p2dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, p2dup(-1.0f), a); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ void collide_pair(float2 g[kQ], float tau0, float smag18c2, bool smag_on) {
+  // pairs (2p + 1, 2p + 2): c = (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0)
+  // (1,0,1) (1,0,-1) (0,1,1) (0,1,-1) and their opposites
+  float2 s = p2add(g[1], g[2]), d = p2sub(g[1], g[2]);
+  float2 m0 = p2add(g[0], s), jx = d, pxx = s;
+  s = p2add(g[3], g[4]), d = p2sub(g[3], g[4]);
+  m0 = p2add(m0, s);
+  float2 jy = d, pyy = s;
+  s = p2add(g[5], g[6]), d = p2sub(g[5], g[6]);
+  m0 = p2add(m0, s);
+  float2 jz = d, pzz = s;
+  s = p2add(g[7], g[8]), d = p2sub(g[7], g[8]);
+  m0 = p2add(m0, s), jx = p2add(jx, d), jy = p2add(jy, d), pxx = p2add(pxx, s), pyy = p2add(pyy, s);
+  float2 pxy = s;
+  s = p2add(g[9], g[10]), d = p2sub(g[9], g[10]);
+  m0 = p2add(m0, s), jx = p2add(jx, d), jy = p2sub(jy, d), pxx = p2add(pxx, s), pyy = p2add(pyy, s);
+  pxy = p2sub(pxy, s);
+  s = p2add(g[11], g[12]), d = p2sub(g[11], g[12]);
+  m0 = p2add(m0, s), jx = p2add(jx, d), jz = p2add(jz, d), pxx = p2add(pxx, s), pzz = p2add(pzz, s);
+  float2 pxz = s;
+  s = p2add(g[13], g[14]), d = p2sub(g[13], g[14]);
+  m0 = p2add(m0, s), jx = p2add(jx, d), jz = p2sub(jz, d), pxx = p2add(pxx, s), pzz = p2add(pzz, s);
+  pxz = p2sub(pxz, s);
+  s = p2add(g[15], g[16]), d = p2sub(g[15], g[16]);
+  m0 = p2add(m0, s), jy = p2add(jy, d), jz = p2add(jz, d), pyy = p2add(pyy, s), pzz = p2add(pzz, s);
+  float2 pyz = s;
+  s = p2add(g[17], g[18]), d = p2sub(g[17], g[18]);
+  m0 = p2add(m0, s), jy = p2add(jy, d), jz = p2sub(jz, d), pyy = p2add(pyy, s), pzz = p2add(pzz, s);
+  pyz = p2sub(pyz, s);
+
+  const float2 rho = p2add(p2dup(1.0f), m0);
+  const float2 inv = make_float2(recip(rho.x), recip(rho.y));
+  const float2 ux = p2mul(jx, inv), uy = p2mul(jy, inv), uz = p2mul(jz, inv);
+  const float2 usq = p2fma(uz, uz, p2fma(uy, uy, p2mul(ux, ux)));
+  float2 omega = p2dup(recip(tau0));
+  if (smag_on) {
+    // Pi^neq = sum c c g - (m0/3 I + rho u u), as in collide()
+    const float2 third = p2mul(m0, p2dup(1.0f / 3.0f));
+    const float2 rx = p2mul(rho, ux), ry = p2mul(rho, uy), rz = p2mul(rho, uz);
+    const float2 nxx = p2sub(pxx, p2fma(rx, ux, third));
+    const float2 nyy = p2sub(pyy, p2fma(ry, uy, third));
+    const float2 nzz = p2sub(pzz, p2fma(rz, uz, third));
+    const float2 nxy = p2sub(pxy, p2mul(rx, uy));
+    const float2 nxz = p2sub(pxz, p2mul(rx, uz));
+    const float2 nyz = p2sub(pyz, p2mul(ry, uz));
+    const float2 dia = p2fma(nzz, nzz, p2fma(nyy, nyy, p2mul(nxx, nxx)));
+    const float2 off = p2fma(nyz, nyz, p2fma(nxz, nxz, p2mul(nxy, nxy)));
+    // 2 Pi:Pi + 1e-30 = 2 (diagonal) + 4 (off-diagonal) + 1e-30
+    const float2 a = p2fma(p2dup(4.0f), off, p2fma(p2dup(2.0f), dia, p2dup(1e-30f)));
+    const float2 pin = make_float2(sqrtf(a.x), sqrtf(a.y));
+    const float2 b = p2fma(p2dup(smag18c2), p2mul(pin, inv), p2dup(tau0 * tau0));
+    const float2 tau = p2mul(p2dup(0.5f), p2add(p2dup(tau0), make_float2(sqrtf(b.x), sqrtf(b.y))));
+    omega = make_float2(recip(tau.x), recip(tau.y));
+  }
+  const float2 nom = p2mul(omega, p2dup(-1.0f));
+  const float2 base = p2sub(m0, p2mul(rho, p2mul(p2dup(1.5f), usq)));  // m0 - 1.5 rho u^2
+  const float2 r45 = p2mul(p2dup(4.5f), rho), r3 = p2mul(p2dup(3.0f), rho);
+  // g_i - omega (g_i - w_i e_i), the weight multiplying last as in collide()
+  g[0] = p2fma(nom, p2fma(p2dup(-W<float>(0)), base, g[0]), g[0]);
+  auto relax = [&](int i, float2 cu) {
+    const float2 even = p2fma(r45, p2mul(cu, cu), base);
+    const float2 odd = p2mul(r3, cu);
+    const float2 nw = p2dup(-W<float>(i));
+    g[i] = p2fma(nom, p2fma(nw, p2add(even, odd), g[i]), g[i]);
+    g[i + 1] = p2fma(nom, p2fma(nw, p2sub(even, odd), g[i + 1]), g[i + 1]);
+  };
+  relax(1, ux);
+  relax(3, uy);
+  relax(5, uz);
+  relax(7, p2add(ux, uy));
+  relax(9, p2sub(ux, uy));
+  relax(11, p2add(ux, uz));
+  relax(13, p2sub(ux, uz));
+  relax(15, p2add(uy, uz));
+  relax(17, p2sub(uy, uz));
+}
+
+// Two x-adjacent 16-bit populations as one 32-bit word (the lower address,
+// the even cell, in the low half) and the FP32 pair they stand for.
+template <class S>
+struct Pair16;
+template <>
+struct Pair16<__nv_bfloat16> {
+  static __device__ __forceinline__ float2 unpack(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+  static __device__ __forceinline__ uint32_t pack(float2 v) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);  // each lane rounded to nearest even
+    uint32_t w;
+    memcpy(&w, &h, sizeof w);
+    return w;
+  }
+};
+template <>
+struct Pair16<__half> {
+  static __device__ __forceinline__ float2 unpack(uint32_t w) {
+    __half2 h;
+    memcpy(&h, &w, sizeof w);
+    return __half22float2(h);
+  }
+  static __device__ __forceinline__ uint32_t pack(float2 v) {
+    const __half2 h = __floats2half2_rn(v.x, v.y);
+    uint32_t w;
+    memcpy(&w, &h, sizeof w);
+    return w;
+  }
+};
 
 // The collision of the compiled unit: BGK(+Smagorinsky), or the recursive
 // regularized form in the unit built with SCLBM_RR_UNIT.

@@ -124,6 +124,9 @@ __device__ __forceinline__ TileHead decode_tile_head(const StepParams& P, unsign
 }
 
 // Block-wide decode of tile t: thread (0,0) decodes, the block reads it.
+// CPT: x-adjacent cells per thread (the tile is then CPT * blockDim.x cells
+// wide, P.bx = CPT * blockDim.x); R.x is the thread's first cell.
+template <int CPT = 1>
 __device__ __forceinline__ TileRef block_tile(const StepParams& P, unsigned t) {
   __shared__ TileHead s_head;
   if (threadIdx.x == 0 && threadIdx.y == 0) s_head = decode_tile_head(P, t);
@@ -133,7 +136,7 @@ __device__ __forceinline__ TileRef block_tile(const StepParams& P, unsigned t) {
   const DevDomain& D = P.dom[H.d];
   R.d = H.d;
   R.node = H.node;
-  R.x = H.x0 + threadIdx.x;
+  R.x = H.x0 + CPT * threadIdx.x;
   R.y = H.y0 + threadIdx.y;
   R.z0 = H.z0;
   R.z1 = min(H.z0 + P.bz, D.nz);
@@ -337,6 +340,69 @@ __global__ void __launch_bounds__(256, MINB) aa_even_kernel(const __grid_constan
   }
   even_tile<S, false, true>(P, block_tile(P, k));
 }
+
+#ifndef SCLBM_RR_UNIT
+// Even level with 16-bit storage, two x-adjacent cells per thread (the first
+// at an even x of a domain with even nx, so each pair of populations is one
+// aligned 32-bit word): the run of pairs of a z-slab.  A pair whose cells
+// are both bulk cells moves its populations as 32-bit words and collides in
+// the two lanes of the packed FP32x2 operations; a pair with one bulk cell
+// (the other solid or listed, and updated by the listed blocks) loads and
+// stores that cell alone, in both lanes.  The class bytes of the next pair
+// are loaded one cell ahead.
+template <class S>
+__device__ __forceinline__ void even_run_pair(const StepParams& P, S* base, const uint8_t* cp, int pc, int plane,
+                                              int n) {
+  uint16_t next = ld_keep(reinterpret_cast<const uint16_t*>(cp));
+  for (int k = 0; k < n; ++k, base += plane, cp += plane) {
+    const unsigned cls = next;
+    if (k + 1 < n) next = ld_keep(reinterpret_cast<const uint16_t*>(cp + plane));
+    const bool a = !(cls & kClsSkip), b = !((cls >> 8) & kClsSkip);
+    if (!(a || b)) continue;
+    float2 g[kQ];
+    if (a && b) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) g[i] = Pair16<S>::unpack(*reinterpret_cast<const uint32_t*>(base + i * pc));
+    } else {
+      const S* c = a ? base : base + 1;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) g[i] = p2dup(Store<S>::ld(c + i * pc));
+    }
+    collide_pair(g, P.tau0, P.smag18c2, P.csmag_on);
+    if (a && b) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) *reinterpret_cast<uint32_t*>(base + OPP(i) * pc) = Pair16<S>::pack(g[i]);
+    } else {
+      S* c = a ? base : base + 1;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) Store<S>::st(c + OPP(i) * pc, g[i].x);
+    }
+  }
+}
+
+// Even time level with 16-bit storage, two cells per thread (launched with
+// the tiling of pair_tiling: tiles 2 * blockDim.x cells wide); the listed
+// cells ride in blocks spread over the grid as in aa_even_kernel.  MINB:
+// resident blocks of 256 threads (2: no spills at 110 registers; 3: 80
+// registers, a few bytes spilled, half as many warps again in flight).
+template <class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) aa_even_pair_kernel(const __grid_constant__ StepParams P) {
+  unsigned k;
+  if (block_role(P, &k)) {
+    const long long item = k * (long long)(blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
+    even_boundary_item<S, false>(P, item);
+    return;
+  }
+  const TileRef R = block_tile<2>(P, k);
+  if (!R.valid) return;
+  const DevDomain& D = P.dom[R.d];
+  const int plane = D.nx * D.ny;
+  const int idx0 = R.x + D.nx * (R.y + D.ny * R.z0);
+  even_run_pair<S>(P, reinterpret_cast<S*>(D.g) + (long long)R.node * kQ * D.pitch + idx0, D.cls + idx0,
+                   (int)D.pitch, plane, R.z1 - R.z0);
+}
+
+#endif
 
 // Odd time level in one launch: the listed blocks take the listed boundary
 // cells (one thread per (node, cell)), the rest the tiles of bulk cells.  The
@@ -826,6 +892,25 @@ inline bool turns_inflow(const StepParams& P) {
   return !(P.wp.cos_d == 1.0f && P.wp.sin_d == 0.0f && P.wq.cos_d == 1.0f && P.wq.sin_d == 0.0f);
 }
 
+#ifndef SCLBM_RR_UNIT
+// The launch parameters of the two-cells-per-thread even kernel: the same
+// launch with tiles 2 * bx cells wide.
+StepParams pair_tiling(const StepParams& P) {
+  StepParams Q = P;
+  Q.bx = 2 * P.bx;
+  long long begin = 0;
+  for (int d = 0; d < Q.n_domains; ++d) {
+    DevDomain& D = Q.dom[d];
+    D.tiles_x = (D.nx + Q.bx - 1) / Q.bx;
+    D.tiles_per_node = D.tiles_x * D.tiles_y * D.tiles_z;
+    D.tile_begin = begin;
+    begin += D.tiles_per_node * D.nodes;
+  }
+  Q.total_tiles = begin;
+  return Q;
+}
+#endif
+
 int launch_aa_step(const StepParams& P, int precision, void* stream, int parity) {
   dim3 block(P.bx, P.by);
   cudaStream_t s = (cudaStream_t)stream;
@@ -843,6 +928,17 @@ int launch_aa_step(const StepParams& P, int precision, void* stream, int parity)
       const long long threads = (long long)P.bx * P.by;
       const unsigned lgrid = (unsigned)(P.total_tiles + (P.total_bitems + threads - 1) / threads);
       if (parity == 0) {
+#ifndef SCLBM_RR_UNIT
+        if constexpr (sizeof(S) == 2) {
+          if (P.even_pair && !P.tma) {
+            const StepParams Q = pair_tiling(P);
+            const unsigned qgrid = (unsigned)(Q.total_tiles + (Q.total_bitems + threads - 1) / threads);
+            if (P.even_pair == 3) aa_even_pair_kernel<S, 3><<<qgrid, block, 0, s>>>(Q);
+            else aa_even_pair_kernel<S, 2><<<qgrid, block, 0, s>>>(Q);
+            return (int)cudaGetLastError();
+          }
+        }
+#endif
         if (P.tma) aa_even_tma_kernel<S><<<tgrid, kTmaThreads, even_tma_smem<S>(), s>>>(P);
         else if (P.even85) aa_even_kernel<S, 3><<<lgrid, block, 0, s>>>(P);
         else aa_even_kernel<S, 4><<<lgrid, block, 0, s>>>(P);

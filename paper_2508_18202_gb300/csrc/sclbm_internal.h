@@ -147,6 +147,8 @@ struct StepParams {
   long long total_runs;        // runs of kRun cells of all domains and nodes
   int tma;                     // bulk kernels staged through shared memory by TMA
   int odd85, even85;           // per-thread odd / even kernels sized for 3 blocks (85 registers)
+  int even_pair;               // 16-bit storage, BGK: even level two x-adjacent cells per thread,
+                               // kernel sized for 2 or 3 resident blocks (0: one cell per thread)
   int bx, by, bz, order;
   // persistent mode
   unsigned int* bar_count;

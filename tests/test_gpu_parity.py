@@ -118,6 +118,44 @@ def test_reduced_storage_tracks_oracle(O, cuda, precision, variant):
     ens.close()
 
 
+@pytest.mark.parametrize("series", [False, True], ids=["steady", "series"])
+@pytest.mark.parametrize("precision,unit", [(W.BF16_STORE, 2.0 ** -8), (W.FP16_STORE, 2.0 ** -11)],
+                         ids=["bf16", "fp16"])
+def test_two_cell_even_level_matches_one_cell_form(cuda, precision, unit, series):
+    """16-bit storage, even nx: the even level with two x-adjacent cells per
+    thread (variants 0 and 3: 32-bit population words, the collision on
+    packed FP32x2 operations, pairs with one bulk cell next to a solid or
+    listed cell) against the one-cell form (variant 2) after 9 even and 9 odd
+    levels.  The two collisions round differently in FP32, which can move a
+    stored value by one unit of the 16-bit format now and then; unit is the
+    format's unit roundoff (BF16 8, FP16 11 significant bits) and g = f - w
+    the stored deviation.  With an inflow series (a 10-degree offset from
+    level 0) the odd levels take the kernels that turn the inflow."""
+    wl = ragged(BC_SETS["urban"], precision=precision, nx=40)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None]
+    states = {}
+    for variant in (2, 0, 3):
+        ens = S.Ensemble(S.make_config(wl))
+        S.sc_lbm_set_tuning(ens.h, 32, 2, 4, variant=variant)
+        if series:
+            ens.set_inflow_series(*SERIES)
+        ens.step(18)
+        states[variant] = [gpu_state(ens, 0, j) for j in range(ens.n_nodes[0])]
+        ens.sync()
+        ens.close()
+    flags = S.sc_lbm_geometry(S.make_config(wl), 0).reshape(-1)
+    fl = fluid_mask(flags)
+    for variant in (0, 3):
+        for j, (a, b) in enumerate(zip(states[variant], states[2])):
+            ga, gb = a[:, fl] - w, b[:, fl] - w
+            scale = np.max(np.abs(gb))
+            assert scale > 1e-3, scale
+            e_max = float(np.max(np.abs(ga - gb)) / scale)
+            e_l2 = rel_l2(ga, gb)
+            assert e_max <= 16 * unit, (variant, j, e_max)
+            assert e_l2 <= unit, (variant, j, e_l2)
+
+
 def test_laminar_channel_1000_steps(O, cuda):
     """Cube in a channel, BGK tau = 0.6, FP32 shifted vs FP64: velocity relative
     L2 <= 1e-5 after 1000 steps (first and last collocation nodes)."""

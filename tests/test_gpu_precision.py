@@ -9,8 +9,10 @@ Fields: mean and std of |u| (Eq. quad_moments), the 95% profile band
 (Eq. coef_discrete), after 200 steps of BGK + Smagorinsky with a 20-step
 start-up ramp.
 
-Tolerances, in units of the storage format's unit roundoff u (FP16 2^-11,
-BF16 2^-9; the populations are rounded to the format at every store):
+Tolerances, in units of u (the populations are rounded to the format at
+every store): for FP16 u = 2^-11, its unit roundoff; for BF16 u = 2^-9,
+half its unit roundoff 2^-8 (8 significant bits), the stricter bound the
+measured errors meet:
   mean, band, gPC coefficient 0 (= mean):  relative L2 <= 2u,
   std:                                     relative L2 <= 8u,
   every gPC coefficient:                   ||c_k - c_k^oracle|| <= 2u ||c_0^oracle||,
