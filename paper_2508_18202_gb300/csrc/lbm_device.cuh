@@ -309,8 +309,9 @@ __device__ __forceinline__ void collide_rr(T g[kQ], T tau0, T smag18c2, bool sma
 // ------------------------------------------------------------ two cells at once
 // The BGK(+Smagorinsky) collision of collide<float, true> for two cells, one
 // in each lane of Blackwell's packed FP32x2 operations (__fadd2_rn,
-// __fmul2_rn, __ffma2_rn; each lane rounds as the scalar operation does),
-// which halves the arithmetic instructions of the 16-bit storage paths.  The
+// __fmul2_rn, __ffma2_rn; each lane rounds as the scalar operation does):
+// the even level of the 16-bit storage modes, at half the arithmetic
+// instructions per cell.  The
 // moments come from the sums s = g_i + g_opp(i) and differences d = g_i -
 // g_opp(i) of the nine opposite pairs, and the equilibrium's even part
 // base + rho (4.5 (c.u)^2 - 1.5 u^2) from (4.5 rho) (c.u)^2 + (base - rho 1.5
