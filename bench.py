@@ -525,10 +525,14 @@ def leg_adjoint(cx):
             "loss": Jg, "grad": [float(gg[0]), float(gg[1])]}
 
 
-def leg_e2e(cx, wl, cfg, columns, L, n_steps, world):
+def leg_e2e(cx, wl, cfg, columns, L, n_steps, world, n_nodes_all):
     """End to end through the C ABI with host buffers: per benchmark step
     sc_lbm_init from pinned host geometry (H2D), L time steps, and the moments
-    into pinned host memory (D2H)."""
+    into pinned host memory (D2H).  Under torchrun each rank initialises its
+    own node range, and the moments come from the FP64 moment sums
+    all-reduced over the ranks and finished by the library (the one exchange
+    of the sharded path); the value counts every rank's lattice updates over
+    the slowest rank's time."""
     S, torch, np = cx.S, cx.torch, cx.np
     D = wl["domains"][0]
     cells = D["nx"] * D["ny"] * D["nz"]
@@ -540,8 +544,13 @@ def leg_e2e(cx, wl, cfg, columns, L, n_steps, world):
     std_h = torch.empty(cells, dtype=torch.float64).pin_memory()
     prof_h = torch.empty(len(columns) * D["nz"] * 4, dtype=torch.float64).pin_memory()
     fh = (S.C.c_void_p * 1)(flags_pinned.data_ptr())
+    if world > 1:
+        dist = torch.distributed
+        s1, s2 = (torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(2))
+        mean_d, std_d = (torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(2))
+        wt = torch.empty(1, dtype=torch.float64, device="cuda")
+        cur = torch.cuda.current_stream()
     t = cx.tuning
-    nodes = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(n_steps):
@@ -552,30 +561,47 @@ def leg_e2e(cx, wl, cfg, columns, L, n_steps, world):
             t["block_x"], t["block_y"], t["slab_z"], t["tile_order"], t["exec_mode"], t["graph_steps"],
             t["variant"])), handle=hh)
         S.sc_lbm_step(hh, L)
-        S.sc_lbm_moments(hh, 0, mean_h, std_h, columns, prof_h, None, None, out_host=True)
+        if world > 1:
+            S.sc_lbm_moment_sums(hh, 0, s1, s2, None)
+            wt.fill_(S.sc_lbm_weight_sum(hh, 0))
+            cur.wait_stream(stream)
+            for x in (s1, s2, wt):
+                dist.all_reduce(x, op=dist.ReduceOp.SUM)
+            stream.wait_stream(cur)
+            S.sc_lbm_moments_from_sums(hh, 0, s1, s2, float(wt.item()), mean_d, std_d)
+            cur.wait_stream(stream)
+            mean_h.copy_(mean_d, non_blocking=True)
+            std_h.copy_(std_d, non_blocking=True)
+            cur.synchronize()
+        else:
+            S.sc_lbm_moments(hh, 0, mean_h, std_h, columns, prof_h, None, None, out_host=True)
         S.sc_lbm_destroy(hh)
     dt = time.perf_counter() - t0
     if world > 1:
         tt = torch.tensor([dt], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         dt = float(tt.item())
-    _, a = S.sc_lbm_quadrature(cfg, 0)
-    nodes = len(a)
     del ws
     torch.cuda.empty_cache()
     # geometry flags, link words, class bytes; listed (outlet) cells with
-    # their 256-byte rule records; inflow tables; node weights x gPC basis
-    # (the ramp travels in the launch parameters)
+    # their 256-byte rule records (each rank holds the geometry); inflow
+    # tables; node weights x gPC basis (the ramp travels in the launch
+    # parameters)
     n_listed = int((flags.reshape(D["nz"], D["ny"], D["nx"])[:, :, -1] == 0).sum())
     P = 1
     if wl.get("gpc_degree", -1) >= 0:
         from math import comb
         P = comb(wl["gpc_degree"] + len(wl["inputs"]), len(wl["inputs"])) + 1
-    h2d = cells * (1 + 8 + 1) + n_listed * (4 + 256) + nodes * D["nz"] * (16 + 24) + nodes * 8 * P
-    d2h = 2 * 8 * cells + len(columns) * D["nz"] * 4 * 8
-    return {"value": round(float(cells) * nodes * L * n_steps * world / dt / 1e9, 4), "unit": "GLUPS",
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_steps,
-            "note": "per step: sc_lbm_init from pinned host geometry, %d time steps, moments to pinned host" % L}
+    h2d = world * (cells * (1 + 8 + 1) + n_listed * (4 + 256)) + n_nodes_all * (D["nz"] * (16 + 24) + 8 * P)
+    if world > 1:
+        d2h = world * 2 * 8 * cells
+        note = ("per step and rank: sc_lbm_init of its node range from pinned host geometry, %d time steps, "
+                "FP64 moment sums all-reduced, mean and std to pinned host; bytes summed over the ranks" % L)
+    else:
+        d2h = 2 * 8 * cells + len(columns) * D["nz"] * 4 * 8
+        note = "per step: sc_lbm_init from pinned host geometry, %d time steps, moments to pinned host" % L
+    return {"value": round(float(cells) * n_nodes_all * L * n_steps / dt / 1e9, 4), "unit": "GLUPS",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_steps, "note": note}
 
 
 def leg_cpu(wl_head):
@@ -650,7 +676,8 @@ def main():
     if args.workload != HEADLINE or args.nodes:
         skip |= set(LEGS.split(",")) - {"tune"}
     if world > 1:
-        skip |= set(LEGS.split(",")) - {"tune"}   # the legs are single-GPU measurements
+        # the extra legs are single-GPU measurements; e2e runs on every rank
+        skip |= set(LEGS.split(",")) - {"tune", "e2e"}
 
     def barrier():
         if world > 1:
@@ -730,6 +757,10 @@ def main():
     peak, peak_kind = peaks()
     khash = kernel_source_hash()
     traffic = recorded_traffic(khash, wl["name"] + ("" if not args.nodes else "_L%d" % args.nodes), tuning)
+    if traffic is not None and world > 1:
+        # the recorded figure covers every node of the rule; this rank's
+        # launches run its node range (traffic is proportional to nodes)
+        traffic = traffic * sum(nodes_d) / len(a_full)
     extra = {}
     out = ens.moments(0, probes=columns[0], gpc=P >= 0)
     fl = torch.from_numpy(S.sc_lbm_geometry(cfg, 0) == 0).cuda()
@@ -769,8 +800,8 @@ def main():
     legs["paper_case"] = run_leg("paper", leg_paper, cx)
     legs["adjoint"] = run_leg("adjoint", leg_adjoint, cx)
     e2e = None
-    if "e2e" not in skip and world == 1:
-        e2e = leg_e2e(cx, wl, cfg, columns[0], L, args.steps, world)
+    if "e2e" not in skip:
+        e2e = leg_e2e(cx, wl, cfg, columns[0], L, args.steps, world, len(a_full))
     cpu = None
     if "cpu" not in skip and rank == 0 and world == 1:
         cpu = leg_cpu(wl)
