@@ -685,6 +685,11 @@ class Ensemble:
         if self.h:
             sc_lbm_destroy(self.h)
             self.h = None
+        # sc_lbm_destroy has waited for the handle's stream, so the library is
+        # done with the workspace: release it now, not when this object goes,
+        # so that the next ensemble (the next wave of run_in_waves) can have
+        # the memory while a reference to this one is still alive
+        self.ws = None
 
     def __del__(self):
         try:
